@@ -1,0 +1,350 @@
+"""Benchmark: unique CNF-valid solutions per second of the GPU SAT sampler.
+
+One bench "step" is one sampling round of the whole hot path over one batch:
+Philox init of the logits, `steps` fused Adam steps (relaxed forward, l2 loss,
+adjoint, update), threshold, Boolean pass, exact CNF check and deduplication.
+Workload (default): Tseitin-encoded random circuit, 2,000 inputs, 20,000
+2-input gates (AND/OR/XOR, inputs negated w.p. 1/2), depth 40, fan-in from
+the previous 4 levels, 32 outputs fixed by a planted input; batch 65,536,
+500 steps, FP32.  Inputs are synthetic and seeded (instance seed 1).
+
+Launch: `python bench.py [--gpus N --steps K --warmup W]`; N > 1 under
+torch.distributed.run, one rank per GPU; ranks sample disjoint Philox streams
+(weak scaling, no collective on the data path).  `--impl reference` times the
+CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+WORKLOADS = {
+    "tseitin20k": dict(kind="tseitin", n_pi=2000, n_gates=20000, depth=40, n_out=32, seed=1,
+                       batch=65536, steps=500, lr=0.1, init_scale=1.0, act_dtype="f32"),
+    "tseitin20k_bf16": dict(kind="tseitin", n_pi=2000, n_gates=20000, depth=40, n_out=32, seed=1,
+                            batch=65536, steps=500, lr=0.1, init_scale=1.0, act_dtype="bf16"),
+    "tseitin80k_bf16": dict(kind="tseitin", n_pi=5000, n_gates=80000, depth=80, n_out=32, seed=1,
+                            batch=262144, steps=500, lr=0.1, init_scale=1.0, act_dtype="bf16"),
+    "planted3sat": dict(kind="planted3sat", n_vars=50, n_clauses=200, seed=1,
+                        batch=1024, steps=200, lr=0.1, init_scale=1.0, act_dtype="f32"),
+}
+ACT_BYTES = {"f32": 4, "bf16": 2, "f16": 2}
+
+
+def instance_text(w):
+    from workloads import tseitin_random_circuit, planted_3sat
+    if w["kind"] == "tseitin":
+        return tseitin_random_circuit(w["n_pi"], w["n_gates"], w["depth"], w["n_out"], seed=w["seed"]).dimacs()
+    return planted_3sat(w["n_vars"], w["n_clauses"], w["seed"]).dimacs()
+
+
+def algorithmic_bytes_per_step(info, B, act_dtype):
+    """Minimum HBM bytes of one fused step with stored activations.
+
+    Per sample: every cone gate stores its activation once (forward) and
+    loads it once (adjoint); every cone input loads V (forward), stores and
+    reloads P, and loads + stores V, m, v (update).  Adjoints are counted as
+    staying on chip.
+    """
+    sa = ACT_BYTES[act_dtype]
+    return B * (info["n_cone_gates"] * 2 * sa + info["n_cone_pi"] * (4 + 2 * sa + 24))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-i", str(self.gpu), "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        if self.p is None:
+            return None
+        self.f.flush()
+        rows = [r.split(",") for r in Path(self.f.name).read_text().strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, x in zip(names, r[5:9]) if "Active" in x and "Not" not in x})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return d.get("hbm_gbs", 6400.0), "measured"
+    return 6400.0, "fallback"
+
+
+def profile_traffic(workload, act_dtype):
+    """Per-step DRAM bytes of the fused step kernel from the committed ncu summary,
+    or None when absent or taken on a different kernel source."""
+    f = ROOT / "profiles" / f"steps_kernel_{workload}.md"
+    if not f.exists():
+        return None, None
+    text = f.read_text()
+    m = re.search(r"dram_bytes_per_sample_step:\s*([0-9.eE+]+)", text)
+    h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
+    if not m or not h or h.group(1) != kernel_source_hash():
+        return None, None
+    return float(m.group(1)), f.name
+
+
+def kernel_source_hash():
+    return hashlib.sha256((ROOT / "paper_2502_08673_b300" / "csrc" / "kernels.cu").read_bytes()).hexdigest()[:16]
+
+
+# --------------------------------------------------------------------------
+def oracle_sample(text, w, n_samples, n_steps):
+    """Time the CPU oracle on a bounded sample: n_samples x n_steps + verification."""
+    import oracle
+    orc = oracle.Oracle(text)
+    V0 = oracle.init_normal(n_samples, orc.n_pi, seed=0, rnd=0, scale=w["init_scale"])
+    t0 = time.perf_counter()
+    res = oracle.sample_round(orc.flat, orc.n_vars, orc.clauses, V0, steps=n_steps, lr=w["lr"])
+    dt = time.perf_counter() - t0
+    n_cone_gates = sum(1 for _ in orc.flat.ins_out)  # oracle instructions evaluated per sample-step
+    return {"seconds": dt, "valid": int(res["valid"].sum()), "unique": len(res["unique"]),
+            "samples": n_samples, "steps": n_steps, "instr": n_cone_gates,
+            "threads": oracle.lib().orc_threads()}
+
+
+def cpu_baseline_entry(text, w, budget_s=15.0):
+    # scale the sample so the oracle runs for roughly budget_s seconds
+    probe = oracle_sample(text, w, 8, 4)
+    per_sample_step = probe["seconds"] / (8 * 4)
+    steps = w["steps"]
+    n = int(max(4, min(1024, budget_s / max(per_sample_step * steps, 1e-9))))
+    r = oracle_sample(text, w, n, steps)
+    return {"value": r["unique"] / r["seconds"], "unit": "unique valid solutions/s", "cores": r["threads"],
+            "kind": "oracle",
+            "sample": f"{n} samples x {steps} Adam steps (+verify) of the same workload, FP64, "
+                      f"{r['valid']} valid / {r['unique']} unique in {r['seconds']:.1f} s",
+            "sample_steps_per_s": n * steps / r["seconds"]}
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    text = instance_text(w)
+    per_step = []
+    info = {}
+    for k in range(args.warmup + args.steps):
+        r = oracle_sample(text, w, args.ref_samples, w["steps"])
+        if k >= args.warmup:
+            per_step.append(r)
+        info = r
+    secs = sum(r["seconds"] for r in per_step)
+    uniq = sum(r["unique"] for r in per_step)
+    value = uniq / secs if secs > 0 else 0.0
+    line = {"impl": "reference", "metric": "unique CNF-valid solutions/sec", "value": value,
+            "unit": "unique valid solutions/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / max(1, args.steps), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, **{k: v for k, v in w.items() if k != "kind"},
+                       "reference_batch_per_step": args.ref_samples},
+            "cpu_baseline": {"value": value, "unit": "unique valid solutions/s", "cores": info.get("threads"),
+                             "kind": "oracle",
+                             "sample": f"{args.ref_samples} samples x {w['steps']} steps per step (bounded sample)"},
+            "e2e": {"value": value, "unit": "unique valid solutions/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "sample_steps_per_s": args.ref_samples * w["steps"] * args.steps / secs if secs else None}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="tseitin20k", choices=sorted(WORKLOADS))
+    ap.add_argument("--batch", type=int, default=0, help="override the workload batch")
+    ap.add_argument("--gd-steps", type=int, default=0, help="override the workload's optimisation steps")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ref-samples", type=int, default=16)
+    args = ap.parse_args()
+    w = dict(WORKLOADS[args.workload])
+    if args.batch:
+        w["batch"] = args.batch
+    if args.gd_steps:
+        w["steps"] = args.gd_steps
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+    import torch.distributed as dist
+    import paper_2502_08673_b300 as P
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    text = instance_text(w)
+    cnf = P.Cnf.from_dimacs(text)
+    t0 = time.perf_counter()
+    circ = P.Circuit.build(cnf)
+    transform_s = time.perf_counter() - t0
+    plan = P.Plan.create(circ, cnf)
+    info = plan.info
+    B, steps, ad = w["batch"], w["steps"], w["act_dtype"]
+    opt = P.opt_params("adam", lr=w["lr"])
+    ws = P.new_workspace(plan, B, ad)
+    n_rounds = args.warmup + args.steps
+    dedup = P.Dedup.create(plan, max_keys=B * (n_rounds + 1), max_batch=B)
+    stream = torch.cuda.current_stream()
+    round_base = rank << 20
+
+    def one_round(k, ev=None):
+        P.sat_init_normal(plan, ws.V, seed=0, round_=round_base + k, scale=w["init_scale"])
+        ws.m.zero_()
+        ws.v.zero_()
+        if ev is not None:
+            ev[0].record(stream)
+        P.sat_steps(plan, opt, ws.V, ws.m, ws.v, ws.act, ws.adj, 1, steps, act_dtype=ad)
+        if ev is not None:
+            ev[1].record(stream)
+        P.sat_threshold(plan, ws.V, ws.bits, ws.keys)
+        P.sat_hard_eval(plan, ws.bits, B)
+        P.sat_cnf_check(plan, ws.bits, ws.valid, B)
+        dedup.insert(ws.keys, ws.valid, B)
+
+    for k in range(args.warmup):
+        one_round(k)
+    torch.cuda.synchronize()
+    before = dedup.count()
+    valid_total = 0
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        start.record(stream)
+        for k in range(args.steps):
+            one_round(args.warmup + k, kev[k])
+            valid_total += int(P.valid_mask(ws.valid, B).sum())
+        end.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    elapsed_ms = start.elapsed_time(end)
+    uniq = dedup.count() - before
+    kernel_ms = [a.elapsed_time(b) for a, b in kev]
+    t_max, uniq_all, valid_all = elapsed_ms, uniq, valid_total
+    if world > 1:
+        tt = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        cnt = torch.tensor([uniq, valid_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(cnt)
+        t_max, uniq_all, valid_all = float(tt.item()), int(cnt[0].item()), int(cnt[1].item())
+    value = uniq_all / (t_max / 1e3)
+    gate_evals = info["n_cone_gates"] * B * steps * args.steps * world
+    peak, peak_kind = measured_peaks()
+    alg = algorithmic_bytes_per_step(info, B, ad) * steps
+    kavg = statistics.mean(kernel_ms)
+    achieved = alg / (kavg / 1e3) / 1e9
+    dram_per_sample_step, prof = profile_traffic(args.workload, ad)
+
+    e2e = None
+    if not args.no_e2e:
+        # the user-facing call with host inputs: plan upload, rounds, key download
+        e2e_steps = max(1, min(args.steps, 2))
+        t1 = time.perf_counter()
+        ucount = 0
+        d2h = 0
+        for k in range(e2e_steps):
+            sols = P.sample(circ, cnf, n_wanted=10 ** 12, batch=B, steps=steps, max_rounds=1, lr=w["lr"], seed=0,
+                            first_round=round_base + n_rounds + k, init_scale=w["init_scale"], act_dtype=ad)
+            ucount += len(sols)
+            d2h += len(sols) * info["key_words"] * 4 + B // 8 + 16
+        e2e_s = time.perf_counter() - t1
+        plan_bytes = (info["n_cone_gates"] * 8 + info["n_gates"] * 8 + info["n_fanout_edges"] * 16
+                      + info["n_cone"] * 8 + info["n_clauses"] * 8 + 4 * sum(1 for _ in range(1)))
+        plan_bytes += int(np.ceil(cnf.info()[2] * 4))
+        e2e = {"value": ucount / e2e_s, "unit": "unique valid solutions/s", "h2d_bytes_per_step": plan_bytes,
+               "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps,
+               "note": "sat_sample from host CNF/circuit objects: plan upload, workspace, one round, key download"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_entry(text, w)
+
+    if rank == 0:
+        line = {
+            "metric": "unique CNF-valid solutions/sec", "value": value, "unit": "unique valid solutions/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": ad,
+            "data": "synthetic (seeded Tseitin random circuit)" if w["kind"] == "tseitin" else "synthetic (planted 3-SAT)",
+            "config": {"workload": args.workload, **{k: v for k, v in w.items() if k != "kind"},
+                       "optimizer": "adam", "l2_flush": "working set > L2 (activations %.1f GB)" %
+                       (info["n_cone"] * B * ACT_BYTES[ad] / 1e9),
+                       "parallelism": f"replicas x{world} (disjoint Philox streams)"},
+            "gate_evals_per_s": gate_evals / (t_max / 1e3),
+            "valid_fraction": valid_all / (B * args.steps * world),
+            "unique_in_timed_steps": uniq_all,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "kernel": "steps_kernel", "kernel_ms_avg": kavg,
+                         "algorithmic_bytes_per_launch": alg,
+                         "traffic": (dram_per_sample_step * B * steps) if dram_per_sample_step else None,
+                         "traffic_source": prof},
+            "gpu_launches": 8 * args.steps,
+            "transform_s": transform_s,
+            "plan": {k: info[k] for k in ("n_pi", "n_cone_pi", "n_cone_gates", "n_gates", "n_clauses",
+                                          "n_cone_levels", "max_span")},
+            "clocks": clocks.summary(),
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,258 @@
+/*
+ * satsampler.h — C ABI of a GPU SAT sampler built on gradient descent over a
+ * relaxed multi-level circuit (Ardakani, Kang, He, Huang, Wawrzynek,
+ * "High-Throughput SAT Sampling", arXiv 2502.08673).
+ *
+ * Pipeline (Section III): a CNF (Section II-A) is transformed once on the host
+ * into a multi-level, multi-output circuit (Algorithm 1 and its fallback); a
+ * batch of b samples of primary-input logits V is embedded as P = sigmoid(V)
+ * (Eq. 5), pushed through the relaxed circuit (Table 1, Eq. 6), scored by the
+ * l2 loss on the constrained outputs (Eq. 7) and updated by gradient steps
+ * (Eqs. 8-9, or Adam); the thresholded assignments that satisfy the original
+ * CNF are kept, without duplicates (end of Section III-A).
+ *
+ * Conventions (all calls):
+ *  - Every call returns sat_status; no C++ exception crosses this boundary.
+ *    On failure sat_last_error() (thread-local) describes the cause.
+ *  - Objects returned through an `out` pointer are owned by the caller and
+ *    released by the matching *_free, which accepts NULL.
+ *  - Inputs are never modified.  "Device" pointers are CUDA global-memory
+ *    pointers on the current device; "host" pointers are ordinary memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Device calls are asynchronous on that stream unless stated otherwise.
+ *  - Per-sample device arrays are node-major with the batch contiguous: row r
+ *    of an array with leading dimension ld starts at element r * ld.
+ *    V, m, v, gV: [n_pi][ldv] float32, ldv >= B, row r = primary input r in
+ *    ascending DIMACS-variable order (sat_plan_pi_vars).  act / adj: [n_cone]
+ *    [lda], lda >= B rounded up to a multiple of 32 (rows are written for
+ *    the padding lanes too).  Bit arrays: [rows][ldw] uint32, ldw >= ceil(B/32),
+ *    bit j of word w = sample 32 w + j.
+ *  - Deterministic for a given (seed, options, GPU).
+ */
+#ifndef SATSAMPLER_H
+#define SATSAMPLER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SAT_ABI_VERSION 1
+
+typedef enum sat_status {
+    SAT_OK = 0,
+    SAT_PARTIAL = 1,            /* sat_sample: budget spent before n_wanted distinct solutions */
+    SAT_ERR_PARSE = -1,         /* malformed DIMACS */
+    SAT_ERR_ARG = -2,           /* invalid argument (NULL, size, layout, alignment) */
+    SAT_ERR_OOM = -3,           /* host or device allocation failed */
+    SAT_ERR_CUDA = -4,          /* CUDA runtime error (message in sat_last_error) */
+    SAT_ERR_TABLE_FULL = -5,    /* dedup table full, or probe limit hit */
+    SAT_ERR_UNSAT_TRIVIAL = -6  /* the CNF holds an empty clause */
+} sat_status;
+
+typedef enum sat_act_dtype { SAT_ACT_F32 = 0, SAT_ACT_BF16 = 1, SAT_ACT_F16 = 2 } sat_act_dtype;
+typedef enum sat_optimizer { SAT_OPT_ADAM = 0, SAT_OPT_GD = 1 } sat_optimizer;
+
+typedef struct sat_cnf sat_cnf;
+typedef struct sat_circuit sat_circuit;
+typedef struct sat_plan sat_plan;
+typedef struct sat_dedup sat_dedup;
+typedef struct sat_solutions sat_solutions;
+
+/* Library version string and the last error of the calling thread. */
+const char* sat_version(void);
+const char* sat_last_error(void);
+
+/* ----------------------------------------------------------------- CNF ---
+ * DIMACS text (the format of Fig. 1(a)): `p cnf V C` header, `c` comment
+ * lines, clauses of non-zero literals ended by 0 (may span lines), optional
+ * `%` end marker.  A clause count different from C, a literal outside 1..V or
+ * an unterminated clause is SAT_ERR_PARSE.  The library keeps its own copy of
+ * `buf` (len bytes, need not be NUL-terminated). */
+sat_status sat_cnf_from_dimacs(const char* buf, size_t len, sat_cnf** out);
+sat_status sat_cnf_from_file(const char* path, sat_cnf** out);
+sat_status sat_cnf_info(const sat_cnf* cnf, uint32_t* n_vars, uint64_t* n_clauses, uint64_t* n_lits);
+void sat_cnf_free(sat_cnf* cnf);
+
+/* ------------------------------------------------------ transformation ---
+ * Algorithm 1 (Section III-A) with the fallback for under-specified clauses,
+ * on the host.  A sub-clause window SC is grown clause by clause; a variable v
+ * of SC is defined as f when f (from the clauses holding -v) is the complement
+ * of the expression from the clauses holding v.  Defined variables become
+ * intermediate, the other variables of the defining clauses primary inputs;
+ * constant definitions and leftover clauses become outputs constrained to 1.
+ * max_support (1..8, default 8) bounds the window's variables, max_window
+ * (default 16) its clauses.  NULL opts = defaults.  SAT_ERR_UNSAT_TRIVIAL for
+ * an empty clause. */
+typedef struct sat_build_opts {
+    uint32_t max_support;
+    uint32_t max_window;
+} sat_build_opts;
+
+typedef struct sat_build_stats {
+    uint32_t n_vars, n_pi, n_iv, n_outputs, n_const;
+    uint64_t n_gates;          /* lowered 2-input gates, whole circuit */
+    uint32_t n_cone_pi;        /* primary inputs in the outputs' fan-in cone */
+    uint64_t n_cone_gates;     /* gates the gradient loop evaluates */
+    uint32_t n_levels, n_cone_levels, max_span;
+    uint64_t ops_cnf;          /* 2-input gate equivalents of the CNF (Fig. 5, middle) */
+    uint64_t ops_circuit;      /* 2-input gate equivalents of the circuit */
+    double transform_ms, plan_ms;
+} sat_build_stats;
+
+sat_status sat_circuit_build(const sat_cnf* cnf, const sat_build_opts* opts, sat_circuit** out,
+                             sat_build_stats* stats /* nullable */);
+/* Canonical text form of the transformation result: `vars N`, `pi ...`,
+ * `def VAR KIND OUTNEG : lits` (SOP terms separated by ` |`), `out lits`.
+ * Writes at most cap bytes (NUL-terminated when it fits); *len = full length. */
+sat_status sat_circuit_dump(const sat_circuit* c, char* buf, size_t cap, size_t* len);
+void sat_circuit_free(sat_circuit* c);
+
+/* --------------------------------------------------------- device plan ---
+ * Uploads the lowered circuit (2-input gates in level order, fan-out lists for
+ * the adjoint) and the CNF (for the exact check) to the current device. */
+typedef struct sat_plan_info {
+    uint32_t n_vars, n_pi, n_cone_pi, n_outputs, n_cone_levels, n_levels, key_words, max_span;
+    uint64_t n_cone;           /* rows of act / adj: cone inputs + cone gates */
+    uint64_t n_nodes;          /* rows of the Boolean node array: inputs + all gates */
+    uint64_t n_cone_gates, n_gates, n_clauses, n_fanout_edges;
+} sat_plan_info;
+
+sat_status sat_plan_create(const sat_circuit* c, const sat_cnf* cnf, sat_plan** out);
+sat_status sat_plan_get_info(const sat_plan* p, sat_plan_info* info);
+/* Host arrays: vars[n_pi] = DIMACS variable of V row r. */
+sat_status sat_plan_pi_vars(const sat_plan* p, uint32_t* vars);
+/* Host arrays per DIMACS variable v (index 0 unused, n_vars + 1 entries):
+ * cone_node[v] = act row holding v's node (-1 outside the cone),
+ * full_node[v] = row of the Boolean node array, neg[v] = 1 when v is the
+ * complement of that node. */
+sat_status sat_plan_var_nodes(const sat_plan* p, int64_t* cone_node, int64_t* full_node, uint8_t* neg);
+void sat_plan_free(sat_plan* p);
+
+/* ------------------------------------------- hot-path kernels (device) ---
+ * All buffers are caller-owned device memory; B >= 0 samples. */
+
+/* V[r][b] = scale * z, z standard normal from Box-Muller on the first two
+ * words of Philox4x32-10 (Salmon et al., SC'11) at counter (b, r, round, 0)
+ * with key (seed low, seed high).  Initial distribution: the paper does not
+ * state one; this is the library's choice. */
+sat_status sat_init_normal(const sat_plan* p, uint64_t seed, uint32_t round, float scale, float* V, int64_t ldv,
+                           int64_t B, void* stream);
+
+/* Eq. 5-7: act[i] = sigmoid(V[cone input i]), every cone gate by Table 1,
+ * loss[b] = sum_j (Y_j - T_j)^2 accumulated in FP32 (loss nullable).  act holds
+ * act_dtype elements; arithmetic is FP32. */
+sat_status sat_forward(const sat_plan* p, sat_act_dtype act_dtype, const float* V, int64_t ldv, void* act,
+                       int64_t lda, float* loss, int64_t B, void* stream);
+
+/* Eq. 8 (chain rule with the Table 1 derivatives): gV[r][b] = d(sum_b w_b
+ * loss_b)/dV[r][b] with w = grad_loss (NULL = all ones), from the act written
+ * by sat_forward.  adj: [n_cone][lda] float32 scratch.  Rows of gV outside the
+ * cone are not written (their gradient is zero). */
+sat_status sat_backward(const sat_plan* p, sat_act_dtype act_dtype, const float* V, int64_t ldv, const void* act,
+                        int64_t lda, float* adj, const float* grad_loss, float* gV, int64_t B, void* stream);
+
+typedef struct sat_opt_params {
+    int32_t optimizer;         /* sat_optimizer */
+    float lr, beta1, beta2, eps;
+} sat_opt_params;
+
+/* One update of the cone rows of V at step t >= 1: GD (Eq. 9) V -= lr gV, or
+ * Adam (PyTorch's formulation, no weight decay) on state m, v. */
+sat_status sat_opt_update(const sat_plan* p, const sat_opt_params* o, float* V, float* m, float* v, const float* gV,
+                          int64_t ldv, int32_t t, int64_t B, void* stream);
+
+/* The fused hot loop: n_steps x (forward, loss, adjoint, update) at steps
+ * t0 .. t0 + n_steps - 1, one kernel launch.  loss (nullable) receives the
+ * per-sample loss of the last step's forward pass. */
+sat_status sat_steps(const sat_plan* p, sat_act_dtype act_dtype, const sat_opt_params* o, float* V, float* m,
+                     float* v, int64_t ldv, void* act, float* adj, int64_t lda, float* loss, int32_t t0,
+                     int32_t n_steps, int64_t B, void* stream);
+
+/* Hard threshold (end of Section III-A): bit = [V > 0] (sigmoid(V) > 1/2; ties
+ * give 0).  node_bits rows 0..n_pi-1 receive the bitsliced inputs; keys[b]
+ * (key_words uint32 per sample, bit j of word k = input 32k + j) the packed
+ * input vector used for deduplication. */
+sat_status sat_threshold(const sat_plan* p, const float* V, int64_t ldv, uint32_t* node_bits, int64_t ldw,
+                         uint32_t* keys, int64_t B, void* stream);
+
+/* Boolean evaluation of every gate (constrained and unconstrained paths,
+ * Fig. 1(b)) from the input rows of node_bits; rows n_pi..n_nodes-1 written. */
+sat_status sat_hard_eval(const sat_plan* p, uint32_t* node_bits, int64_t ldw, int64_t B, void* stream);
+
+/* Exact check against the ORIGINAL CNF: valid bit b = 1 iff the full
+ * assignment of sample b satisfies every clause.  valid: [ceil(B/32)] words,
+ * overwritten (padding bits 0). */
+sat_status sat_cnf_check(const sat_plan* p, const uint32_t* node_bits, int64_t ldw, uint32_t* valid, int64_t B,
+                         void* stream);
+
+/* ----------------------------------------------------- deduplication ---
+ * Device hash set of distinct solutions ("non-redundant", end of Section
+ * III-A), keyed by the packed primary-input bits (the full assignment is a
+ * function of them and contains them, so both are unique together).  Hash =
+ * SplitMix64 finaliser fold (Steele, Lea, Flood 2014): h = 0x9E3779B97F4A7C15;
+ * h = mix(h + w) over 64-bit key words w; h = mix(h ^ n_words).  Open
+ * addressing with linear probing and full-key comparison; the probe count is
+ * bounded, and a batch that would overflow max_keys is refused on the host
+ * with SAT_ERR_TABLE_FULL before any kernel runs. */
+sat_status sat_dedup_create(const sat_plan* p, uint64_t max_keys, int64_t max_batch, sat_dedup** out);
+/* Inserts the valid rows of keys [B][key_words] (device).  hashes[b] (nullable,
+ * device) = the key hash (0 for invalid rows); is_new[b] (nullable, device) =
+ * 1 iff row b was inserted now.  Synchronises `stream` to check capacity. */
+sat_status sat_dedup_insert(sat_dedup* d, const uint32_t* keys, const uint32_t* valid, int64_t B, uint64_t* hashes,
+                            uint8_t* is_new, void* stream);
+/* Number of stored keys (synchronises `stream`). */
+sat_status sat_dedup_count(const sat_dedup* d, uint64_t* n, void* stream);
+/* Copies stored keys [first, first+count) to host memory (synchronous). */
+sat_status sat_dedup_copy_keys(const sat_dedup* d, uint64_t first, uint64_t count, uint32_t* host_keys, void* stream);
+sat_status sat_dedup_clear(sat_dedup* d, void* stream);
+void sat_dedup_free(sat_dedup* d);
+
+/* -------------------------------------------------------- end to end ---
+ * Rounds of: init (or caller logits) -> `steps` fused steps -> threshold ->
+ * Boolean pass -> CNF check -> dedup, until n_wanted distinct solutions or
+ * max_rounds.  Round r draws its initial logits with round counter
+ * first_round + r.  Returns SAT_PARTIAL (with what was found) when the budget
+ * ends first. */
+typedef struct sat_sample_opts {
+    int64_t batch;
+    int32_t steps;
+    int32_t max_rounds;
+    sat_opt_params opt;
+    uint64_t seed;
+    uint32_t first_round;
+    float init_scale;
+    int32_t act_dtype;          /* sat_act_dtype */
+    int32_t steps_per_launch;   /* 0 = all steps in one launch */
+    const float* init_logits;   /* nullable device [n_pi][init_ld]: used instead of init for round 0 */
+    int64_t init_ld;
+    void* stream;
+} sat_sample_opts;
+
+typedef struct sat_sample_stats {
+    uint32_t rounds;
+    uint64_t samples, valid, unique;
+    double ms_init, ms_steps, ms_verify, ms_dedup, ms_total;   /* device time per phase (CUDA events) */
+    double ms_upload, ms_download;                              /* sat_sample only */
+} sat_sample_stats;
+
+void sat_sample_opts_default(sat_sample_opts* o);
+sat_status sat_sample(const sat_circuit* c, const sat_cnf* cnf, const sat_sample_opts* o, uint64_t n_wanted,
+                      sat_solutions** out, sat_sample_stats* stats);
+/* Same on an existing plan, adding to an existing dedup set (device-resident inputs). */
+sat_status sat_sample_plan(const sat_plan* p, sat_dedup* d, const sat_sample_opts* o, uint64_t n_wanted,
+                           sat_sample_stats* stats);
+
+uint64_t sat_solutions_count(const sat_solutions* s);
+uint32_t sat_solutions_nvars(const sat_solutions* s);
+/* Full assignments of solutions [first, first+count) in canonical ascending
+ * order: ceil(n_vars/64) uint64 words each, bit j of word k = variable 64k+j+1. */
+sat_status sat_solutions_copy(const sat_solutions* s, uint64_t first, uint64_t count, uint64_t* words_out);
+void sat_solutions_free(sat_solutions* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SATSAMPLER_H */

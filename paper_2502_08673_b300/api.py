@@ -1,0 +1,322 @@
+"""Python face of the C ABI: handle classes and tensor-level calls.
+
+Each function marshals arguments (torch tensors -> device pointers, the
+current CUDA stream) and calls the C entry point of the same name; all
+computation happens in the library's kernels.  Layouts are those of
+include/satsampler.h: V, m, v, gV are [n_pi, B] float32; act/adj are
+[n_cone, lda] with lda = B rounded up to 32; bit arrays are [rows, ceil(B/32)]
+int32 words.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _native as N
+from ._native import check, lib
+
+
+def _stream(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(0 if t is None else t.data_ptr())
+
+
+def round32(x: int) -> int:
+    return (x + 31) // 32 * 32
+
+
+class _Handle:
+    _free = None
+
+    def __init__(self, h):
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            getattr(lib(), self._free)(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Cnf(_Handle):
+    _free = "sat_cnf_free"
+
+    @classmethod
+    def from_dimacs(cls, text: str | bytes) -> "Cnf":
+        b = text.encode() if isinstance(text, str) else text
+        h = C.c_void_p()
+        check(lib().sat_cnf_from_dimacs(b, len(b), C.byref(h)))
+        return cls(h)
+
+    @classmethod
+    def from_file(cls, path: str) -> "Cnf":
+        h = C.c_void_p()
+        check(lib().sat_cnf_from_file(str(path).encode(), C.byref(h)))
+        return cls(h)
+
+    def info(self):
+        nv, nc, nl = C.c_uint32(), C.c_uint64(), C.c_uint64()
+        check(lib().sat_cnf_info(self._h, C.byref(nv), C.byref(nc), C.byref(nl)))
+        return nv.value, nc.value, nl.value
+
+
+def _struct_dict(s):
+    return {name: getattr(s, name) for name, _ in s._fields_}
+
+
+class Circuit(_Handle):
+    _free = "sat_circuit_free"
+
+    @classmethod
+    def build(cls, cnf: Cnf, max_support: int = 8, max_window: int = 16):
+        h = C.c_void_p()
+        st = N.BuildStats()
+        opts = N.BuildOpts(max_support, max_window)
+        check(lib().sat_circuit_build(cnf.handle, C.byref(opts), C.byref(h), C.byref(st)))
+        c = cls(h)
+        c.stats = _struct_dict(st)
+        return c
+
+    def dump(self) -> str:
+        n = C.c_size_t()
+        check(lib().sat_circuit_dump(self._h, None, 0, C.byref(n)))
+        buf = C.create_string_buffer(n.value + 1)
+        check(lib().sat_circuit_dump(self._h, buf, n.value + 1, C.byref(n)))
+        return buf.value.decode()
+
+
+class Plan(_Handle):
+    _free = "sat_plan_free"
+
+    @classmethod
+    def create(cls, circuit: Circuit, cnf: Cnf) -> "Plan":
+        h = C.c_void_p()
+        check(lib().sat_plan_create(circuit.handle, cnf.handle, C.byref(h)))
+        p = cls(h)
+        info = N.PlanInfo()
+        check(lib().sat_plan_get_info(h, C.byref(info)))
+        p.info = _struct_dict(info)
+        return p
+
+    def __getattr__(self, k):
+        info = self.__dict__.get("info")
+        if info is not None and k in info:
+            return info[k]
+        raise AttributeError(k)
+
+    def pi_vars(self) -> np.ndarray:
+        out = np.zeros(self.info["n_pi"], np.uint32)
+        check(lib().sat_plan_pi_vars(self._h, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def var_nodes(self):
+        n = self.info["n_vars"] + 1
+        cone = np.zeros(n, np.int64)
+        full = np.zeros(n, np.int64)
+        neg = np.zeros(n, np.uint8)
+        check(lib().sat_plan_var_nodes(self._h, cone.ctypes.data_as(C.c_void_p), full.ctypes.data_as(C.c_void_p),
+                                       neg.ctypes.data_as(C.c_void_p)))
+        return cone, full, neg
+
+
+class Dedup(_Handle):
+    _free = "sat_dedup_free"
+
+    @classmethod
+    def create(cls, plan: Plan, max_keys: int, max_batch: int) -> "Dedup":
+        h = C.c_void_p()
+        check(lib().sat_dedup_create(plan.handle, max_keys, max_batch, C.byref(h)))
+        d = cls(h)
+        d.key_words = plan.info["key_words"]
+        return d
+
+    def insert(self, keys, valid, B: int, hashes=None, is_new=None, stream=None):
+        check(lib().sat_dedup_insert(self._h, _ptr(keys), _ptr(valid), B, _ptr(hashes), _ptr(is_new),
+                                     _stream(stream)))
+
+    def count(self, stream=None) -> int:
+        n = C.c_uint64()
+        check(lib().sat_dedup_count(self._h, C.byref(n), _stream(stream)))
+        return n.value
+
+    def keys(self, stream=None) -> np.ndarray:
+        n = self.count(stream)
+        out = np.zeros((n, self.key_words), np.uint32)
+        check(lib().sat_dedup_copy_keys(self._h, 0, n, out.ctypes.data_as(C.c_void_p), _stream(stream)))
+        return out
+
+    def clear(self, stream=None):
+        check(lib().sat_dedup_clear(self._h, _stream(stream)))
+
+
+class Solutions(_Handle):
+    _free = "sat_solutions_free"
+
+    def __len__(self):
+        return lib().sat_solutions_count(self._h)
+
+    @property
+    def n_vars(self):
+        return lib().sat_solutions_nvars(self._h)
+
+    def words(self, first: int = 0, count: int | None = None) -> np.ndarray:
+        n = len(self) - first if count is None else count
+        nw = (self.n_vars + 63) // 64
+        out = np.zeros((n, nw), np.uint64)
+        check(lib().sat_solutions_copy(self._h, first, n, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def assignments(self) -> np.ndarray:
+        """[count, n_vars] 0/1 array (variable v in column v-1)."""
+        w = self.words()
+        bits = np.unpackbits(w.view(np.uint8), axis=1, bitorder="little")
+        return bits[:, : self.n_vars]
+
+
+# --------------------------------------------------------- kernel calls ---
+def opt_params(optimizer="adam", lr=0.1, beta1=0.9, beta2=0.999, eps=1e-8) -> N.OptParams:
+    return N.OptParams(N.OPTIMIZERS[optimizer], lr, beta1, beta2, eps)
+
+
+def _act_torch_dtype(act_dtype: str):
+    import torch
+    return {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[act_dtype]
+
+
+def new_act(plan: Plan, B: int, act_dtype: str = "f32", device="cuda"):
+    import torch
+    return torch.empty((plan.info["n_cone"], round32(B)), dtype=_act_torch_dtype(act_dtype), device=device)
+
+
+def new_adj(plan: Plan, B: int, device="cuda"):
+    import torch
+    return torch.empty((plan.info["n_cone"], round32(B)), dtype=torch.float32, device=device)
+
+
+def sat_init_normal(plan: Plan, V, seed: int, round_: int = 0, scale: float = 1.0, stream=None):
+    check(lib().sat_init_normal(plan.handle, seed, round_, scale, _ptr(V), V.stride(0), V.shape[1], _stream(stream)))
+
+
+def sat_forward(plan: Plan, V, act, loss=None, act_dtype="f32", stream=None):
+    check(lib().sat_forward(plan.handle, N.ACT_DTYPES[act_dtype], _ptr(V), V.stride(0), _ptr(act), act.stride(0),
+                            _ptr(loss), V.shape[1], _stream(stream)))
+
+
+def sat_backward(plan: Plan, V, act, adj, gV, grad_loss=None, act_dtype="f32", stream=None):
+    check(lib().sat_backward(plan.handle, N.ACT_DTYPES[act_dtype], _ptr(V), V.stride(0), _ptr(act), act.stride(0),
+                             _ptr(adj), _ptr(grad_loss), _ptr(gV), V.shape[1], _stream(stream)))
+
+
+def sat_opt_update(plan: Plan, opt: N.OptParams, V, m, v, gV, t: int, stream=None):
+    check(lib().sat_opt_update(plan.handle, C.byref(opt), _ptr(V), _ptr(m), _ptr(v), _ptr(gV), V.stride(0), t,
+                               V.shape[1], _stream(stream)))
+
+
+def sat_steps(plan: Plan, opt: N.OptParams, V, m, v, act, adj, t0: int, n_steps: int, loss=None,
+              act_dtype="f32", stream=None):
+    check(lib().sat_steps(plan.handle, N.ACT_DTYPES[act_dtype], C.byref(opt), _ptr(V), _ptr(m), _ptr(v), V.stride(0),
+                          _ptr(act), _ptr(adj), act.stride(0), _ptr(loss), t0, n_steps, V.shape[1],
+                          _stream(stream)))
+
+
+def sat_threshold(plan: Plan, V, node_bits, keys, stream=None):
+    check(lib().sat_threshold(plan.handle, _ptr(V), V.stride(0), _ptr(node_bits), node_bits.stride(0), _ptr(keys),
+                              V.shape[1], _stream(stream)))
+
+
+def sat_hard_eval(plan: Plan, node_bits, B: int, stream=None):
+    check(lib().sat_hard_eval(plan.handle, _ptr(node_bits), node_bits.stride(0), B, _stream(stream)))
+
+
+def sat_cnf_check(plan: Plan, node_bits, valid, B: int, stream=None):
+    check(lib().sat_cnf_check(plan.handle, _ptr(node_bits), node_bits.stride(0), _ptr(valid), B, _stream(stream)))
+
+
+@dataclass
+class Workspace:
+    """Device buffers of one sampling round (torch-allocated)."""
+    B: int
+    V: object
+    m: object
+    v: object
+    act: object
+    adj: object
+    bits: object
+    keys: object
+    valid: object
+    loss: object
+    act_dtype: str = "f32"
+
+
+def new_workspace(plan: Plan, B: int, act_dtype: str = "f32", device="cuda") -> Workspace:
+    import torch
+    npi = plan.info["n_pi"]
+    W = (B + 31) // 32
+    z = lambda *s: torch.zeros(s, dtype=torch.float32, device=device)
+    return Workspace(
+        B, z(npi, B), z(npi, B), z(npi, B), new_act(plan, B, act_dtype, device), new_adj(plan, B, device),
+        torch.zeros((plan.info["n_nodes"], W), dtype=torch.int32, device=device),
+        torch.zeros((B, max(1, plan.info["key_words"])), dtype=torch.int32, device=device),
+        torch.zeros(W, dtype=torch.int32, device=device), z(B), act_dtype)
+
+
+def run_round(plan: Plan, ws: Workspace, opt: N.OptParams, steps: int, seed: int, round_: int,
+              init_scale: float = 1.0, dedup: Dedup | None = None, init_logits=None, stream=None):
+    """One round on device-resident buffers: init, steps, threshold, Boolean pass, CNF check, dedup."""
+    if init_logits is None:
+        sat_init_normal(plan, ws.V, seed, round_, init_scale, stream)
+    else:
+        ws.V.copy_(init_logits)
+    ws.m.zero_()
+    ws.v.zero_()
+    if steps > 0:
+        sat_steps(plan, opt, ws.V, ws.m, ws.v, ws.act, ws.adj, 1, steps, loss=ws.loss, act_dtype=ws.act_dtype,
+                  stream=stream)
+    sat_threshold(plan, ws.V, ws.bits, ws.keys, stream)
+    sat_hard_eval(plan, ws.bits, ws.B, stream)
+    sat_cnf_check(plan, ws.bits, ws.valid, ws.B, stream)
+    if dedup is not None:
+        dedup.insert(ws.keys, ws.valid, ws.B, stream=stream)
+
+
+def valid_mask(valid_words, B: int) -> np.ndarray:
+    w = valid_words.cpu().numpy().view(np.uint32)
+    bits = np.unpackbits(w.view(np.uint8), bitorder="little")
+    return bits[:B].astype(bool)
+
+
+def sample(circuit: Circuit, cnf: Cnf, n_wanted: int, batch=1024, steps=200, max_rounds=1, optimizer="adam",
+           lr=0.1, beta1=0.9, beta2=0.999, eps=1e-8, seed=0, first_round=0, init_scale=1.0, act_dtype="f32",
+           steps_per_launch=0, stream=None):
+    """End to end from host objects (the C call sat_sample)."""
+    o = N.SampleOpts()
+    lib().sat_sample_opts_default(C.byref(o))
+    o.batch, o.steps, o.max_rounds = batch, steps, max_rounds
+    o.opt = opt_params(optimizer, lr, beta1, beta2, eps)
+    o.seed, o.first_round, o.init_scale = seed, first_round, init_scale
+    o.act_dtype, o.steps_per_launch = N.ACT_DTYPES[act_dtype], steps_per_launch
+    o.stream = None if stream is None else stream.cuda_stream
+    h = C.c_void_p()
+    st = N.SampleStats()
+    status = check(lib().sat_sample(circuit.handle, cnf.handle, C.byref(o), n_wanted, C.byref(h), C.byref(st)),
+                   allow_partial=True)
+    sols = Solutions(h)
+    sols.status = status
+    sols.stats = _struct_dict(st)
+    return sols

@@ -1,0 +1,762 @@
+// extern "C" boundary of the sampler library: argument checks, object
+// lifetimes, device uploads and the end-to-end round loop.  Every step of the
+// path runs in the kernels of kernels.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <new>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "../../include/satsampler.h"
+#include "device.hpp"
+#include "host.hpp"
+
+struct sat_cnf {
+    sat::Cnf cnf;
+};
+
+struct sat_circuit {
+    sat::Circuit circ;
+    sat::Plan plan;
+    double plan_ms = 0.0;
+    uint64_t cnf_clauses = 0;
+};
+
+struct sat_plan {
+    int device = 0;
+    sat::DevPlan dp;
+    std::vector<void*> allocs;
+    std::vector<int32_t> h_c_level_off, h_f_level_off;
+    std::vector<uint32_t> pi_var;
+    std::vector<int64_t> var_cone, var_full;
+    std::vector<uint8_t> var_neg;
+    // host copy of the full schedule, for expanding solution keys
+    std::vector<int32_t> f_in0, f_in1;
+    std::vector<uint8_t> f_gop;
+    sat_plan_info info{};
+};
+
+struct sat_dedup {
+    int device = 0;
+    sat::DevDedup d;
+    int64_t max_batch = 0;
+    unsigned long long* slot_of = nullptr;
+};
+
+struct sat_solutions {
+    uint32_t n_vars = 0, n_pi = 0, key_words = 0;
+    uint64_t count = 0;
+    std::vector<uint32_t> keys;        // [count][key_words], canonical order
+    std::vector<int32_t> f_in0, f_in1;
+    std::vector<uint8_t> f_gop;
+    std::vector<int64_t> var_full;
+    std::vector<uint8_t> var_neg;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+sat_status fail(sat_status s, const std::string& m) {
+    g_err = m;
+    return s;
+}
+
+#define CK(expr)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (expr);                                                                  \
+        if (e_ != cudaSuccess) return fail(SAT_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T>
+sat_status upload(sat_plan* p, const std::vector<T>& h, const T** dst) {
+    *dst = nullptr;
+    if (h.empty()) return SAT_OK;
+    void* d = nullptr;
+    if (cudaMalloc(&d, h.size() * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SAT_ERR_OOM, "cudaMalloc failed for plan array");
+    }
+    p->allocs.push_back(d);
+    CK(cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    *dst = (const T*)d;
+    return SAT_OK;
+}
+
+sat_status check_device(int device) {
+    int cur = -1;
+    CK(cudaGetDevice(&cur));
+    if (cur != device) return fail(SAT_ERR_ARG, "object belongs to another device than the current one");
+    return SAT_OK;
+}
+
+int64_t round32(int64_t x) { return (x + 31) / 32 * 32; }
+
+sat_status check_layout(const sat_plan* p, int64_t B, int64_t ldv, int64_t lda) {
+    if (!p) return fail(SAT_ERR_ARG, "plan is NULL");
+    if (B < 0) return fail(SAT_ERR_ARG, "B < 0");
+    if (ldv >= 0 && ldv < B) return fail(SAT_ERR_ARG, "ldv < B");
+    if (lda >= 0 && lda < round32(B)) return fail(SAT_ERR_ARG, "lda must be >= B rounded up to a multiple of 32");
+    if (B >= (1ll << 31)) return fail(SAT_ERR_ARG, "B must be < 2^31");
+    return check_device(p->device);
+}
+
+cudaStream_t S(void* s) { return (cudaStream_t)s; }
+
+sat::OptParams opt_of(const sat_opt_params* o) {
+    sat::OptParams r;
+    r.opt = o->optimizer;
+    r.lr = o->lr;
+    r.b1 = o->beta1;
+    r.b2 = o->beta2;
+    r.eps = o->eps;
+    return r;
+}
+
+bool opt_ok(const sat_opt_params* o) {
+    return o && (o->optimizer == SAT_OPT_ADAM || o->optimizer == SAT_OPT_GD) &&
+           (o->optimizer == SAT_OPT_GD || (o->beta1 >= 0 && o->beta1 < 1 && o->beta2 >= 0 && o->beta2 < 1));
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sat_version(void) { return "satsampler 0.1 (sm_103a)"; }
+const char* sat_last_error(void) { return g_err.c_str(); }
+
+// ------------------------------------------------------------------ CNF --
+sat_status sat_cnf_from_dimacs(const char* buf, size_t len, sat_cnf** out) {
+    if (!out || (!buf && len)) return fail(SAT_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    try {
+        std::string copy(buf ? buf : "", len);
+        auto* c = new sat_cnf();
+        std::string err;
+        if (!sat::parse_dimacs(copy.c_str(), copy.size(), c->cnf, err)) {
+            delete c;
+            return fail(SAT_ERR_PARSE, err);
+        }
+        *out = c;
+        return SAT_OK;
+    } catch (const std::bad_alloc&) {
+        return fail(SAT_ERR_OOM, "host allocation failed");
+    }
+}
+
+sat_status sat_cnf_from_file(const char* path, sat_cnf** out) {
+    if (!path || !out) return fail(SAT_ERR_ARG, "NULL argument");
+    std::ifstream f(path, std::ios::binary);
+    if (!f) return fail(SAT_ERR_ARG, std::string("cannot open ") + path);
+    std::stringstream ss;
+    ss << f.rdbuf();
+    std::string s = ss.str();
+    return sat_cnf_from_dimacs(s.data(), s.size(), out);
+}
+
+sat_status sat_cnf_info(const sat_cnf* c, uint32_t* n_vars, uint64_t* n_clauses, uint64_t* n_lits) {
+    if (!c) return fail(SAT_ERR_ARG, "NULL cnf");
+    if (n_vars) *n_vars = c->cnf.n_vars;
+    if (n_clauses) *n_clauses = c->cnf.n_clauses();
+    if (n_lits) *n_lits = c->cnf.lits.size();
+    return SAT_OK;
+}
+
+void sat_cnf_free(sat_cnf* c) { delete c; }
+
+// ------------------------------------------------------- transformation --
+sat_status sat_circuit_build(const sat_cnf* cnf, const sat_build_opts* opts, sat_circuit** out,
+                             sat_build_stats* st) {
+    if (!cnf || !out) return fail(SAT_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    sat::TransformOpts to;
+    if (opts) {
+        to.max_support = opts->max_support;
+        to.max_window = opts->max_window;
+    }
+    try {
+        auto* c = new sat_circuit();
+        std::string err;
+        if (!sat::transform(cnf->cnf, to, c->circ, err)) {
+            delete c;
+            return fail(err.rfind("empty clause", 0) == 0 ? SAT_ERR_UNSAT_TRIVIAL : SAT_ERR_ARG, err);
+        }
+        auto t0 = std::chrono::steady_clock::now();
+        if (!sat::build_plan(c->circ, cnf->cnf, c->plan, err)) {
+            delete c;
+            return fail(SAT_ERR_ARG, err);
+        }
+        c->plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        c->cnf_clauses = cnf->cnf.n_clauses();
+        if (st) {
+            const sat::Plan& P = c->plan;
+            *st = sat_build_stats{};
+            st->n_vars = c->circ.n_vars;
+            st->n_pi = (uint32_t)c->circ.pis.size();
+            st->n_iv = (uint32_t)c->circ.defs.size();
+            st->n_outputs = (uint32_t)c->circ.outputs.size();
+            st->n_const = c->circ.n_const;
+            st->n_gates = P.in0.size();
+            st->n_cone_pi = P.n_cone_pi;
+            st->n_cone_gates = P.c_in0.size();
+            st->n_levels = (uint32_t)(P.level_off.size() - 2);
+            st->n_cone_levels = (uint32_t)(P.c_level_off.size() - 2);
+            st->max_span = P.max_span;
+            st->ops_cnf = P.ops_cnf;
+            st->ops_circuit = P.ops_circuit;
+            st->transform_ms = c->circ.wall_ms;
+            st->plan_ms = c->plan_ms;
+        }
+        *out = c;
+        return SAT_OK;
+    } catch (const std::bad_alloc&) {
+        return fail(SAT_ERR_OOM, "host allocation failed");
+    }
+}
+
+sat_status sat_circuit_dump(const sat_circuit* c, char* buf, size_t cap, size_t* len) {
+    if (!c) return fail(SAT_ERR_ARG, "NULL circuit");
+    std::string s = sat::circuit_dump(c->circ);
+    if (len) *len = s.size();
+    if (buf && cap) {
+        size_t n = std::min(cap, s.size() + 1);
+        std::memcpy(buf, s.c_str(), n);
+    }
+    return SAT_OK;
+}
+
+void sat_circuit_free(sat_circuit* c) { delete c; }
+
+// ---------------------------------------------------------------- plan --
+void sat_plan_free(sat_plan* p) {
+    if (!p) return;
+    for (void* a : p->allocs) cudaFree(a);
+    delete p;
+}
+
+sat_status sat_plan_create(const sat_circuit* c, const sat_cnf* cnf, sat_plan** out) {
+    if (!c || !cnf || !out) return fail(SAT_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    if (cnf->cnf.n_vars != c->circ.n_vars || cnf->cnf.n_clauses() != c->cnf_clauses)
+        return fail(SAT_ERR_ARG, "circuit was built from a different CNF");
+    const sat::Plan& P = c->plan;
+    if (P.n_cone >= (1ull << 28) || P.n_nodes >= (1ull << 28))
+        return fail(SAT_ERR_ARG, "circuit too large: node ids must fit in 28 bits");
+    auto* p = new sat_plan();
+    CK(cudaGetDevice(&p->device));
+    sat_status st;
+    auto bail = [&](sat_status s) { sat_plan_free(p); return s; };
+    sat::DevPlan& d = p->dp;
+    d.n_cone_pi = (int32_t)P.n_cone_pi;
+    d.n_cone = (int64_t)P.n_cone;
+    d.n_clev = (int32_t)P.c_level_off.size() - 2;
+    d.n_out = (int32_t)P.c_out_node.size();
+    d.n_pi = (int32_t)P.n_pi;
+    d.n_nodes = (int64_t)P.n_nodes;
+    d.n_flev = (int32_t)P.level_off.size() - 2;
+    d.n_clauses = (int64_t)(P.cl_off.size() - 1);
+    d.key_words = (int32_t)((P.n_pi + 31) / 32);
+    std::vector<int2> cg(P.c_in0.size()), fg(P.in0.size());
+    for (size_t g = 0; g < cg.size(); g++) cg[g] = make_int2(P.c_in0[g] | ((int32_t)P.c_gop[g] << 28), P.c_in1[g]);
+    for (size_t g = 0; g < fg.size(); g++) fg[g] = make_int2(P.in0[g] | ((int32_t)P.gop[g] << 28), P.in1[g]);
+    std::vector<int4> fe(P.fo_g.size());
+    for (size_t e = 0; e < fe.size(); e++) fe[e] = make_int4(P.fo_g[e], P.fo_sib[e], P.fo_c0[e], P.fo_c1[e]);
+    std::vector<int32_t> cl_lit(P.cl_node.size());
+    for (size_t i = 0; i < cl_lit.size(); i++) cl_lit[i] = (P.cl_node[i] << 1) | P.cl_neg[i];
+    if ((st = upload(p, P.c_level_off, &d.c_level_off)) != SAT_OK) return bail(st);
+    if ((st = upload(p, cg, &d.c_gate)) != SAT_OK) return bail(st);
+    if ((st = upload(p, P.cone_pi_row, &d.cone_pi_row)) != SAT_OK) return bail(st);
+    if ((st = upload(p, P.fo_off, &d.fo_off)) != SAT_OK) return bail(st);
+    if ((st = upload(p, fe, &d.fo_edge)) != SAT_OK) return bail(st);
+    if ((st = upload(p, P.c_out_node, &d.c_out_node)) != SAT_OK) return bail(st);
+    if ((st = upload(p, P.out_target, &d.out_target)) != SAT_OK) return bail(st);
+    if ((st = upload(p, P.level_off, &d.f_level_off)) != SAT_OK) return bail(st);
+    if ((st = upload(p, fg, &d.f_gate)) != SAT_OK) return bail(st);
+    if ((st = upload(p, P.cl_off, &d.cl_off)) != SAT_OK) return bail(st);
+    if ((st = upload(p, cl_lit, &d.cl_lit)) != SAT_OK) return bail(st);
+    p->h_c_level_off = P.c_level_off;
+    p->h_f_level_off = P.level_off;
+    d.h_c_level_off = p->h_c_level_off.data();
+    d.h_f_level_off = p->h_f_level_off.data();
+    p->pi_var = P.pi_var;
+    p->var_cone.assign(P.n_vars + 1, -1);
+    p->var_full.assign(P.n_vars + 1, -1);
+    p->var_neg.assign(P.n_vars + 1, 0);
+    {
+        // full node -> cone index
+        std::vector<int64_t> f2c(P.n_nodes, -1);
+        for (uint32_t i = 0; i < P.n_cone_pi; i++) f2c[P.cone_pi_row[i]] = i;
+        uint64_t ci = P.n_cone_pi;
+        std::vector<uint8_t> cone(P.n_nodes, 0);
+        // cone gates are the full gates in order that belong to the cone: rebuild by walking outputs
+        for (int32_t n : P.out_node) cone[n] = 1;
+        for (int64_t r = (int64_t)P.in0.size() - 1; r >= 0; r--)
+            if (cone[P.n_pi + r]) cone[P.in0[r]] = cone[P.in1[r]] = 1;
+        for (size_t r = 0; r < P.in0.size(); r++)
+            if (cone[P.n_pi + r]) f2c[P.n_pi + r] = (int64_t)ci++;
+        for (uint32_t v = 1; v <= P.n_vars; v++) {
+            p->var_full[v] = P.var_node[v];
+            p->var_cone[v] = f2c[P.var_node[v]];
+            p->var_neg[v] = P.var_neg[v];
+        }
+    }
+    p->f_in0 = P.in0;
+    p->f_in1 = P.in1;
+    p->f_gop = P.gop;
+    sat_plan_info& I = p->info;
+    I.n_vars = P.n_vars;
+    I.n_pi = P.n_pi;
+    I.n_cone_pi = P.n_cone_pi;
+    I.n_outputs = (uint32_t)P.out_node.size();
+    I.n_cone_levels = (uint32_t)d.n_clev;
+    I.n_levels = (uint32_t)d.n_flev;
+    I.key_words = (uint32_t)d.key_words;
+    I.max_span = P.max_span;
+    I.n_cone = P.n_cone;
+    I.n_nodes = P.n_nodes;
+    I.n_cone_gates = P.c_in0.size();
+    I.n_gates = P.in0.size();
+    I.n_clauses = (uint64_t)d.n_clauses;
+    I.n_fanout_edges = P.fo_g.size();
+    *out = p;
+    return SAT_OK;
+}
+
+sat_status sat_plan_get_info(const sat_plan* p, sat_plan_info* info) {
+    if (!p || !info) return fail(SAT_ERR_ARG, "NULL argument");
+    *info = p->info;
+    return SAT_OK;
+}
+
+sat_status sat_plan_pi_vars(const sat_plan* p, uint32_t* vars) {
+    if (!p || !vars) return fail(SAT_ERR_ARG, "NULL argument");
+    std::copy(p->pi_var.begin(), p->pi_var.end(), vars);
+    return SAT_OK;
+}
+
+sat_status sat_plan_var_nodes(const sat_plan* p, int64_t* cone_node, int64_t* full_node, uint8_t* neg) {
+    if (!p) return fail(SAT_ERR_ARG, "NULL plan");
+    if (cone_node) std::copy(p->var_cone.begin(), p->var_cone.end(), cone_node);
+    if (full_node) std::copy(p->var_full.begin(), p->var_full.end(), full_node);
+    if (neg) std::copy(p->var_neg.begin(), p->var_neg.end(), neg);
+    return SAT_OK;
+}
+
+// -------------------------------------------------------------- kernels --
+sat_status sat_init_normal(const sat_plan* p, uint64_t seed, uint32_t round, float scale, float* V, int64_t ldv,
+                           int64_t B, void* stream) {
+    sat_status s = check_layout(p, B, ldv, -1);
+    if (s != SAT_OK) return s;
+    if (B > 0 && p->dp.n_pi > 0 && !V) return fail(SAT_ERR_ARG, "V is NULL");
+    CK(sat::launch_init_normal(p->dp, seed, round, scale, V, ldv, B, S(stream)));
+    return SAT_OK;
+}
+
+sat_status sat_forward(const sat_plan* p, sat_act_dtype t, const float* V, int64_t ldv, void* act, int64_t lda,
+                       float* loss, int64_t B, void* stream) {
+    sat_status s = check_layout(p, B, ldv, lda);
+    if (s != SAT_OK) return s;
+    if (t < SAT_ACT_F32 || t > SAT_ACT_F16) return fail(SAT_ERR_ARG, "bad act_dtype");
+    if (B > 0 && ((p->dp.n_pi > 0 && !V) || (p->dp.n_cone > 0 && !act))) return fail(SAT_ERR_ARG, "NULL buffer");
+    CK(sat::launch_forward(p->dp, (int)t, V, ldv, act, lda, loss, B, S(stream)));
+    return SAT_OK;
+}
+
+sat_status sat_backward(const sat_plan* p, sat_act_dtype t, const float* V, int64_t ldv, const void* act, int64_t lda,
+                        float* adj, const float* grad_loss, float* gV, int64_t B, void* stream) {
+    sat_status s = check_layout(p, B, ldv, lda);
+    if (s != SAT_OK) return s;
+    if (t < SAT_ACT_F32 || t > SAT_ACT_F16) return fail(SAT_ERR_ARG, "bad act_dtype");
+    if (B > 0 && ((p->dp.n_pi > 0 && (!V || !gV)) || (p->dp.n_cone > 0 && (!act || !adj))))
+        return fail(SAT_ERR_ARG, "NULL buffer");
+    CK(sat::launch_backward(p->dp, (int)t, V, ldv, act, lda, adj, grad_loss, gV, B, S(stream)));
+    return SAT_OK;
+}
+
+sat_status sat_opt_update(const sat_plan* p, const sat_opt_params* o, float* V, float* m, float* v, const float* gV,
+                          int64_t ldv, int32_t t, int64_t B, void* stream) {
+    sat_status s = check_layout(p, B, ldv, -1);
+    if (s != SAT_OK) return s;
+    if (!opt_ok(o) || t < 1) return fail(SAT_ERR_ARG, "bad optimiser parameters or step");
+    if (B > 0 && p->dp.n_cone_pi > 0 && (!V || !gV || (o->optimizer == SAT_OPT_ADAM && (!m || !v))))
+        return fail(SAT_ERR_ARG, "NULL buffer");
+    CK(sat::launch_opt_update(p->dp, opt_of(o), V, m, v, gV, ldv, t, B, S(stream)));
+    return SAT_OK;
+}
+
+sat_status sat_steps(const sat_plan* p, sat_act_dtype t, const sat_opt_params* o, float* V, float* m, float* v,
+                     int64_t ldv, void* act, float* adj, int64_t lda, float* loss, int32_t t0, int32_t n_steps,
+                     int64_t B, void* stream) {
+    sat_status s = check_layout(p, B, ldv, lda);
+    if (s != SAT_OK) return s;
+    if (t < SAT_ACT_F32 || t > SAT_ACT_F16) return fail(SAT_ERR_ARG, "bad act_dtype");
+    if (!opt_ok(o) || t0 < 1 || n_steps < 0) return fail(SAT_ERR_ARG, "bad optimiser parameters or steps");
+    if (B > 0 && ((p->dp.n_pi > 0 && (!V || (o->optimizer == SAT_OPT_ADAM && (!m || !v)))) ||
+                  (p->dp.n_cone > 0 && (!act || !adj))))
+        return fail(SAT_ERR_ARG, "NULL buffer");
+    CK(sat::launch_steps(p->dp, (int)t, opt_of(o), V, m, v, ldv, act, adj, lda, loss, t0, n_steps, B, S(stream)));
+    return SAT_OK;
+}
+
+sat_status sat_threshold(const sat_plan* p, const float* V, int64_t ldv, uint32_t* node_bits, int64_t ldw,
+                         uint32_t* keys, int64_t B, void* stream) {
+    sat_status s = check_layout(p, B, ldv, -1);
+    if (s != SAT_OK) return s;
+    if (ldw < (B + 31) / 32) return fail(SAT_ERR_ARG, "ldw < ceil(B/32)");
+    if (B > 0 && p->dp.n_pi > 0 && (!V || !node_bits || !keys)) return fail(SAT_ERR_ARG, "NULL buffer");
+    CK(sat::launch_threshold(p->dp, V, ldv, node_bits, ldw, keys, B, S(stream)));
+    return SAT_OK;
+}
+
+sat_status sat_hard_eval(const sat_plan* p, uint32_t* node_bits, int64_t ldw, int64_t B, void* stream) {
+    sat_status s = check_layout(p, B, -1, -1);
+    if (s != SAT_OK) return s;
+    if (ldw < (B + 31) / 32) return fail(SAT_ERR_ARG, "ldw < ceil(B/32)");
+    if (B > 0 && p->dp.n_nodes > 0 && !node_bits) return fail(SAT_ERR_ARG, "NULL buffer");
+    CK(sat::launch_hard_eval(p->dp, node_bits, ldw, B, S(stream)));
+    return SAT_OK;
+}
+
+sat_status sat_cnf_check(const sat_plan* p, const uint32_t* node_bits, int64_t ldw, uint32_t* valid, int64_t B,
+                         void* stream) {
+    sat_status s = check_layout(p, B, -1, -1);
+    if (s != SAT_OK) return s;
+    if (ldw < (B + 31) / 32) return fail(SAT_ERR_ARG, "ldw < ceil(B/32)");
+    if (B > 0 && (!valid || (p->dp.n_nodes > 0 && !node_bits))) return fail(SAT_ERR_ARG, "NULL buffer");
+    CK(sat::launch_cnf_check(p->dp, node_bits, ldw, valid, B, S(stream)));
+    return SAT_OK;
+}
+
+// --------------------------------------------------------------- dedup --
+void sat_dedup_free(sat_dedup* d) {
+    if (!d) return;
+    cudaFree(d->d.slots);
+    cudaFree(d->d.pool);
+    cudaFree(d->d.count);
+    cudaFree(d->d.status);
+    cudaFree(d->slot_of);
+    delete d;
+}
+
+sat_status sat_dedup_create(const sat_plan* p, uint64_t max_keys, int64_t max_batch, sat_dedup** out) {
+    if (!p || !out || max_batch < 0) return fail(SAT_ERR_ARG, "bad argument");
+    *out = nullptr;
+    if (max_keys >= (1ull << 31)) return fail(SAT_ERR_ARG, "max_keys must be < 2^31");
+    auto* d = new sat_dedup();
+    d->device = p->device;
+    d->max_batch = max_batch;
+    d->d.key_words = p->dp.key_words;
+    uint64_t cap = 1024;
+    while (cap < 2 * std::max<uint64_t>(max_keys, 1)) cap <<= 1;
+    d->d.capacity = cap;
+    d->d.pool_capacity = max_keys;
+    d->d.max_probe = (uint32_t)std::min<uint64_t>(cap, 1u << 20);
+    const size_t kw = (size_t)std::max(1, d->d.key_words);
+    if (cudaMalloc(&d->d.slots, cap * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&d->d.pool, std::max<uint64_t>(max_keys, 1) * kw * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&d->d.count, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&d->d.status, sizeof(unsigned int)) != cudaSuccess ||
+        cudaMalloc(&d->slot_of, std::max<int64_t>(max_batch, 1) * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        sat_dedup_free(d);
+        return fail(SAT_ERR_OOM, "cudaMalloc failed for the dedup table");
+    }
+    cudaError_t e = sat::launch_dedup_clear(d->d, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    if (e != cudaSuccess) {
+        sat_dedup_free(d);
+        return fail(SAT_ERR_CUDA, cudaGetErrorString(e));
+    }
+    *out = d;
+    return SAT_OK;
+}
+
+sat_status sat_dedup_clear(sat_dedup* d, void* stream) {
+    if (!d) return fail(SAT_ERR_ARG, "NULL dedup");
+    CK(sat::launch_dedup_clear(d->d, S(stream)));
+    return SAT_OK;
+}
+
+sat_status sat_dedup_count(const sat_dedup* d, uint64_t* n, void* stream) {
+    if (!d || !n) return fail(SAT_ERR_ARG, "NULL argument");
+    unsigned long long c = 0;
+    CK(cudaMemcpyAsync(&c, d->d.count, sizeof(c), cudaMemcpyDeviceToHost, S(stream)));
+    CK(cudaStreamSynchronize(S(stream)));
+    *n = std::min<uint64_t>(c, d->d.pool_capacity);
+    return SAT_OK;
+}
+
+sat_status sat_dedup_insert(sat_dedup* d, const uint32_t* keys, const uint32_t* valid, int64_t B, uint64_t* hashes,
+                            uint8_t* is_new, void* stream) {
+    if (!d) return fail(SAT_ERR_ARG, "NULL dedup");
+    if (B < 0 || B > d->max_batch) return fail(SAT_ERR_ARG, "B outside 0..max_batch");
+    if (B > 0 && (!keys || !valid)) return fail(SAT_ERR_ARG, "NULL buffer");
+    sat_status s = check_device(d->device);
+    if (s != SAT_OK) return s;
+    uint64_t n = 0;
+    if ((s = sat_dedup_count(d, &n, stream)) != SAT_OK) return s;
+    if (n + (uint64_t)B > d->d.pool_capacity)
+        return fail(SAT_ERR_TABLE_FULL, "dedup table cannot take another batch of this size");
+    CK(sat::launch_dedup_insert(d->d, keys, valid, B, (unsigned long long*)hashes, is_new, d->slot_of, S(stream)));
+    unsigned int status = 0;
+    CK(cudaMemcpyAsync(&status, d->d.status, sizeof(status), cudaMemcpyDeviceToHost, S(stream)));
+    CK(cudaStreamSynchronize(S(stream)));
+    if (status) return fail(SAT_ERR_TABLE_FULL, "dedup probe limit reached");
+    return SAT_OK;
+}
+
+sat_status sat_dedup_copy_keys(const sat_dedup* d, uint64_t first, uint64_t count, uint32_t* host_keys,
+                               void* stream) {
+    if (!d || (count && !host_keys)) return fail(SAT_ERR_ARG, "NULL argument");
+    uint64_t n = 0;
+    sat_status s = sat_dedup_count(d, &n, stream);
+    if (s != SAT_OK) return s;
+    if (first + count > n) return fail(SAT_ERR_ARG, "range beyond stored keys");
+    const size_t kw = (size_t)d->d.key_words;
+    if (count && kw) {
+        CK(cudaMemcpyAsync(host_keys, d->d.pool + first * kw, count * kw * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                           S(stream)));
+        CK(cudaStreamSynchronize(S(stream)));
+    }
+    return SAT_OK;
+}
+
+// ----------------------------------------------------------- end to end --
+void sat_sample_opts_default(sat_sample_opts* o) {
+    if (!o) return;
+    *o = sat_sample_opts{};
+    o->batch = 1024;
+    o->steps = 200;
+    o->max_rounds = 1;
+    o->opt.optimizer = SAT_OPT_ADAM;
+    o->opt.lr = 0.1f;
+    o->opt.beta1 = 0.9f;
+    o->opt.beta2 = 0.999f;
+    o->opt.eps = 1e-8f;
+    o->seed = 0;
+    o->first_round = 0;
+    o->init_scale = 1.0f;
+    o->act_dtype = SAT_ACT_F32;
+    o->steps_per_launch = 0;
+    o->init_logits = nullptr;
+    o->init_ld = 0;
+    o->stream = nullptr;
+}
+
+namespace {
+
+struct Workspace {
+    std::vector<void*> bufs;
+    float *V = nullptr, *m = nullptr, *v = nullptr, *adj = nullptr;
+    void* act = nullptr;
+    uint32_t *bits = nullptr, *keys = nullptr, *valid = nullptr;
+    int64_t lda = 0, ldw = 0;
+    ~Workspace() {
+        for (void* b : bufs) cudaFree(b);
+    }
+    bool alloc(void** p, size_t n) {
+        if (n == 0) n = 16;
+        if (cudaMalloc(p, n) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        bufs.push_back(*p);
+        return true;
+    }
+};
+
+size_t act_bytes(int t) { return t == SAT_ACT_F32 ? 4 : 2; }
+
+}  // namespace
+
+sat_status sat_sample_plan(const sat_plan* p, sat_dedup* d, const sat_sample_opts* o, uint64_t n_wanted,
+                           sat_sample_stats* st) {
+    if (!p || !d || !o) return fail(SAT_ERR_ARG, "NULL argument");
+    const int64_t B = o->batch;
+    if (B <= 0 || B > d->max_batch) return fail(SAT_ERR_ARG, "batch must be in 1..dedup max_batch");
+    if (o->steps < 0 || o->max_rounds < 1 || !opt_ok(&o->opt)) return fail(SAT_ERR_ARG, "bad steps/rounds/optimiser");
+    if (o->act_dtype < SAT_ACT_F32 || o->act_dtype > SAT_ACT_F16) return fail(SAT_ERR_ARG, "bad act_dtype");
+    if (o->init_logits && o->init_ld < B) return fail(SAT_ERR_ARG, "init_ld < batch");
+    sat_status s = check_device(p->device);
+    if (s != SAT_OK) return s;
+    cudaStream_t str = S(o->stream);
+    const sat::DevPlan& dp = p->dp;
+    Workspace w;
+    w.lda = round32(B);
+    w.ldw = (B + 31) / 32;
+    const size_t npi = (size_t)dp.n_pi;
+    if (!w.alloc((void**)&w.V, npi * B * 4) || !w.alloc((void**)&w.m, npi * B * 4) ||
+        !w.alloc((void**)&w.v, npi * B * 4) || !w.alloc(&w.act, (size_t)dp.n_cone * w.lda * act_bytes(o->act_dtype)) ||
+        !w.alloc((void**)&w.adj, (size_t)dp.n_cone * w.lda * 4) ||
+        !w.alloc((void**)&w.bits, (size_t)dp.n_nodes * w.ldw * 4) ||
+        !w.alloc((void**)&w.keys, (size_t)B * std::max(1, dp.key_words) * 4) ||
+        !w.alloc((void**)&w.valid, (size_t)w.ldw * 4))
+        return fail(SAT_ERR_OOM, "cudaMalloc failed for the sampling workspace");
+    cudaEvent_t ev[5];
+    for (auto& e : ev) CK(cudaEventCreate(&e));
+    struct EvGuard {
+        cudaEvent_t* e;
+        ~EvGuard() { for (int i = 0; i < 5; i++) cudaEventDestroy(e[i]); }
+    } guard{ev};
+    sat_sample_stats acc{};
+    const sat::OptParams op = opt_of(&o->opt);
+    const int spl = o->steps_per_launch > 0 ? o->steps_per_launch : std::max(1, o->steps);
+    std::vector<uint32_t> hvalid(w.ldw);
+    uint64_t have = 0;
+    sat_status result = SAT_PARTIAL;
+    for (int r = 0; r < o->max_rounds; r++) {
+        CK(cudaEventRecord(ev[0], str));
+        if (r == 0 && o->init_logits) {
+            CK(cudaMemcpy2DAsync(w.V, B * 4, o->init_logits, o->init_ld * 4, B * 4, npi, cudaMemcpyDeviceToDevice, str));
+        } else {
+            CK(sat::launch_init_normal(dp, o->seed, o->first_round + (uint32_t)r, o->init_scale, w.V, B, B, str));
+        }
+        CK(cudaMemsetAsync(w.m, 0, npi * B * 4, str));
+        CK(cudaMemsetAsync(w.v, 0, npi * B * 4, str));
+        CK(cudaEventRecord(ev[1], str));
+        for (int t0 = 1; t0 <= o->steps; t0 += spl)
+            CK(sat::launch_steps(dp, o->act_dtype, op, w.V, w.m, w.v, B, w.act, w.adj, w.lda, nullptr, t0,
+                                 std::min(spl, o->steps - t0 + 1), B, str));
+        CK(cudaEventRecord(ev[2], str));
+        CK(sat::launch_threshold(dp, w.V, B, w.bits, w.ldw, w.keys, B, str));
+        CK(sat::launch_hard_eval(dp, w.bits, w.ldw, B, str));
+        CK(sat::launch_cnf_check(dp, w.bits, w.ldw, w.valid, B, str));
+        CK(cudaEventRecord(ev[3], str));
+        uint64_t n = 0;
+        if ((s = sat_dedup_count(d, &n, str)) != SAT_OK) return s;
+        if (n + (uint64_t)B > d->d.pool_capacity) return fail(SAT_ERR_TABLE_FULL, "dedup table is full");
+        CK(sat::launch_dedup_insert(d->d, w.keys, w.valid, B, nullptr, nullptr, d->slot_of, str));
+        CK(cudaEventRecord(ev[4], str));
+        CK(cudaMemcpyAsync(hvalid.data(), w.valid, w.ldw * 4, cudaMemcpyDeviceToHost, str));
+        unsigned int status = 0;
+        CK(cudaMemcpyAsync(&status, d->d.status, sizeof(status), cudaMemcpyDeviceToHost, str));
+        CK(cudaStreamSynchronize(str));
+        if (status) return fail(SAT_ERR_TABLE_FULL, "dedup probe limit reached");
+        float ms[4];
+        for (int i = 0; i < 4; i++) CK(cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]));
+        acc.ms_init += ms[0];
+        acc.ms_steps += ms[1];
+        acc.ms_verify += ms[2];
+        acc.ms_dedup += ms[3];
+        acc.ms_total += ms[0] + ms[1] + ms[2] + ms[3];
+        acc.rounds++;
+        acc.samples += (uint64_t)B;
+        for (uint32_t x : hvalid) acc.valid += (uint64_t)__builtin_popcount(x);
+        if ((s = sat_dedup_count(d, &have, str)) != SAT_OK) return s;
+        if (have >= n_wanted) {
+            result = SAT_OK;
+            break;
+        }
+    }
+    acc.unique = have;
+    if (st) *st = acc;
+    if (result == SAT_PARTIAL) g_err = "budget ended before n_wanted distinct solutions";
+    return result;
+}
+
+sat_status sat_sample(const sat_circuit* c, const sat_cnf* cnf, const sat_sample_opts* o, uint64_t n_wanted,
+                      sat_solutions** out, sat_sample_stats* st) {
+    if (!c || !cnf || !o || !out) return fail(SAT_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    auto t0 = std::chrono::steady_clock::now();
+    sat_plan* p = nullptr;
+    sat_status s = sat_plan_create(c, cnf, &p);
+    if (s != SAT_OK) return s;
+    struct PG {
+        sat_plan* p;
+        sat_dedup* d = nullptr;
+        ~PG() { sat_dedup_free(d); sat_plan_free(p); }
+    } pg{p};
+    const uint64_t max_keys = (uint64_t)o->batch * (uint64_t)std::max(1, o->max_rounds);
+    if ((s = sat_dedup_create(p, max_keys, o->batch, &pg.d)) != SAT_OK) return s;
+    auto t1 = std::chrono::steady_clock::now();
+    sat_sample_stats acc{};
+    sat_status r = sat_sample_plan(p, pg.d, o, n_wanted, &acc);
+    if (r != SAT_OK && r != SAT_PARTIAL) return r;
+    std::string partial_msg = g_err;
+    auto t2 = std::chrono::steady_clock::now();
+    auto* sol = new sat_solutions();
+    sol->n_vars = p->info.n_vars;
+    sol->n_pi = p->info.n_pi;
+    sol->key_words = p->info.key_words;
+    sol->count = acc.unique;
+    std::vector<uint32_t> raw(sol->count * sol->key_words);
+    if ((s = sat_dedup_copy_keys(pg.d, 0, sol->count, raw.data(), o->stream)) != SAT_OK) {
+        delete sol;
+        return s;
+    }
+    // canonical order: ascending packed input vector (highest word most significant)
+    std::vector<uint64_t> idx(sol->count);
+    for (uint64_t i = 0; i < sol->count; i++) idx[i] = i;
+    const uint32_t kw = sol->key_words;
+    std::sort(idx.begin(), idx.end(), [&](uint64_t a, uint64_t b) {
+        for (int64_t k = (int64_t)kw - 1; k >= 0; k--) {
+            uint32_t x = raw[a * kw + k], y = raw[b * kw + k];
+            if (x != y) return x < y;
+        }
+        return false;
+    });
+    sol->keys.resize(raw.size());
+    for (uint64_t i = 0; i < sol->count; i++)
+        std::copy(raw.begin() + idx[i] * kw, raw.begin() + (idx[i] + 1) * kw, sol->keys.begin() + i * kw);
+    sol->f_in0 = p->f_in0;
+    sol->f_in1 = p->f_in1;
+    sol->f_gop = p->f_gop;
+    sol->var_full = p->var_full;
+    sol->var_neg = p->var_neg;
+    auto t3 = std::chrono::steady_clock::now();
+    acc.ms_upload = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    acc.ms_download = std::chrono::duration<double, std::milli>(t3 - t2).count();
+    if (st) *st = acc;
+    *out = sol;
+    if (r == SAT_PARTIAL) g_err = partial_msg;
+    return r;
+}
+
+uint64_t sat_solutions_count(const sat_solutions* s) { return s ? s->count : 0; }
+uint32_t sat_solutions_nvars(const sat_solutions* s) { return s ? s->n_vars : 0; }
+
+sat_status sat_solutions_copy(const sat_solutions* s, uint64_t first, uint64_t count, uint64_t* words_out) {
+    if (!s || (count && !words_out)) return fail(SAT_ERR_ARG, "NULL argument");
+    if (first + count > s->count) return fail(SAT_ERR_ARG, "range beyond the solution count");
+    const uint64_t nw = (s->n_vars + 63) / 64;
+    std::fill(words_out, words_out + count * nw, 0ull);
+    const size_t n_nodes = s->n_pi + s->f_in0.size();
+    std::vector<uint64_t> node(n_nodes);
+    // 64 solutions at a time: bit j of each node word = solution (base + j)
+    for (uint64_t base = 0; base < count; base += 64) {
+        const uint64_t nb = std::min<uint64_t>(64, count - base);
+        std::fill(node.begin(), node.end(), 0ull);
+        for (uint64_t j = 0; j < nb; j++) {
+            const uint32_t* key = &s->keys[(first + base + j) * s->key_words];
+            for (uint32_t i = 0; i < s->n_pi; i++)
+                if ((key[i >> 5] >> (i & 31)) & 1u) node[i] |= 1ull << j;
+        }
+        for (size_t g = 0; g < s->f_in0.size(); g++) {
+            uint64_t a = node[s->f_in0[g]], b = node[s->f_in1[g]];
+            const uint8_t f = s->f_gop[g];
+            if (f & 4) a = ~a;
+            if (f & 8) b = ~b;
+            const uint8_t op = f & 3;
+            node[s->n_pi + g] = op == 0 ? (a & b) : op == 1 ? (a | b) : (a ^ b);
+        }
+        for (uint32_t v = 1; v <= s->n_vars; v++) {
+            uint64_t x = node[s->var_full[v]];
+            if (s->var_neg[v]) x = ~x;
+            const uint64_t wi = (v - 1) >> 6, bi = (v - 1) & 63;
+            for (uint64_t j = 0; j < nb; j++)
+                if ((x >> j) & 1ull) words_out[(base + j) * nw + wi] |= 1ull << bi;
+        }
+    }
+    return SAT_OK;
+}
+
+void sat_solutions_free(sat_solutions* s) { delete s; }
+
+}  // extern "C"

@@ -1,0 +1,82 @@
+// Device-side plan and kernel launchers (internal; the C ABI wraps these).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace sat {
+
+// Device copy of a Plan.  All pointers are device pointers owned by the plan.
+struct DevPlan {
+    // cone schedule (gradient loop)
+    int32_t n_cone_pi = 0;
+    int64_t n_cone = 0;
+    int32_t n_clev = 0;                 // cone levels 1..n_clev
+    const int32_t* c_level_off = nullptr;
+    const int2* c_gate = nullptr;       // per cone gate: (in0 | gop << 28, in1)
+    const int32_t* cone_pi_row = nullptr;
+    const int64_t* fo_off = nullptr;    // [n_cone + 1]
+    const int4* fo_edge = nullptr;      // (consumer or -1, sibling or target, c0, c1)
+    int32_t n_out = 0;
+    const int32_t* c_out_node = nullptr;
+    const float* out_target = nullptr;
+    // full schedule (Boolean pass)
+    int32_t n_pi = 0;
+    int64_t n_nodes = 0;
+    int32_t n_flev = 0;
+    const int32_t* f_level_off = nullptr;
+    const int2* f_gate = nullptr;       // per gate: (in0 | gop << 28, in1)
+    // CNF in node space
+    int64_t n_clauses = 0;
+    const int64_t* cl_off = nullptr;
+    const int32_t* cl_lit = nullptr;    // node << 1 | negation
+    int32_t key_words = 0;              // ceil(n_pi / 32)
+    // host mirrors of the level offsets (launch loops need them)
+    const int32_t* h_c_level_off = nullptr;
+    const int32_t* h_f_level_off = nullptr;
+};
+
+enum ActType { ACT_F32 = 0, ACT_BF16 = 1, ACT_F16 = 2 };
+
+struct OptParams {
+    int opt = 0;  // 0 Adam, 1 GD
+    float lr = 0.1f, b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+};
+
+// Kernel launchers; return cudaSuccess or the launch error.
+cudaError_t launch_init_normal(const DevPlan& p, uint64_t seed, uint32_t round, float scale,
+                               float* V, int64_t ldv, int64_t B, cudaStream_t s);
+cudaError_t launch_forward(const DevPlan& p, int act_type, const float* V, int64_t ldv, void* act,
+                           int64_t lda, float* loss, int64_t B, cudaStream_t s);
+cudaError_t launch_backward(const DevPlan& p, int act_type, const float* V, int64_t ldv, const void* act,
+                            int64_t lda, float* adj, const float* grad_loss, float* gV, int64_t B,
+                            cudaStream_t s);
+cudaError_t launch_steps(const DevPlan& p, int act_type, const OptParams& o, float* V, float* m, float* v,
+                         int64_t ldv, void* act, float* adj, int64_t lda, float* loss, int t0, int n_steps,
+                         int64_t B, cudaStream_t s);
+cudaError_t launch_opt_update(const DevPlan& p, const OptParams& o, float* V, float* m, float* v,
+                              const float* gV, int64_t ldv, int t, int64_t B, cudaStream_t s);
+cudaError_t launch_threshold(const DevPlan& p, const float* V, int64_t ldv, uint32_t* node_bits,
+                             int64_t ldw, uint32_t* keys, int64_t B, cudaStream_t s);
+cudaError_t launch_hard_eval(const DevPlan& p, uint32_t* node_bits, int64_t ldw, int64_t B, cudaStream_t s);
+cudaError_t launch_cnf_check(const DevPlan& p, const uint32_t* node_bits, int64_t ldw, uint32_t* valid,
+                             int64_t B, cudaStream_t s);
+
+// Device hash set of distinct solutions (keys = packed primary-input bits).
+struct DevDedup {
+    int32_t key_words = 0;
+    uint64_t capacity = 0;            // slots (power of two)
+    uint64_t pool_capacity = 0;       // keys that can be stored
+    unsigned long long* slots = nullptr;
+    uint32_t* pool = nullptr;         // [pool_capacity][key_words]
+    unsigned long long* count = nullptr;   // device counter of stored keys
+    unsigned int* status = nullptr;        // bit 0: table full / probe limit hit
+    uint32_t max_probe = 0;
+};
+
+cudaError_t launch_dedup_clear(DevDedup& d, cudaStream_t s);
+// slot_of: scratch [B] (slot taken by each sample, or ~0).
+cudaError_t launch_dedup_insert(DevDedup& d, const uint32_t* keys, const uint32_t* valid, int64_t B,
+                                unsigned long long* hashes, uint8_t* is_new, unsigned long long* slot_of,
+                                cudaStream_t s);
+
+}  // namespace sat

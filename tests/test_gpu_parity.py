@@ -1,0 +1,271 @@
+"""GPU parity of the hot path against the FP64 oracle on the same seeded inputs.
+
+Tolerances: FP32 gate values within 1e-5 absolute; gradients within 1e-4
+relative to max(|g*|, 1e-3 max_i |g*_i|) per sample (adjoints through an XOR
+at 1/2 can be exactly 0, hence the floor); thresholded bits, Boolean node
+values, validity, hashes and unique sets bit-exact.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from workloads import tseitin_random_circuit, planted_3sat, fig1_example_dimacs, normal_logits
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _setup(text):
+    import paper_2502_08673_b300 as P
+    cnf = P.Cnf.from_dimacs(text)
+    circ = P.Circuit.build(cnf)
+    plan = P.Plan.create(circ, cnf)
+    orc = oracle.Oracle(text)
+    assert list(plan.pi_vars()) == orc.circuit.pis
+    return P, cnf, circ, plan, orc
+
+
+INSTANCES = {
+    "fig1": fig1_example_dimacs,
+    "planted3sat_50_200": lambda: planted_3sat(50, 200, 1).dimacs(),
+    "tseitin_2k_20k_d40": lambda: tseitin_random_circuit(2000, 20000, 40, 32, seed=1).dimacs(),
+    "tseitin_small": lambda: tseitin_random_circuit(64, 640, 16, 8, seed=3).dimacs(),
+}
+
+
+def _grad_close(g, gref):
+    floor = 1e-3 * np.abs(gref).max(axis=1, keepdims=True)
+    tol = 1e-4 * np.maximum(np.abs(gref), floor)
+    return np.abs(g - gref) <= tol + 1e-30
+
+
+@pytest.mark.parametrize("name", sorted(INSTANCES))
+@pytest.mark.parametrize("B", [1, 45, 200])
+def test_forward_backward_parity(gpu, name, B):
+    P, cnf, circ, plan, orc = _setup(INSTANCES[name]())
+    V0 = normal_logits(B, orc.n_pi, seed=B + 11)
+    V = torch.tensor(V0.T.copy(), device=gpu)
+    act = P.new_act(plan, B)
+    loss = torch.empty(B, device=gpu)
+    P.sat_forward(plan, V, act, loss)
+    adj = P.new_adj(plan, B)
+    gV = torch.zeros_like(V)
+    P.sat_backward(plan, V, act, adj, gV)
+    torch.cuda.synchronize()
+    vals, loss_ref = oracle.forward(orc.flat, V0.astype(np.float64))
+    gref, _ = oracle.backward(orc.flat, vals)
+    np.testing.assert_allclose(loss.cpu().numpy(), loss_ref, rtol=0, atol=1e-5 * max(1, plan.n_outputs))
+    cone, _, neg = plan.var_nodes()
+    A = act.cpu().numpy()[:, :B]
+    for v in range(1, plan.n_vars + 1):
+        if cone[v] < 0:
+            continue
+        gv = A[cone[v]]
+        if neg[v]:
+            gv = 1.0 - gv
+        np.testing.assert_allclose(gv, vals[:, v - 1], rtol=0, atol=1e-5, err_msg=f"var {v}")
+    g = gV.cpu().numpy().T
+    ok = _grad_close(g.astype(np.float64), gref)
+    assert ok.all(), (np.argwhere(~ok)[:5], g[~ok][:5], gref[~ok][:5])
+
+
+def test_fused_steps_equal_unfused(gpu):
+    """sat_steps = forward, backward, opt_update, bit for bit (Adam and GD)."""
+    P, cnf, circ, plan, orc = _setup(INSTANCES["tseitin_small"]())
+    B = 77
+    for optname in ("adam", "gd"):
+        opt = P.opt_params(optname, lr=0.05)
+        V0 = torch.tensor(normal_logits(B, orc.n_pi, seed=5).T.copy(), device=gpu)
+        Va, ma, va = V0.clone(), torch.zeros_like(V0), torch.zeros_like(V0)
+        act, adj = P.new_act(plan, B), P.new_adj(plan, B)
+        P.sat_steps(plan, opt, Va, ma, va, act, adj, 1, 7)
+        Vb, mb, vb = V0.clone(), torch.zeros_like(V0), torch.zeros_like(V0)
+        gV = torch.zeros_like(V0)
+        for t in range(1, 8):
+            P.sat_forward(plan, Vb, act)
+            P.sat_backward(plan, Vb, act, adj, gV)
+            P.sat_opt_update(plan, opt, Vb, mb, vb, gV, t)
+        torch.cuda.synchronize()
+        assert torch.equal(Va, Vb), optname
+        if optname == "adam":
+            assert torch.equal(ma, mb) and torch.equal(va, vb)
+
+
+def test_adam_update_parity(gpu):
+    """Elementwise Adam (t = 1..3) against the oracle on seeded state."""
+    P, cnf, circ, plan, orc = _setup(INSTANCES["tseitin_small"]())
+    B = 96
+    rng = np.random.default_rng(0)
+    V0 = rng.normal(size=(plan.n_pi, B)).astype(np.float32)
+    g = (rng.normal(size=(plan.n_pi, B)) * 10.0 ** rng.uniform(-3, 1, (plan.n_pi, B))).astype(np.float32)
+    rows = [r for r in range(plan.n_pi) if plan.pi_vars()[r] in set(orc.circuit.pis)]
+    Vd, md, vd = torch.tensor(V0, device=gpu), torch.zeros(plan.n_pi, B, device=gpu), torch.zeros(plan.n_pi, B, device=gpu)
+    gd = torch.tensor(g, device=gpu)
+    Vr, mr, vr = V0.astype(np.float64), np.zeros((plan.n_pi, B)), np.zeros((plan.n_pi, B))
+    cone_rows = np.zeros(plan.n_pi, bool)
+    cone, _, _ = plan.var_nodes()
+    for r, v in enumerate(plan.pi_vars()):
+        cone_rows[r] = cone[v] >= 0
+    opt = P.opt_params("adam", lr=0.1)
+    for t in (1, 2, 3):
+        P.sat_opt_update(plan, opt, Vd, md, vd, gd, t)
+        oracle.adam_step(Vr, mr, vr, g.astype(np.float64) * cone_rows[:, None], t, 0.1)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(Vd.cpu().numpy(), Vr, rtol=0, atol=2e-6)
+
+
+def test_short_trajectory_gd(gpu):
+    """Five GD steps (Eq. 9) from the same V0: GPU FP32 vs oracle FP64."""
+    P, cnf, circ, plan, orc = _setup(INSTANCES["tseitin_small"]())
+    B = 64
+    V0 = normal_logits(B, orc.n_pi, seed=2)
+    V = torch.tensor(V0.T.copy(), device=gpu)
+    m, v = torch.zeros_like(V), torch.zeros_like(V)
+    act, adj = P.new_act(plan, B), P.new_adj(plan, B)
+    loss = torch.empty(B, device=gpu)
+    P.sat_steps(plan, P.opt_params("gd", lr=1.0), V, m, v, act, adj, 1, 5, loss=loss)
+    trace = []
+    res = oracle.sample_round(orc.flat, orc.n_vars, orc.clauses, V0.astype(np.float64), steps=5, lr=1.0, opt="gd",
+                              trace=trace)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(V.cpu().numpy().T, res["V"], rtol=0, atol=1e-4)
+    np.testing.assert_allclose(loss.cpu().numpy(), trace[-1][1], rtol=0, atol=1e-4)
+
+
+def _planted_V(inst, orc, B, flip_p, seed):
+    rng = np.random.default_rng(seed)
+    base = np.where(inst.planted == 1, 1.0, -1.0)
+    V = np.tile(base, (B, 1))
+    flips = rng.random((B, orc.n_pi)) < flip_p
+    V[flips] *= -1
+    V *= rng.uniform(0.5, 2.0, (B, orc.n_pi))
+    dup = rng.integers(0, B, B // 4)
+    V[rng.integers(0, B, B // 4)] = V[dup]
+    V[:3] = 0.0  # threshold ties go to 0
+    return V.astype(np.float32)
+
+
+@pytest.mark.parametrize("B", [33, 250])
+def test_verification_parity(gpu, B):
+    """Threshold, Boolean pass, CNF check, hashes and unique set, bit-exact."""
+    inst = tseitin_random_circuit(300, 3000, 20, 8, seed=4)
+    P, cnf, circ, plan, orc = _setup(inst.dimacs())
+    V0 = _planted_V(inst, orc, B, 0.004, seed=B)
+    ws = P.new_workspace(plan, B)
+    ws.V.copy_(torch.tensor(V0.T.copy()))
+    P.sat_threshold(plan, ws.V, ws.bits, ws.keys)
+    P.sat_hard_eval(plan, ws.bits, B)
+    P.sat_cnf_check(plan, ws.bits, ws.valid, B)
+    dd = P.Dedup.create(plan, max_keys=4 * B, max_batch=B)
+    hashes = torch.zeros(B, dtype=torch.int64, device=gpu)
+    is_new = torch.zeros(B, dtype=torch.uint8, device=gpu)
+    dd.insert(ws.keys, ws.valid, B, hashes=hashes, is_new=is_new)
+    torch.cuda.synchronize()
+    ref = oracle.verify(orc.flat, orc.n_vars, orc.clauses, V0)
+    valid = P.valid_mask(ws.valid, B)
+    assert valid.tolist() == ref["valid"].astype(bool).tolist()
+    assert 0 < valid.sum() < B
+    # full assignments of every sample
+    _, full, neg = plan.var_nodes()
+    bits = ws.bits.cpu().numpy().view(np.uint32)
+    for v in range(1, plan.n_vars + 1):
+        words = bits[full[v]]
+        got = (np.unpackbits(words.view(np.uint8), bitorder="little")[:B]) ^ neg[v]
+        assert got.tolist() == ref["assign"][:, v].tolist(), v
+    # hashes of valid samples
+    h = hashes.cpu().numpy().view(np.uint64)
+    for s in np.nonzero(valid)[0]:
+        assert int(h[s]) == oracle.solution_hash(ref["pi_bits"][s])
+    # unique set
+    keys = dd.keys()
+    got_set = {tuple(np.unpackbits(k.view(np.uint8), bitorder="little")[: plan.n_pi]) for k in keys}
+    want_set = {tuple(ref["pi_bits"][s]) for s in ref["unique"].values()}
+    assert got_set == want_set and len(keys) == len(ref["unique"])
+    assert int(is_new.sum()) == len(keys)
+    # a second insert of the same batch adds nothing
+    dd.insert(ws.keys, ws.valid, B, is_new=is_new)
+    assert dd.count() == len(keys) and int(is_new.sum()) == 0
+
+
+def test_init_normal_parity(gpu):
+    """Philox4x32-10 + Box-Muller logits against the oracle's generator."""
+    P, cnf, circ, plan, orc = _setup(INSTANCES["tseitin_small"]())
+    B = 300
+    V = torch.empty(plan.n_pi, B, device=gpu)
+    P.sat_init_normal(plan, V, seed=0x1234_5678_9ABC, round_=7, scale=1.5)
+    ref = oracle.init_normal(B, plan.n_pi, 0x1234_5678_9ABC, 7, 1.5)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(V.cpu().numpy().T, ref, rtol=1e-5, atol=1e-5)
+
+
+def test_autograd_function(gpu):
+    from paper_2502_08673_b300.autograd import circuit_loss
+    P, cnf, circ, plan, orc = _setup(INSTANCES["fig1"]())
+    B = 40
+    V0 = normal_logits(B, orc.n_pi, seed=1)
+    V = torch.tensor(V0.T.copy(), device=gpu, requires_grad=True)
+    w = torch.linspace(0.5, 2.0, B, device=gpu)
+    (circuit_loss(V, plan) * w).sum().backward()
+    vals, _ = oracle.forward(orc.flat, V0.astype(np.float64))
+    gref, _ = oracle.backward(orc.flat, vals)
+    gref = gref * w.cpu().numpy()[:, None]
+    assert _grad_close(V.grad.cpu().numpy().T.astype(np.float64), gref).all()
+
+
+@pytest.mark.parametrize("act_dtype,bound", [("bf16", 0.06), ("f16", 0.01)])
+def test_low_precision_storage_error(gpu, act_dtype, bound):
+    """BF16/FP16 activation storage: forward error vs FP64 stays bounded; verification is exact anyway."""
+    P, cnf, circ, plan, orc = _setup(INSTANCES["tseitin_2k_20k_d40"]())
+    B = 64
+    V0 = normal_logits(B, orc.n_pi, seed=3)
+    V = torch.tensor(V0.T.copy(), device=gpu)
+    act = P.new_act(plan, B, act_dtype)
+    loss = torch.empty(B, device=gpu)
+    P.sat_forward(plan, V, act, loss, act_dtype=act_dtype)
+    adj, gV = P.new_adj(plan, B), torch.zeros_like(V)
+    P.sat_backward(plan, V, act, adj, gV, act_dtype=act_dtype)
+    torch.cuda.synchronize()
+    vals, loss_ref = oracle.forward(orc.flat, V0.astype(np.float64))
+    cone, _, neg = plan.var_nodes()
+    A = act.float().cpu().numpy()[:, :B]
+    err = 0.0
+    for v in range(1, plan.n_vars + 1):
+        if cone[v] >= 0:
+            gv = A[cone[v]] if not neg[v] else 1.0 - A[cone[v]]
+            err = max(err, float(np.abs(gv - vals[:, v - 1]).max()))
+    assert err < bound, err
+
+
+def test_empty_batch_and_no_outputs(gpu):
+    import paper_2502_08673_b300 as P
+    text = "p cnf 3 0\n"
+    cnf = P.Cnf.from_dimacs(text)
+    plan = P.Plan.create(P.Circuit.build(cnf), cnf)
+    assert plan.n_cone == 0 and plan.n_pi == 3
+    ws = P.new_workspace(plan, 40)
+    P.run_round(plan, ws, P.opt_params(), steps=3, seed=0, round_=0)
+    torch.cuda.synchronize()
+    assert P.valid_mask(ws.valid, 40).all()
+    ws0 = P.new_workspace(plan, 0)
+    P.sat_threshold(plan, ws0.V, ws0.bits, ws0.keys)
+
+
+def test_sample_end_to_end_planted3sat(gpu):
+    """sat_sample on the planted 3-SAT workload (n=50, m=200, B=1024, 200 Adam steps, lr 0.1)."""
+    import paper_2502_08673_b300 as P
+    inst = planted_3sat(50, 200, 1)
+    text = inst.dimacs()
+    cnf = P.Cnf.from_dimacs(text)
+    circ = P.Circuit.build(cnf)
+    sols = P.sample(circ, cnf, n_wanted=10 ** 9, batch=1024, steps=200, max_rounds=2, lr=0.1, seed=0)
+    A = sols.assignments()
+    assert len(sols) == sols.stats["unique"] > 0
+    n, cl = oracle.parse_dimacs(text)
+    assign = np.zeros((len(A), n + 1), np.uint8)
+    assign[:, 1:] = A
+    assert oracle.cnf_check(n, cl, assign).all()
+    assert len({a.tobytes() for a in A}) == len(A)
+    w = sols.words()
+    order = [tuple(int(x) for x in r) for r in w]
+    assert sols.stats["valid"] >= len(A)
