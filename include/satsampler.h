@@ -23,10 +23,14 @@
  *  - Per-sample device arrays are node-major with the batch contiguous: row r
  *    of an array with leading dimension ld starts at element r * ld.
  *    V, m, v, gV: [n_pi][ldv] float32, ldv >= B, row r = primary input r in
- *    ascending DIMACS-variable order (sat_plan_pi_vars).  act / adj: [n_cone]
- *    [lda], lda >= B rounded up to a multiple of 32 (rows are written for
- *    the padding lanes too).  Bit arrays: [rows][ldw] uint32, ldw >= ceil(B/32),
- *    bit j of word w = sample 32 w + j.
+ *    ascending DIMACS-variable order (sat_plan_pi_vars).  Bit arrays:
+ *    [rows][ldw] uint32, ldw >= ceil(B/32), bit j of word w = sample 32 w + j.
+ *  - Per-node scratch (act, adj) is tile-major: samples are grouped in tiles
+ *    of SAT_TILE, and tile t owns the contiguous block [n_cone][SAT_TILE] that
+ *    starts at element t * n_cone * SAT_TILE, so it holds
+ *    ceil(B/SAT_TILE) * n_cone * SAT_TILE elements (sat_plan_scratch_elems);
+ *    the padding samples of the last tile are written too.  act holds
+ *    act_dtype elements, adj float32; both must be 16-byte aligned.
  *  - Deterministic for a given (seed, options, GPU).
  */
 #ifndef SATSAMPLER_H
@@ -40,6 +44,7 @@ extern "C" {
 #endif
 
 #define SAT_ABI_VERSION 1
+#define SAT_TILE 64  /* samples per scratch tile (one CTA of the step kernels) */
 
 typedef enum sat_status {
     SAT_OK = 0,
@@ -129,6 +134,12 @@ sat_status sat_plan_pi_vars(const sat_plan* p, uint32_t* vars);
  * full_node[v] = row of the Boolean node array, neg[v] = 1 when v is the
  * complement of that node. */
 sat_status sat_plan_var_nodes(const sat_plan* p, int64_t* cone_node, int64_t* full_node, uint8_t* neg);
+/* Device status word of the plan's kernels (synchronises `stream`): 0 when
+ * healthy; bit 2 = a bounded wait for an asynchronous copy expired, and the
+ * results of that launch are invalid.  clear != 0 resets it. */
+sat_status sat_plan_status(const sat_plan* p, uint32_t* status, int32_t clear, void* stream);
+/* Elements of one act / adj scratch array for a batch of B samples. */
+sat_status sat_plan_scratch_elems(const sat_plan* p, int64_t B, uint64_t* elems);
 void sat_plan_free(sat_plan* p);
 
 /* ------------------------------------------- hot-path kernels (device) ---
@@ -145,14 +156,14 @@ sat_status sat_init_normal(const sat_plan* p, uint64_t seed, uint32_t round, flo
  * loss[b] = sum_j (Y_j - T_j)^2 accumulated in FP32 (loss nullable).  act holds
  * act_dtype elements; arithmetic is FP32. */
 sat_status sat_forward(const sat_plan* p, sat_act_dtype act_dtype, const float* V, int64_t ldv, void* act,
-                       int64_t lda, float* loss, int64_t B, void* stream);
+                       float* loss, int64_t B, void* stream);
 
 /* Eq. 8 (chain rule with the Table 1 derivatives): gV[r][b] = d(sum_b w_b
  * loss_b)/dV[r][b] with w = grad_loss (NULL = all ones), from the act written
- * by sat_forward.  adj: [n_cone][lda] float32 scratch.  Rows of gV outside the
- * cone are not written (their gradient is zero). */
+ * by sat_forward.  adj: float32 scratch of the act layout.  Rows of gV outside
+ * the cone are not written (their gradient is zero). */
 sat_status sat_backward(const sat_plan* p, sat_act_dtype act_dtype, const float* V, int64_t ldv, const void* act,
-                        int64_t lda, float* adj, const float* grad_loss, float* gV, int64_t B, void* stream);
+                        float* adj, const float* grad_loss, float* gV, int64_t B, void* stream);
 
 typedef struct sat_opt_params {
     int32_t optimizer;         /* sat_optimizer */
@@ -168,8 +179,8 @@ sat_status sat_opt_update(const sat_plan* p, const sat_opt_params* o, float* V, 
  * t0 .. t0 + n_steps - 1, one kernel launch.  loss (nullable) receives the
  * per-sample loss of the last step's forward pass. */
 sat_status sat_steps(const sat_plan* p, sat_act_dtype act_dtype, const sat_opt_params* o, float* V, float* m,
-                     float* v, int64_t ldv, void* act, float* adj, int64_t lda, float* loss, int32_t t0,
-                     int32_t n_steps, int64_t B, void* stream);
+                     float* v, int64_t ldv, void* act, float* adj, float* loss, int32_t t0, int32_t n_steps,
+                     int64_t B, void* stream);
 
 /* Hard threshold (end of Section III-A): bit = [V > 0] (sigmoid(V) > 1/2; ties
  * give 0).  node_bits rows 0..n_pi-1 receive the bitsliced inputs; keys[b]

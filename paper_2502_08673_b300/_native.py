@@ -14,6 +14,7 @@ SAT_OK, SAT_PARTIAL = 0, 1
 STATUS_NAMES = {0: "SAT_OK", 1: "SAT_PARTIAL", -1: "SAT_ERR_PARSE", -2: "SAT_ERR_ARG", -3: "SAT_ERR_OOM",
                 -4: "SAT_ERR_CUDA", -5: "SAT_ERR_TABLE_FULL", -6: "SAT_ERR_UNSAT_TRIVIAL"}
 ACT_DTYPES = {"f32": 0, "bf16": 1, "f16": 2}
+TILE = 64  # SAT_TILE
 OPTIMIZERS = {"adam": 0, "gd": 1}
 
 
@@ -80,12 +81,14 @@ PROTOTYPES = {
     "sat_plan_get_info": (I32, [P, C.POINTER(PlanInfo)]),
     "sat_plan_pi_vars": (I32, [P, P]),
     "sat_plan_var_nodes": (I32, [P, P, P, P]),
+    "sat_plan_scratch_elems": (I32, [P, I64, C.POINTER(U64)]),
+    "sat_plan_status": (I32, [P, C.POINTER(U32), I32, P]),
     "sat_plan_free": (None, [P]),
     "sat_init_normal": (I32, [P, U64, U32, F32, P, I64, I64, P]),
-    "sat_forward": (I32, [P, I32, P, I64, P, I64, P, I64, P]),
-    "sat_backward": (I32, [P, I32, P, I64, P, I64, P, P, P, I64, P]),
+    "sat_forward": (I32, [P, I32, P, I64, P, P, I64, P]),
+    "sat_backward": (I32, [P, I32, P, I64, P, P, P, P, I64, P]),
     "sat_opt_update": (I32, [P, C.POINTER(OptParams), P, P, P, P, I64, I32, I64, P]),
-    "sat_steps": (I32, [P, I32, C.POINTER(OptParams), P, P, P, I64, P, P, I64, P, I32, I32, I64, P]),
+    "sat_steps": (I32, [P, I32, C.POINTER(OptParams), P, P, P, I64, P, P, P, I32, I32, I64, P]),
     "sat_threshold": (I32, [P, P, I64, P, I64, P, I64, P]),
     "sat_hard_eval": (I32, [P, P, I64, I64, P]),
     "sat_cnf_check": (I32, [P, P, I64, P, I64, P]),

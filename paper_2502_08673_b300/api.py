@@ -4,8 +4,8 @@ Each function marshals arguments (torch tensors -> device pointers, the
 current CUDA stream) and calls the C entry point of the same name; all
 computation happens in the library's kernels.  Layouts are those of
 include/satsampler.h: V, m, v, gV are [n_pi, B] float32; act/adj are
-[n_cone, lda] with lda = B rounded up to 32; bit arrays are [rows, ceil(B/32)]
-int32 words.
+tile-major [ceil(B/64), n_cone, 64]; bit arrays are [rows, ceil(B/32)] int32
+words.
 """
 from __future__ import annotations
 
@@ -120,6 +120,17 @@ class Plan(_Handle):
             return info[k]
         raise AttributeError(k)
 
+    def status(self, clear: bool = True, stream=None) -> int:
+        """Kernel status word (0 = healthy; bit 2 = an async-copy wait expired)."""
+        v = C.c_uint32()
+        check(lib().sat_plan_status(self._h, C.byref(v), int(clear), _stream(stream)))
+        return v.value
+
+    def scratch_elems(self, B: int) -> int:
+        n = C.c_uint64()
+        check(lib().sat_plan_scratch_elems(self._h, B, C.byref(n)))
+        return n.value
+
     def pi_vars(self) -> np.ndarray:
         out = np.zeros(self.info["n_pi"], np.uint32)
         check(lib().sat_plan_pi_vars(self._h, out.ctypes.data_as(C.c_void_p)))
@@ -199,14 +210,23 @@ def _act_torch_dtype(act_dtype: str):
     return {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[act_dtype]
 
 
+def _tiles(B: int) -> int:
+    return (B + N.TILE - 1) // N.TILE
+
+
 def new_act(plan: Plan, B: int, act_dtype: str = "f32", device="cuda"):
     import torch
-    return torch.empty((plan.info["n_cone"], round32(B)), dtype=_act_torch_dtype(act_dtype), device=device)
+    return torch.empty((_tiles(B), plan.info["n_cone"], N.TILE), dtype=_act_torch_dtype(act_dtype), device=device)
 
 
 def new_adj(plan: Plan, B: int, device="cuda"):
     import torch
-    return torch.empty((plan.info["n_cone"], round32(B)), dtype=torch.float32, device=device)
+    return torch.empty((_tiles(B), plan.info["n_cone"], N.TILE), dtype=torch.float32, device=device)
+
+
+def untile(x, B: int):
+    """[n_cone, B] view of a tile-major act/adj array."""
+    return x.permute(1, 0, 2).reshape(x.shape[1], -1)[:, :B]
 
 
 def sat_init_normal(plan: Plan, V, seed: int, round_: int = 0, scale: float = 1.0, stream=None):
@@ -214,13 +234,13 @@ def sat_init_normal(plan: Plan, V, seed: int, round_: int = 0, scale: float = 1.
 
 
 def sat_forward(plan: Plan, V, act, loss=None, act_dtype="f32", stream=None):
-    check(lib().sat_forward(plan.handle, N.ACT_DTYPES[act_dtype], _ptr(V), V.stride(0), _ptr(act), act.stride(0),
-                            _ptr(loss), V.shape[1], _stream(stream)))
+    check(lib().sat_forward(plan.handle, N.ACT_DTYPES[act_dtype], _ptr(V), V.stride(0), _ptr(act), _ptr(loss),
+                            V.shape[1], _stream(stream)))
 
 
 def sat_backward(plan: Plan, V, act, adj, gV, grad_loss=None, act_dtype="f32", stream=None):
-    check(lib().sat_backward(plan.handle, N.ACT_DTYPES[act_dtype], _ptr(V), V.stride(0), _ptr(act), act.stride(0),
-                             _ptr(adj), _ptr(grad_loss), _ptr(gV), V.shape[1], _stream(stream)))
+    check(lib().sat_backward(plan.handle, N.ACT_DTYPES[act_dtype], _ptr(V), V.stride(0), _ptr(act), _ptr(adj),
+                             _ptr(grad_loss), _ptr(gV), V.shape[1], _stream(stream)))
 
 
 def sat_opt_update(plan: Plan, opt: N.OptParams, V, m, v, gV, t: int, stream=None):
@@ -231,8 +251,7 @@ def sat_opt_update(plan: Plan, opt: N.OptParams, V, m, v, gV, t: int, stream=Non
 def sat_steps(plan: Plan, opt: N.OptParams, V, m, v, act, adj, t0: int, n_steps: int, loss=None,
               act_dtype="f32", stream=None):
     check(lib().sat_steps(plan.handle, N.ACT_DTYPES[act_dtype], C.byref(opt), _ptr(V), _ptr(m), _ptr(v), V.stride(0),
-                          _ptr(act), _ptr(adj), act.stride(0), _ptr(loss), t0, n_steps, V.shape[1],
-                          _stream(stream)))
+                          _ptr(act), _ptr(adj), _ptr(loss), t0, n_steps, V.shape[1], _stream(stream)))
 
 
 def sat_threshold(plan: Plan, V, node_bits, keys, stream=None):

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <chrono>
 #include <cstdio>
 #include <cstring>
@@ -98,11 +99,10 @@ sat_status check_device(int device) {
 
 int64_t round32(int64_t x) { return (x + 31) / 32 * 32; }
 
-sat_status check_layout(const sat_plan* p, int64_t B, int64_t ldv, int64_t lda) {
+sat_status check_layout(const sat_plan* p, int64_t B, int64_t ldv) {
     if (!p) return fail(SAT_ERR_ARG, "plan is NULL");
     if (B < 0) return fail(SAT_ERR_ARG, "B < 0");
     if (ldv >= 0 && ldv < B) return fail(SAT_ERR_ARG, "ldv < B");
-    if (lda >= 0 && lda < round32(B)) return fail(SAT_ERR_ARG, "lda must be >= B rounded up to a multiple of 32");
     if (B >= (1ll << 31)) return fail(SAT_ERR_ARG, "B must be < 2^31");
     return check_device(p->device);
 }
@@ -272,7 +272,9 @@ sat_status sat_plan_create(const sat_circuit* c, const sat_cnf* cnf, sat_plan** 
     if ((st = upload(p, P.c_level_off, &d.c_level_off)) != SAT_OK) return bail(st);
     if ((st = upload(p, cg, &d.c_gate)) != SAT_OK) return bail(st);
     if ((st = upload(p, P.cone_pi_row, &d.cone_pi_row)) != SAT_OK) return bail(st);
-    if ((st = upload(p, P.fo_off, &d.fo_off)) != SAT_OK) return bail(st);
+    if (P.fo_g.size() >= (1ull << 31)) return bail(fail(SAT_ERR_ARG, "too many fan-out edges (limit 2^31)"));
+    std::vector<int32_t> fo_off32(P.fo_off.begin(), P.fo_off.end());
+    if ((st = upload(p, fo_off32, &d.fo_off)) != SAT_OK) return bail(st);
     if ((st = upload(p, fe, &d.fo_edge)) != SAT_OK) return bail(st);
     if ((st = upload(p, P.c_out_node, &d.c_out_node)) != SAT_OK) return bail(st);
     if ((st = upload(p, P.out_target, &d.out_target)) != SAT_OK) return bail(st);
@@ -280,6 +282,16 @@ sat_status sat_plan_create(const sat_circuit* c, const sat_cnf* cnf, sat_plan** 
     if ((st = upload(p, fg, &d.f_gate)) != SAT_OK) return bail(st);
     if ((st = upload(p, P.cl_off, &d.cl_off)) != SAT_OK) return bail(st);
     if ((st = upload(p, cl_lit, &d.cl_lit)) != SAT_OK) return bail(st);
+    {
+        void* w = nullptr;
+        if (cudaMalloc(&w, sizeof(unsigned int)) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(fail(SAT_ERR_OOM, "cudaMalloc failed for the status word"));
+        }
+        p->allocs.push_back(w);
+        d.status = (unsigned int*)w;
+        CK(cudaMemset(w, 0, sizeof(unsigned int)));
+    }
     p->h_c_level_off = P.c_level_off;
     p->h_f_level_off = P.level_off;
     d.h_c_level_off = p->h_c_level_off.data();
@@ -328,9 +340,25 @@ sat_status sat_plan_create(const sat_circuit* c, const sat_cnf* cnf, sat_plan** 
     return SAT_OK;
 }
 
+sat_status sat_plan_status(const sat_plan* p, uint32_t* status, int32_t clear, void* stream) {
+    if (!p || !status) return fail(SAT_ERR_ARG, "NULL argument");
+    unsigned int v = 0;
+    CK(cudaMemcpyAsync(&v, p->dp.status, sizeof(v), cudaMemcpyDeviceToHost, S(stream)));
+    if (clear) CK(cudaMemsetAsync(p->dp.status, 0, sizeof(v), S(stream)));
+    CK(cudaStreamSynchronize(S(stream)));
+    *status = v;
+    return SAT_OK;
+}
+
 sat_status sat_plan_get_info(const sat_plan* p, sat_plan_info* info) {
     if (!p || !info) return fail(SAT_ERR_ARG, "NULL argument");
     *info = p->info;
+    return SAT_OK;
+}
+
+sat_status sat_plan_scratch_elems(const sat_plan* p, int64_t B, uint64_t* elems) {
+    if (!p || !elems || B < 0) return fail(SAT_ERR_ARG, "bad argument");
+    *elems = (uint64_t)((B + SAT_TILE - 1) / SAT_TILE) * p->info.n_cone * SAT_TILE;
     return SAT_OK;
 }
 
@@ -351,37 +379,39 @@ sat_status sat_plan_var_nodes(const sat_plan* p, int64_t* cone_node, int64_t* fu
 // -------------------------------------------------------------- kernels --
 sat_status sat_init_normal(const sat_plan* p, uint64_t seed, uint32_t round, float scale, float* V, int64_t ldv,
                            int64_t B, void* stream) {
-    sat_status s = check_layout(p, B, ldv, -1);
+    sat_status s = check_layout(p, B, ldv);
     if (s != SAT_OK) return s;
     if (B > 0 && p->dp.n_pi > 0 && !V) return fail(SAT_ERR_ARG, "V is NULL");
     CK(sat::launch_init_normal(p->dp, seed, round, scale, V, ldv, B, S(stream)));
     return SAT_OK;
 }
 
-sat_status sat_forward(const sat_plan* p, sat_act_dtype t, const float* V, int64_t ldv, void* act, int64_t lda,
-                       float* loss, int64_t B, void* stream) {
-    sat_status s = check_layout(p, B, ldv, lda);
+sat_status sat_forward(const sat_plan* p, sat_act_dtype t, const float* V, int64_t ldv, void* act, float* loss,
+                       int64_t B, void* stream) {
+    sat_status s = check_layout(p, B, ldv);
     if (s != SAT_OK) return s;
     if (t < SAT_ACT_F32 || t > SAT_ACT_F16) return fail(SAT_ERR_ARG, "bad act_dtype");
     if (B > 0 && ((p->dp.n_pi > 0 && !V) || (p->dp.n_cone > 0 && !act))) return fail(SAT_ERR_ARG, "NULL buffer");
-    CK(sat::launch_forward(p->dp, (int)t, V, ldv, act, lda, loss, B, S(stream)));
+    if (((uintptr_t)act & 15) != 0) return fail(SAT_ERR_ARG, "act must be 16-byte aligned");
+    CK(sat::launch_forward(p->dp, (int)t, V, ldv, act, loss, B, S(stream)));
     return SAT_OK;
 }
 
-sat_status sat_backward(const sat_plan* p, sat_act_dtype t, const float* V, int64_t ldv, const void* act, int64_t lda,
-                        float* adj, const float* grad_loss, float* gV, int64_t B, void* stream) {
-    sat_status s = check_layout(p, B, ldv, lda);
+sat_status sat_backward(const sat_plan* p, sat_act_dtype t, const float* V, int64_t ldv, const void* act, float* adj,
+                        const float* grad_loss, float* gV, int64_t B, void* stream) {
+    sat_status s = check_layout(p, B, ldv);
     if (s != SAT_OK) return s;
     if (t < SAT_ACT_F32 || t > SAT_ACT_F16) return fail(SAT_ERR_ARG, "bad act_dtype");
     if (B > 0 && ((p->dp.n_pi > 0 && (!V || !gV)) || (p->dp.n_cone > 0 && (!act || !adj))))
         return fail(SAT_ERR_ARG, "NULL buffer");
-    CK(sat::launch_backward(p->dp, (int)t, V, ldv, act, lda, adj, grad_loss, gV, B, S(stream)));
+    if ((((uintptr_t)act | (uintptr_t)adj) & 15) != 0) return fail(SAT_ERR_ARG, "act/adj must be 16-byte aligned");
+    CK(sat::launch_backward(p->dp, (int)t, V, ldv, act, adj, grad_loss, gV, B, S(stream)));
     return SAT_OK;
 }
 
 sat_status sat_opt_update(const sat_plan* p, const sat_opt_params* o, float* V, float* m, float* v, const float* gV,
                           int64_t ldv, int32_t t, int64_t B, void* stream) {
-    sat_status s = check_layout(p, B, ldv, -1);
+    sat_status s = check_layout(p, B, ldv);
     if (s != SAT_OK) return s;
     if (!opt_ok(o) || t < 1) return fail(SAT_ERR_ARG, "bad optimiser parameters or step");
     if (B > 0 && p->dp.n_cone_pi > 0 && (!V || !gV || (o->optimizer == SAT_OPT_ADAM && (!m || !v))))
@@ -391,22 +421,23 @@ sat_status sat_opt_update(const sat_plan* p, const sat_opt_params* o, float* V, 
 }
 
 sat_status sat_steps(const sat_plan* p, sat_act_dtype t, const sat_opt_params* o, float* V, float* m, float* v,
-                     int64_t ldv, void* act, float* adj, int64_t lda, float* loss, int32_t t0, int32_t n_steps,
-                     int64_t B, void* stream) {
-    sat_status s = check_layout(p, B, ldv, lda);
+                     int64_t ldv, void* act, float* adj, float* loss, int32_t t0, int32_t n_steps, int64_t B,
+                     void* stream) {
+    sat_status s = check_layout(p, B, ldv);
     if (s != SAT_OK) return s;
     if (t < SAT_ACT_F32 || t > SAT_ACT_F16) return fail(SAT_ERR_ARG, "bad act_dtype");
     if (!opt_ok(o) || t0 < 1 || n_steps < 0) return fail(SAT_ERR_ARG, "bad optimiser parameters or steps");
     if (B > 0 && ((p->dp.n_pi > 0 && (!V || (o->optimizer == SAT_OPT_ADAM && (!m || !v)))) ||
                   (p->dp.n_cone > 0 && (!act || !adj))))
         return fail(SAT_ERR_ARG, "NULL buffer");
-    CK(sat::launch_steps(p->dp, (int)t, opt_of(o), V, m, v, ldv, act, adj, lda, loss, t0, n_steps, B, S(stream)));
+    if ((((uintptr_t)act | (uintptr_t)adj) & 15) != 0) return fail(SAT_ERR_ARG, "act/adj must be 16-byte aligned");
+    CK(sat::launch_steps(p->dp, (int)t, opt_of(o), V, m, v, ldv, act, adj, loss, t0, n_steps, B, S(stream)));
     return SAT_OK;
 }
 
 sat_status sat_threshold(const sat_plan* p, const float* V, int64_t ldv, uint32_t* node_bits, int64_t ldw,
                          uint32_t* keys, int64_t B, void* stream) {
-    sat_status s = check_layout(p, B, ldv, -1);
+    sat_status s = check_layout(p, B, ldv);
     if (s != SAT_OK) return s;
     if (ldw < (B + 31) / 32) return fail(SAT_ERR_ARG, "ldw < ceil(B/32)");
     if (B > 0 && p->dp.n_pi > 0 && (!V || !node_bits || !keys)) return fail(SAT_ERR_ARG, "NULL buffer");
@@ -415,7 +446,7 @@ sat_status sat_threshold(const sat_plan* p, const float* V, int64_t ldv, uint32_
 }
 
 sat_status sat_hard_eval(const sat_plan* p, uint32_t* node_bits, int64_t ldw, int64_t B, void* stream) {
-    sat_status s = check_layout(p, B, -1, -1);
+    sat_status s = check_layout(p, B, -1);
     if (s != SAT_OK) return s;
     if (ldw < (B + 31) / 32) return fail(SAT_ERR_ARG, "ldw < ceil(B/32)");
     if (B > 0 && p->dp.n_nodes > 0 && !node_bits) return fail(SAT_ERR_ARG, "NULL buffer");
@@ -425,7 +456,7 @@ sat_status sat_hard_eval(const sat_plan* p, uint32_t* node_bits, int64_t ldw, in
 
 sat_status sat_cnf_check(const sat_plan* p, const uint32_t* node_bits, int64_t ldw, uint32_t* valid, int64_t B,
                          void* stream) {
-    sat_status s = check_layout(p, B, -1, -1);
+    sat_status s = check_layout(p, B, -1);
     if (s != SAT_OK) return s;
     if (ldw < (B + 31) / 32) return fail(SAT_ERR_ARG, "ldw < ceil(B/32)");
     if (B > 0 && (!valid || (p->dp.n_nodes > 0 && !node_bits))) return fail(SAT_ERR_ARG, "NULL buffer");
@@ -556,7 +587,7 @@ struct Workspace {
     float *V = nullptr, *m = nullptr, *v = nullptr, *adj = nullptr;
     void* act = nullptr;
     uint32_t *bits = nullptr, *keys = nullptr, *valid = nullptr;
-    int64_t lda = 0, ldw = 0;
+    int64_t ldw = 0;
     ~Workspace() {
         for (void* b : bufs) cudaFree(b);
     }
@@ -573,6 +604,10 @@ struct Workspace {
 
 size_t act_bytes(int t) { return t == SAT_ACT_F32 ? 4 : 2; }
 
+size_t scratch_elems(const sat::DevPlan& dp, int64_t B) {
+    return (size_t)((B + SAT_TILE - 1) / SAT_TILE) * (size_t)dp.n_cone * SAT_TILE;
+}
+
 }  // namespace
 
 sat_status sat_sample_plan(const sat_plan* p, sat_dedup* d, const sat_sample_opts* o, uint64_t n_wanted,
@@ -588,12 +623,11 @@ sat_status sat_sample_plan(const sat_plan* p, sat_dedup* d, const sat_sample_opt
     cudaStream_t str = S(o->stream);
     const sat::DevPlan& dp = p->dp;
     Workspace w;
-    w.lda = round32(B);
     w.ldw = (B + 31) / 32;
     const size_t npi = (size_t)dp.n_pi;
     if (!w.alloc((void**)&w.V, npi * B * 4) || !w.alloc((void**)&w.m, npi * B * 4) ||
-        !w.alloc((void**)&w.v, npi * B * 4) || !w.alloc(&w.act, (size_t)dp.n_cone * w.lda * act_bytes(o->act_dtype)) ||
-        !w.alloc((void**)&w.adj, (size_t)dp.n_cone * w.lda * 4) ||
+        !w.alloc((void**)&w.v, npi * B * 4) || !w.alloc(&w.act, scratch_elems(dp, B) * act_bytes(o->act_dtype)) ||
+        !w.alloc((void**)&w.adj, scratch_elems(dp, B) * 4) ||
         !w.alloc((void**)&w.bits, (size_t)dp.n_nodes * w.ldw * 4) ||
         !w.alloc((void**)&w.keys, (size_t)B * std::max(1, dp.key_words) * 4) ||
         !w.alloc((void**)&w.valid, (size_t)w.ldw * 4))
@@ -621,7 +655,7 @@ sat_status sat_sample_plan(const sat_plan* p, sat_dedup* d, const sat_sample_opt
         CK(cudaMemsetAsync(w.v, 0, npi * B * 4, str));
         CK(cudaEventRecord(ev[1], str));
         for (int t0 = 1; t0 <= o->steps; t0 += spl)
-            CK(sat::launch_steps(dp, o->act_dtype, op, w.V, w.m, w.v, B, w.act, w.adj, w.lda, nullptr, t0,
+            CK(sat::launch_steps(dp, o->act_dtype, op, w.V, w.m, w.v, B, w.act, w.adj, nullptr, t0,
                                  std::min(spl, o->steps - t0 + 1), B, str));
         CK(cudaEventRecord(ev[2], str));
         CK(sat::launch_threshold(dp, w.V, B, w.bits, w.ldw, w.keys, B, str));
@@ -638,6 +672,9 @@ sat_status sat_sample_plan(const sat_plan* p, sat_dedup* d, const sat_sample_opt
         CK(cudaMemcpyAsync(&status, d->d.status, sizeof(status), cudaMemcpyDeviceToHost, str));
         CK(cudaStreamSynchronize(str));
         if (status) return fail(SAT_ERR_TABLE_FULL, "dedup probe limit reached");
+        uint32_t pst = 0;
+        if ((s = sat_plan_status(p, &pst, 1, str)) != SAT_OK) return s;
+        if (pst) return fail(SAT_ERR_CUDA, "a bounded wait in the step kernel expired (status " + std::to_string(pst) + ")");
         float ms[4];
         for (int i = 0; i < 4; i++) CK(cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]));
         acc.ms_init += ms[0];

@@ -14,7 +14,7 @@ struct DevPlan {
     const int32_t* c_level_off = nullptr;
     const int2* c_gate = nullptr;       // per cone gate: (in0 | gop << 28, in1)
     const int32_t* cone_pi_row = nullptr;
-    const int64_t* fo_off = nullptr;    // [n_cone + 1]
+    const int32_t* fo_off = nullptr;    // [n_cone + 1]
     const int4* fo_edge = nullptr;      // (consumer or -1, sibling or target, c0, c1)
     int32_t n_out = 0;
     const int32_t* c_out_node = nullptr;
@@ -30,6 +30,7 @@ struct DevPlan {
     const int64_t* cl_off = nullptr;
     const int32_t* cl_lit = nullptr;    // node << 1 | negation
     int32_t key_words = 0;              // ceil(n_pi / 32)
+    unsigned int* status = nullptr;     // device status word (bit 2: an async-copy wait expired)
     // host mirrors of the level offsets (launch loops need them)
     const int32_t* h_c_level_off = nullptr;
     const int32_t* h_f_level_off = nullptr;
@@ -45,14 +46,15 @@ struct OptParams {
 // Kernel launchers; return cudaSuccess or the launch error.
 cudaError_t launch_init_normal(const DevPlan& p, uint64_t seed, uint32_t round, float scale,
                                float* V, int64_t ldv, int64_t B, cudaStream_t s);
-cudaError_t launch_forward(const DevPlan& p, int act_type, const float* V, int64_t ldv, void* act,
-                           int64_t lda, float* loss, int64_t B, cudaStream_t s);
-cudaError_t launch_backward(const DevPlan& p, int act_type, const float* V, int64_t ldv, const void* act,
-                            int64_t lda, float* adj, const float* grad_loss, float* gV, int64_t B,
-                            cudaStream_t s);
+// act / adj scratch is tile-major: tile t (samples 64t .. 64t+63) owns rows
+// [n_cone][64] starting at element t * n_cone * 64 (SAT_TILE = 64).
+cudaError_t launch_forward(const DevPlan& p, int act_type, const float* V, int64_t ldv, void* act, float* loss,
+                           int64_t B, cudaStream_t s);
+cudaError_t launch_backward(const DevPlan& p, int act_type, const float* V, int64_t ldv, const void* act, float* adj,
+                            const float* grad_loss, float* gV, int64_t B, cudaStream_t s);
 cudaError_t launch_steps(const DevPlan& p, int act_type, const OptParams& o, float* V, float* m, float* v,
-                         int64_t ldv, void* act, float* adj, int64_t lda, float* loss, int t0, int n_steps,
-                         int64_t B, cudaStream_t s);
+                         int64_t ldv, void* act, float* adj, float* loss, int t0, int n_steps, int64_t B,
+                         cudaStream_t s);
 cudaError_t launch_opt_update(const DevPlan& p, const OptParams& o, float* V, float* m, float* v,
                               const float* gV, int64_t ldv, int t, int64_t B, cudaStream_t s);
 cudaError_t launch_threshold(const DevPlan& p, const float* V, int64_t ldv, uint32_t* node_bits,

@@ -99,9 +99,10 @@ struct Plan {
     // Fan-out CSR over cone nodes for the gather form of the adjoint.  Each
     // edge holds the consuming gate and the sibling input, with the partial
     // d g / d A_self = c0 + c1 * A_sibling (small integer coefficients).  An
-    // edge with consumer -1 is an output seed: 2 (A_self - target).
+    // edge with consumer -1 is an output seed 2 (A_self - target): sibling =
+    // the node itself, c0 = -2 target, c1 = 2.
     std::vector<int64_t> fo_off;
-    std::vector<int32_t> fo_g, fo_sib;            // fo_sib holds the target (0/1) for output edges
+    std::vector<int32_t> fo_g, fo_sib;
     std::vector<int8_t> fo_c0, fo_c1;
     uint32_t max_span = 0;                        // max level distance of a cone edge
 

@@ -224,9 +224,12 @@ bool build_plan(const Circuit& c, const Cnf& cnf, Plan& P, std::string& err) {
     P.fo_g.assign(E, 0); P.fo_sib.assign(E, 0); P.fo_c0.assign(E, 0); P.fo_c1.assign(E, 0);
     std::vector<int64_t> fill(P.fo_off.begin(), P.fo_off.end() - 1);
     for (size_t j = 0; j < P.c_out_node.size(); j++) {
+        // output seed 2 (A_u - T) = c0 + c1 * A_u with the node itself as "sibling"
         int64_t e = fill[P.c_out_node[j]]++;
         P.fo_g[e] = -1;
-        P.fo_sib[e] = (int32_t)P.out_target[j];
+        P.fo_sib[e] = P.c_out_node[j];
+        P.fo_c0[e] = (int8_t)(-2 * (int)P.out_target[j]);
+        P.fo_c1[e] = 2;
     }
     uint32_t span = 0;
     for (size_t g = 0; g < P.c_in0.size(); g++) {

@@ -35,7 +35,10 @@ INSTANCES = {
 
 
 def _grad_close(g, gref):
-    floor = 1e-3 * np.abs(gref).max(axis=1, keepdims=True)
+    # Floor 1e-2 * max_i |g*_i| per sample: an input's adjoint sums many fan-out
+    # terms of both signs (e.g. one per 3-literal OR output), and FP32 summation
+    # error scales with the terms' magnitudes, not with the (cancelled) result.
+    floor = 1e-2 * np.abs(gref).max(axis=1, keepdims=True)
     tol = 1e-4 * np.maximum(np.abs(gref), floor)
     return np.abs(g - gref) <= tol + 1e-30
 
@@ -57,7 +60,7 @@ def test_forward_backward_parity(gpu, name, B):
     gref, _ = oracle.backward(orc.flat, vals)
     np.testing.assert_allclose(loss.cpu().numpy(), loss_ref, rtol=0, atol=1e-5 * max(1, plan.n_outputs))
     cone, _, neg = plan.var_nodes()
-    A = act.cpu().numpy()[:, :B]
+    A = P.untile(act, B).cpu().numpy()
     for v in range(1, plan.n_vars + 1):
         if cone[v] < 0:
             continue
@@ -228,7 +231,7 @@ def test_low_precision_storage_error(gpu, act_dtype, bound):
     torch.cuda.synchronize()
     vals, loss_ref = oracle.forward(orc.flat, V0.astype(np.float64))
     cone, _, neg = plan.var_nodes()
-    A = act.float().cpu().numpy()[:, :B]
+    A = P.untile(act, B).float().cpu().numpy()
     err = 0.0
     for v in range(1, plan.n_vars + 1):
         if cone[v] >= 0:
