@@ -149,8 +149,8 @@ def oracle_sample(text, w, n_samples, n_steps):
 
 def cpu_baseline_entry(text, w, budget_s=15.0):
     # scale the sample so the oracle runs for roughly budget_s seconds
-    probe = oracle_sample(text, w, 8, 4)
-    per_sample_step = probe["seconds"] / (8 * 4)
+    probe = oracle_sample(text, w, 16, 40)
+    per_sample_step = probe["seconds"] / (16 * 40)
     steps = w["steps"]
     n = int(max(4, min(1024, budget_s / max(per_sample_step * steps, 1e-9))))
     r = oracle_sample(text, w, n, steps)
@@ -303,10 +303,8 @@ def main():
             ucount += len(sols)
             d2h += len(sols) * info["key_words"] * 4 + B // 8 + 16
         e2e_s = time.perf_counter() - t1
-        plan_bytes = (info["n_cone_gates"] * 8 + info["n_gates"] * 8 + info["n_fanout_edges"] * 16
-                      + info["n_cone"] * 8 + info["n_clauses"] * 8 + 4 * sum(1 for _ in range(1)))
-        plan_bytes += int(np.ceil(cnf.info()[2] * 4))
-        e2e = {"value": ucount / e2e_s, "unit": "unique valid solutions/s", "h2d_bytes_per_step": plan_bytes,
+        e2e = {"value": ucount / e2e_s, "unit": "unique valid solutions/s",
+               "h2d_bytes_per_step": info["upload_bytes"],
                "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps,
                "note": "sat_sample from host CNF/circuit objects: plan upload, workspace, one round, key download"}
 

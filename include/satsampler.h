@@ -44,7 +44,7 @@ extern "C" {
 #endif
 
 #define SAT_ABI_VERSION 1
-#define SAT_TILE 64  /* samples per scratch tile (one CTA of the step kernels) */
+#define SAT_TILE 128  /* samples per scratch tile (one CTA of the step kernels) */
 
 typedef enum sat_status {
     SAT_OK = 0,
@@ -123,6 +123,7 @@ typedef struct sat_plan_info {
     uint64_t n_cone;           /* rows of act / adj: cone inputs + cone gates */
     uint64_t n_nodes;          /* rows of the Boolean node array: inputs + all gates */
     uint64_t n_cone_gates, n_gates, n_clauses, n_fanout_edges;
+    uint64_t upload_bytes;     /* bytes copied host -> device by sat_plan_create */
 } sat_plan_info;
 
 sat_status sat_plan_create(const sat_circuit* c, const sat_cnf* cnf, sat_plan** out);

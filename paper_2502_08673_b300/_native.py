@@ -14,7 +14,7 @@ SAT_OK, SAT_PARTIAL = 0, 1
 STATUS_NAMES = {0: "SAT_OK", 1: "SAT_PARTIAL", -1: "SAT_ERR_PARSE", -2: "SAT_ERR_ARG", -3: "SAT_ERR_OOM",
                 -4: "SAT_ERR_CUDA", -5: "SAT_ERR_TABLE_FULL", -6: "SAT_ERR_UNSAT_TRIVIAL"}
 ACT_DTYPES = {"f32": 0, "bf16": 1, "f16": 2}
-TILE = 64  # SAT_TILE
+TILE = 128  # SAT_TILE
 OPTIMIZERS = {"adam": 0, "gd": 1}
 
 
@@ -41,7 +41,7 @@ class PlanInfo(C.Structure):
                 ("n_cone_levels", C.c_uint32), ("n_levels", C.c_uint32), ("key_words", C.c_uint32),
                 ("max_span", C.c_uint32), ("n_cone", C.c_uint64), ("n_nodes", C.c_uint64),
                 ("n_cone_gates", C.c_uint64), ("n_gates", C.c_uint64), ("n_clauses", C.c_uint64),
-                ("n_fanout_edges", C.c_uint64)]
+                ("n_fanout_edges", C.c_uint64), ("upload_bytes", C.c_uint64)]
 
 
 class OptParams(C.Structure):

@@ -4,7 +4,7 @@ Each function marshals arguments (torch tensors -> device pointers, the
 current CUDA stream) and calls the C entry point of the same name; all
 computation happens in the library's kernels.  Layouts are those of
 include/satsampler.h: V, m, v, gV are [n_pi, B] float32; act/adj are
-tile-major [ceil(B/64), n_cone, 64]; bit arrays are [rows, ceil(B/32)] int32
+tile-major [ceil(B/128), n_cone, 128]; bit arrays are [rows, ceil(B/32)] int32
 words.
 """
 from __future__ import annotations

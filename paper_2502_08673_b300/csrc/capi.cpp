@@ -18,6 +18,8 @@
 #include "device.hpp"
 #include "host.hpp"
 
+static_assert(SAT_TILE == SAT_TILE_SAMPLES, "ABI tile width");
+
 struct sat_cnf {
     sat::Cnf cnf;
 };
@@ -79,6 +81,7 @@ template <typename T>
 sat_status upload(sat_plan* p, const std::vector<T>& h, const T** dst) {
     *dst = nullptr;
     if (h.empty()) return SAT_OK;
+    p->info.upload_bytes += h.size() * sizeof(T);
     void* d = nullptr;
     if (cudaMalloc(&d, h.size() * sizeof(T)) != cudaSuccess) {
         cudaGetLastError();
@@ -256,6 +259,7 @@ sat_status sat_plan_create(const sat_circuit* c, const sat_cnf* cnf, sat_plan** 
     d.n_cone_pi = (int32_t)P.n_cone_pi;
     d.n_cone = (int64_t)P.n_cone;
     d.n_clev = (int32_t)P.c_level_off.size() - 2;
+    d.max_span = (int32_t)std::max<uint32_t>(P.max_span, 1);
     d.n_out = (int32_t)P.c_out_node.size();
     d.n_pi = (int32_t)P.n_pi;
     d.n_nodes = (int64_t)P.n_nodes;
@@ -266,7 +270,14 @@ sat_status sat_plan_create(const sat_circuit* c, const sat_cnf* cnf, sat_plan** 
     for (size_t g = 0; g < cg.size(); g++) cg[g] = make_int2(P.c_in0[g] | ((int32_t)P.c_gop[g] << 28), P.c_in1[g]);
     for (size_t g = 0; g < fg.size(); g++) fg[g] = make_int2(P.in0[g] | ((int32_t)P.gop[g] << 28), P.in1[g]);
     std::vector<int4> fe(P.fo_g.size());
-    for (size_t e = 0; e < fe.size(); e++) fe[e] = make_int4(P.fo_g[e], P.fo_sib[e], P.fo_c0[e], P.fo_c1[e]);
+    // edge record: consumer, sibling, and the partial's coefficients c0, c1 as float bits
+    for (size_t e = 0; e < fe.size(); e++) {
+        float c0 = (float)P.fo_c0[e], c1 = (float)P.fo_c1[e];
+        int32_t i0, i1;
+        std::memcpy(&i0, &c0, 4);
+        std::memcpy(&i1, &c1, 4);
+        fe[e] = make_int4(P.fo_g[e], P.fo_sib[e], i0, i1);
+    }
     std::vector<int32_t> cl_lit(P.cl_node.size());
     for (size_t i = 0; i < cl_lit.size(); i++) cl_lit[i] = (P.cl_node[i] << 1) | P.cl_neg[i];
     if ((st = upload(p, P.c_level_off, &d.c_level_off)) != SAT_OK) return bail(st);
@@ -321,7 +332,7 @@ sat_status sat_plan_create(const sat_circuit* c, const sat_cnf* cnf, sat_plan** 
     p->f_in0 = P.in0;
     p->f_in1 = P.in1;
     p->f_gop = P.gop;
-    sat_plan_info& I = p->info;
+    sat_plan_info& I = p->info;  // upload_bytes was accumulated by upload()
     I.n_vars = P.n_vars;
     I.n_pi = P.n_pi;
     I.n_cone_pi = P.n_cone_pi;
@@ -358,7 +369,7 @@ sat_status sat_plan_get_info(const sat_plan* p, sat_plan_info* info) {
 
 sat_status sat_plan_scratch_elems(const sat_plan* p, int64_t B, uint64_t* elems) {
     if (!p || !elems || B < 0) return fail(SAT_ERR_ARG, "bad argument");
-    *elems = (uint64_t)((B + SAT_TILE - 1) / SAT_TILE) * p->info.n_cone * SAT_TILE;
+    *elems = (uint64_t)((B + SAT_TILE_SAMPLES - 1) / SAT_TILE_SAMPLES) * p->info.n_cone * SAT_TILE_SAMPLES;
     return SAT_OK;
 }
 
@@ -605,7 +616,7 @@ struct Workspace {
 size_t act_bytes(int t) { return t == SAT_ACT_F32 ? 4 : 2; }
 
 size_t scratch_elems(const sat::DevPlan& dp, int64_t B) {
-    return (size_t)((B + SAT_TILE - 1) / SAT_TILE) * (size_t)dp.n_cone * SAT_TILE;
+    return (size_t)((B + SAT_TILE_SAMPLES - 1) / SAT_TILE_SAMPLES) * (size_t)dp.n_cone * SAT_TILE_SAMPLES;
 }
 
 }  // namespace

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 
+#define SAT_TILE_SAMPLES 128  // samples per scratch tile (SAT_TILE in the C ABI)
+
 namespace sat {
 
 // Device copy of a Plan.  All pointers are device pointers owned by the plan.
@@ -11,11 +13,12 @@ struct DevPlan {
     int32_t n_cone_pi = 0;
     int64_t n_cone = 0;
     int32_t n_clev = 0;                 // cone levels 1..n_clev
+    int32_t max_span = 0;               // max level distance of a cone edge (consumer level - input level)
     const int32_t* c_level_off = nullptr;
     const int2* c_gate = nullptr;       // per cone gate: (in0 | gop << 28, in1)
     const int32_t* cone_pi_row = nullptr;
     const int32_t* fo_off = nullptr;    // [n_cone + 1]
-    const int4* fo_edge = nullptr;      // (consumer or -1, sibling or target, c0, c1)
+    const int4* fo_edge = nullptr;      // (consumer or -1, sibling, float bits of c0, float bits of c1)
     int32_t n_out = 0;
     const int32_t* c_out_node = nullptr;
     const float* out_target = nullptr;
@@ -46,8 +49,8 @@ struct OptParams {
 // Kernel launchers; return cudaSuccess or the launch error.
 cudaError_t launch_init_normal(const DevPlan& p, uint64_t seed, uint32_t round, float scale,
                                float* V, int64_t ldv, int64_t B, cudaStream_t s);
-// act / adj scratch is tile-major: tile t (samples 64t .. 64t+63) owns rows
-// [n_cone][64] starting at element t * n_cone * 64 (SAT_TILE = 64).
+// act / adj scratch is tile-major: tile t (samples 128t .. 128t+127) owns rows
+// [n_cone][128] starting at element t * n_cone * 128 (SAT_TILE = 128).
 cudaError_t launch_forward(const DevPlan& p, int act_type, const float* V, int64_t ldv, void* act, float* loss,
                            int64_t B, cudaStream_t s);
 cudaError_t launch_backward(const DevPlan& p, int act_type, const float* V, int64_t ldv, const void* act, float* adj,

@@ -1,16 +1,18 @@
 // CUDA kernels of the sampler's hot path (sm_103a).
 //
 // Layout: every per-sample quantity is stored node-major with the batch
-// contiguous ("SoA"): row r of V, m, v, gV is primary input r over the batch;
-// row u of act / adj is cone node u over the batch.  A CTA owns a tile of 32
-// samples (lane = sample) and walks the levels of the circuit; samples are
+// contiguous ("SoA"): row r of V, m, v, gV is primary input r over the batch.
+// The per-node scratch (act, adj) is tile-major: a CTA owns a tile of TILE
+// samples (VEC consecutive samples per lane) and its contiguous block of
+// [n_cone][TILE] rows, and walks the levels of the circuit.  Samples are
 // independent, so the only synchronisation is __syncthreads between levels.
 //
-// Relaxation (Table 1): AND a*b, OR 1-(1-a)(1-b), XOR a+b-2ab, input negation
-// 1-a; embedding P = sigmoid(V) (Eq. 5); loss sum_j (Y_j - T_j)^2 (Eq. 7); the
-// adjoint is the chain rule of Eq. 8 in gather form (each node sums, in a fixed
-// order, the contributions of its fan-out edges); the update is Eq. 9 (GD) or
-// Adam in PyTorch's formulation.
+// Relaxation (Table 1): with input negation x -> 1 - x folded in, every
+// 2-input gate is a bilinear form y = k0 + k1 a + k2 b + k3 a b (AND: a b;
+// OR: a + b - a b; XOR: a + b - 2 a b); embedding P = sigmoid(V) (Eq. 5); loss
+// sum_j (Y_j - T_j)^2 (Eq. 7); the adjoint is the chain rule of Eq. 8 in
+// gather form (each node sums, in a fixed order, the contributions of its
+// fan-out edges); the update is Eq. 9 (GD) or Adam in PyTorch's formulation.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -22,54 +24,105 @@
 namespace sat {
 namespace {
 
-constexpr int VEC = 2;                 // consecutive samples per lane
+#ifndef SAT_VEC
+#define SAT_VEC 4
+#endif
+constexpr int VEC = SAT_VEC;           // consecutive samples per lane
 constexpr int TILE = 32 * VEC;         // samples per CTA
+static_assert(TILE == SAT_TILE_SAMPLES, "tile width must match the ABI");
 constexpr int STEP_THREADS = 512;
 constexpr int UBATCH = 2;              // input rows per warp in the input-level passes
 constexpr unsigned FULL = 0xffffffffu;
 
-// Two consecutive samples of one scratch row, in registers as float2.
+// VEC consecutive samples of one row, in registers.
+struct VF {
+    float v[VEC];
+};
+
+__device__ __forceinline__ VF vf_fill(float x) {
+    VF r;
+#pragma unroll
+    for (int q = 0; q < VEC; q++) r.v[q] = x;
+    return r;
+}
+
 template <typename T> struct ActIO;
 template <> struct ActIO<float> {
-    static __device__ __forceinline__ float2 ld(const float* p) { return *reinterpret_cast<const float2*>(p); }
-    static __device__ __forceinline__ void st(float* p, float2 x) { *reinterpret_cast<float2*>(p) = x; }
+    static __device__ __forceinline__ VF ld(const float* p) {
+        VF r;
+        if constexpr (VEC == 4) {
+            const float4 q = *reinterpret_cast<const float4*>(p);
+            r.v[0] = q.x; r.v[1] = q.y; r.v[2] = q.z; r.v[3] = q.w;
+        } else {
+            const float2 q = *reinterpret_cast<const float2*>(p);
+            r.v[0] = q.x; r.v[1] = q.y;
+        }
+        return r;
+    }
+    static __device__ __forceinline__ void st(float* p, const VF& x) {
+        if constexpr (VEC == 4) *reinterpret_cast<float4*>(p) = make_float4(x.v[0], x.v[1], x.v[2], x.v[3]);
+        else *reinterpret_cast<float2*>(p) = make_float2(x.v[0], x.v[1]);
+    }
 };
 template <> struct ActIO<__nv_bfloat16> {
-    static __device__ __forceinline__ float2 ld(const __nv_bfloat16* p) {
-        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+    static __device__ __forceinline__ VF ld(const __nv_bfloat16* p) {
+        VF r;
+#pragma unroll
+        for (int q = 0; q < VEC; q += 2) {
+            const float2 f = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(p)[q / 2]);
+            r.v[q] = f.x; r.v[q + 1] = f.y;
+        }
+        return r;
     }
-    static __device__ __forceinline__ void st(__nv_bfloat16* p, float2 x) {
-        *reinterpret_cast<__nv_bfloat162*>(p) = __float22bfloat162_rn(x);
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, const VF& x) {
+#pragma unroll
+        for (int q = 0; q < VEC; q += 2)
+            reinterpret_cast<__nv_bfloat162*>(p)[q / 2] = __float22bfloat162_rn(make_float2(x.v[q], x.v[q + 1]));
     }
 };
 template <> struct ActIO<__half> {
-    static __device__ __forceinline__ float2 ld(const __half* p) {
-        return __half22float2(*reinterpret_cast<const __half2*>(p));
+    static __device__ __forceinline__ VF ld(const __half* p) {
+        VF r;
+#pragma unroll
+        for (int q = 0; q < VEC; q += 2) {
+            const float2 f = __half22float2(reinterpret_cast<const __half2*>(p)[q / 2]);
+            r.v[q] = f.x; r.v[q + 1] = f.y;
+        }
+        return r;
     }
-    static __device__ __forceinline__ void st(__half* p, float2 x) { *reinterpret_cast<__half2*>(p) = __float22half2_rn(x); }
+    static __device__ __forceinline__ void st(__half* p, const VF& x) {
+#pragma unroll
+        for (int q = 0; q < VEC; q += 2)
+            reinterpret_cast<__half2*>(p)[q / 2] = __float22half2_rn(make_float2(x.v[q], x.v[q + 1]));
+    }
 };
 
 __device__ __forceinline__ float sigmoidf_(float v) { return 1.0f / (1.0f + expf(-v)); }
 
-// Table 1 on (possibly negated) inputs; gop = op | neg0 << 2 | neg1 << 3.
-__device__ __forceinline__ float gate_eval(uint32_t gop, float a, float b) {
-    if (gop & 4) a = 1.0f - a;
-    if (gop & 8) b = 1.0f - b;
-    switch (gop & 3) {
-    case 0: return a * b;
-    case 1: return fmaf(-a, b, a + b);
-    default: return fmaf(-2.0f * a, b, a + b);
+// Bilinear coefficients (k0, k1, k2, k3) of gate code gop = op | neg0 << 2 |
+// neg1 << 3, with a' = n0 + s0 a and b' = n1 + s1 b (s = 1 - 2 n):
+//   AND a'b':         (n0 n1,             s0 n1,         n0 s1,         s0 s1)
+//   OR a'+b'-a'b':    (n0 + n1 - n0 n1,   s0 (1 - n1),   s1 (1 - n0),  -s0 s1)
+//   XOR a'+b'-2a'b':  (n0 + n1 - 2 n0 n1, s0 (1 - 2 n1), s1 (1 - 2 n0), -2 s0 s1)
+__device__ __forceinline__ float4 gate_coeffs(uint32_t gop) {
+    const float n0 = (float)((gop >> 2) & 1u), n1 = (float)((gop >> 3) & 1u);
+    const float s0 = 1.0f - 2.0f * n0, s1 = 1.0f - 2.0f * n1;
+    switch (gop & 3u) {
+    case 0: return make_float4(n0 * n1, s0 * n1, n0 * s1, s0 * s1);
+    case 1: return make_float4(n0 + n1 - n0 * n1, s0 * (1.0f - n1), s1 * (1.0f - n0), -s0 * s1);
+    default: return make_float4(n0 + n1 - 2.0f * n0 * n1, s0 * (1.0f - 2.0f * n1), s1 * (1.0f - 2.0f * n0),
+                                -2.0f * s0 * s1);
     }
 }
 
-__device__ __forceinline__ float2 gate_eval2(uint32_t gop, float2 a, float2 b) {
-    return make_float2(gate_eval(gop, a.x, b.x), gate_eval(gop, a.y, b.y));
+__device__ __forceinline__ float gate_apply(const float4& k, float a, float b) {
+    return fmaf(fmaf(k.w, a, k.z), b, fmaf(k.y, a, k.x));
 }
 
 struct TileCtx {
     int lane, warp, nw;
     int64_t b;      // first of this lane's VEC samples
-    bool ok0, ok1;  // b < B, b + 1 < B
+    int nvalid;     // how many of them are < B
 };
 
 __device__ __forceinline__ TileCtx tile_ctx(int64_t B) {
@@ -78,8 +131,8 @@ __device__ __forceinline__ TileCtx tile_ctx(int64_t B) {
     c.warp = threadIdx.x >> 5;
     c.nw = blockDim.x >> 5;
     c.b = (int64_t)blockIdx.x * TILE + c.lane * VEC;
-    c.ok0 = c.b < B;
-    c.ok1 = c.b + 1 < B;
+    const int64_t rem = B - c.b;
+    c.nvalid = rem <= 0 ? 0 : (rem >= VEC ? VEC : (int)rem);
     return c;
 }
 
@@ -102,7 +155,10 @@ __device__ __forceinline__ void adam_bias(const OptParams& o, double p1, double 
 // in flight while it computes on the oldest one.  Every mbarrier wait is
 // bounded: on expiry the kernel records STATUS_WAIT_TIMEOUT in the plan's
 // status word and carries on (results are then invalid, the GPU is not hung).
-constexpr int CHUNK = 8;   // gates (forward) or fan-out edges (adjoint) per chunk
+#ifndef SAT_CHUNK
+#define SAT_CHUNK 4
+#endif
+constexpr int CHUNK = SAT_CHUNK;  // gates (forward) or fan-out edges (adjoint) per chunk
 constexpr int NSLOT = 3;   // pipeline depth per warp
 constexpr unsigned STATUS_WAIT_TIMEOUT = 4u;
 constexpr uint32_t WAIT_LIMIT = 1u << 24;
@@ -130,6 +186,26 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                      smem_u32(dst)),
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
+}
+// Bulk copy with an L2 eviction-priority policy (streaming reads that should
+// not displace the rows reused within the next few levels).
+__device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                              uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+// Drop 128-byte lines from L2 without writing them back (their contents become
+// undefined): used for adjoint rows whose last reader has run.
+__device__ __forceinline__ void discard_l2_line(const void* p) {
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
 }
 __device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
@@ -189,28 +265,35 @@ __device__ __forceinline__ void stage_wait(Stage& st, int s) {
 // level.  Within a level each warp takes a contiguous run of gates; 32 gate
 // records come in one coalesced load and are broadcast by shuffles; the two
 // input rows of each gate are bulk-copied into shared memory, CHUNK gates per
-// slot, NSLOT-1 chunks ahead of the computation.
+// slot, NSLOT-1 chunks ahead of the computation.  gcoef: the 16 bilinear
+// coefficient sets in shared memory.
 template <typename T>
 __device__ void tile_forward(const DevPlan& p, const float* __restrict__ V, int64_t ldv, T* act, Stage& st,
-                             const TileCtx& c) {
+                             const float4* gcoef, const TileCtx& c) {
     constexpr int ROWB = TILE * (int)sizeof(T);
     constexpr int SLOT = slot_bytes<T>();
     for (int i0 = c.warp * UBATCH; i0 < p.n_cone_pi; i0 += c.nw * UBATCH) {
-        float2 x[UBATCH];
+        VF x[UBATCH];
 #pragma unroll
         for (int u = 0; u < UBATCH; u++) {
             const int i = i0 + u;
-            x[u] = make_float2(0.0f, 0.0f);
+            x[u] = vf_fill(0.0f);
             if (i < p.n_cone_pi) {
                 const float* r = V + (int64_t)__ldg(&p.cone_pi_row[i]) * ldv + c.b;
-                if (c.ok0) x[u].x = r[0];
-                if (c.ok1) x[u].y = r[1];
+#pragma unroll
+                for (int q = 0; q < VEC; q++)
+                    if (q < c.nvalid) x[u].v[q] = r[q];
             }
         }
 #pragma unroll
         for (int u = 0; u < UBATCH; u++) {
             const int i = i0 + u;
-            if (i < p.n_cone_pi) ActIO<T>::st(act + at(i, c), make_float2(sigmoidf_(x[u].x), sigmoidf_(x[u].y)));
+            if (i < p.n_cone_pi) {
+                VF y;
+#pragma unroll
+                for (int q = 0; q < VEC; q++) y.v[q] = sigmoidf_(x[u].v[q]);
+                ActIO<T>::st(act + at(i, c), y);
+            }
         }
     }
     fence_async_global();
@@ -248,9 +331,13 @@ __device__ void tile_forward(const DevPlan& p, const float* __restrict__ V, int6
                     const int gl = ch * CHUNK + j;
                     const uint32_t gop = (uint32_t)__shfl_sync(FULL, mine.x, gl & 31) >> 28;
                     if (gl < cnt) {
-                        const float2 x = ActIO<T>::ld(reinterpret_cast<const T*>(sb + (2 * j) * ROWB) + c.lane * VEC);
-                        const float2 y = ActIO<T>::ld(reinterpret_cast<const T*>(sb + (2 * j + 1) * ROWB) + c.lane * VEC);
-                        ActIO<T>::st(act + at(base + gl, c), gate_eval2(gop, x, y));
+                        const float4 k = gcoef[gop];
+                        const VF x = ActIO<T>::ld(reinterpret_cast<const T*>(sb + (2 * j) * ROWB) + c.lane * VEC);
+                        const VF y = ActIO<T>::ld(reinterpret_cast<const T*>(sb + (2 * j + 1) * ROWB) + c.lane * VEC);
+                        VF z;
+#pragma unroll
+                        for (int q = 0; q < VEC; q++) z.v[q] = gate_apply(k, x.v[q], y.v[q]);
+                        ActIO<T>::st(act + at(base + gl, c), z);
                     }
                 }
                 fence_async_shared();
@@ -265,24 +352,24 @@ __device__ void tile_forward(const DevPlan& p, const float* __restrict__ V, int6
 // Per-sample loss sum_j (Y_j - T_j)^2, FP32, fixed order (warp-strided partials, then warp order).
 template <typename T>
 __device__ void tile_loss(const DevPlan& p, const T* act, float* loss, const TileCtx& c) {
-    __shared__ float2 part[STEP_THREADS / 32][32];
-    float2 acc = make_float2(0.0f, 0.0f);
+    __shared__ VF part[STEP_THREADS / 32][32];
+    VF acc = vf_fill(0.0f);
     for (int j = c.warp; j < p.n_out; j += c.nw) {
-        const float2 y = ActIO<T>::ld(act + at(p.c_out_node[j], c));
+        const VF y = ActIO<T>::ld(act + at(p.c_out_node[j], c));
         const float t = p.out_target[j];
-        acc.x = fmaf(y.x - t, y.x - t, acc.x);
-        acc.y = fmaf(y.y - t, y.y - t, acc.y);
+#pragma unroll
+        for (int q = 0; q < VEC; q++) acc.v[q] = fmaf(y.v[q] - t, y.v[q] - t, acc.v[q]);
     }
     part[c.warp][c.lane] = acc;
     __syncthreads();
     if (c.warp == 0) {
-        float2 s = make_float2(0.0f, 0.0f);
-        for (int w = 0; w < c.nw; w++) {
-            s.x += part[w][c.lane].x;
-            s.y += part[w][c.lane].y;
-        }
-        if (c.ok0) loss[c.b] = s.x;
-        if (c.ok1) loss[c.b + 1] = s.y;
+        VF sum = vf_fill(0.0f);
+        for (int w = 0; w < c.nw; w++)
+#pragma unroll
+            for (int q = 0; q < VEC; q++) sum.v[q] += part[w][c.lane].v[q];
+#pragma unroll
+        for (int q = 0; q < VEC; q++)
+            if (q < c.nvalid) loss[c.b + q] = sum.v[q];
     }
     __syncthreads();
 }
@@ -294,13 +381,14 @@ __device__ void tile_loss(const DevPlan& p, const T* act, float* loss, const Til
 // consumer-adjoint and sibling rows are bulk-copied into shared memory, CHUNK
 // edges per slot.
 template <typename T>
-__device__ void level_adjoint(const DevPlan& p, int lo, int hi, const T* act, float* adj, float2 seed_scale,
+__device__ void level_adjoint(const DevPlan& p, int lo, int hi, const T* act, float* adj, const VF& seed_scale,
                               Stage& st, const TileCtx& c) {
     constexpr int ROWB = TILE * (int)sizeof(T);
     constexpr int ROWF = TILE * 4;
     constexpr int SLOT = slot_bytes<T>();
     const char* abytes = reinterpret_cast<const char*>(act);
     const char* gbytes = reinterpret_cast<const char*>(adj);
+    const uint64_t stream_policy = policy_evict_first();
     const int per = (hi - lo + c.nw - 1) / c.nw;
     const int u0 = lo + c.warp * per, u1 = min(u0 + per, hi);
     for (int ua = u0; ua < u1; ua += 31) {
@@ -309,7 +397,7 @@ __device__ void level_adjoint(const DevPlan& p, int lo, int hi, const T* act, fl
         const int e_begin = __shfl_sync(FULL, off, 0), e_end = __shfl_sync(FULL, off, nn);
         int k = 0;
         int k_end = __shfl_sync(FULL, off, 1);
-        float2 acc = make_float2(0.0f, 0.0f);
+        VF acc = vf_fill(0.0f);
         for (int base = e_begin; base < e_end; base += 32) {
             const int cnt = min(32, e_end - base);
             int4 mine = make_int4(-1, 0, 0, 0);
@@ -329,7 +417,9 @@ __device__ void level_adjoint(const DevPlan& p, int lo, int hi, const T* act, fl
                 __syncwarp();
                 char* sb = st.buf + s * SLOT;
                 if (adj_row) bulk_g2s(sb + j * ROWF, gbytes + (size_t)g * ROWF, ROWF, st.bar + s);
-                if (act_row) bulk_g2s(sb + CHUNK * ROWF + j * ROWB, abytes + (size_t)sib * ROWB, ROWB, st.bar + s);
+                if (act_row)
+                    bulk_g2s_hint(sb + CHUNK * ROWF + j * ROWB, abytes + (size_t)sib * ROWB, ROWB, st.bar + s,
+                                  stream_policy);
             };
             for (int ch = 0; ch < NSLOT - 1 && ch < nch; ch++) issue(ch);
             for (int ch = 0; ch < nch; ch++) {
@@ -341,22 +431,22 @@ __device__ void level_adjoint(const DevPlan& p, int lo, int hi, const T* act, fl
                 for (int j = 0; j < CHUNK; j++) {
                     const int el = ch * CHUNK + j;
                     const int gx = __shfl_sync(FULL, mine.x, el & 31);
-                    const float c0 = (float)__shfl_sync(FULL, mine.z, el & 31);
-                    const float c1 = (float)__shfl_sync(FULL, mine.w, el & 31);
+                    const float c0 = __int_as_float(__shfl_sync(FULL, mine.z, el & 31));
+                    const float c1 = __int_as_float(__shfl_sync(FULL, mine.w, el & 31));
                     if (el < cnt) {
                         const int e = base + el;
                         while (e >= k_end) {
-                            *reinterpret_cast<float2*>(adj + at(ua + k, c)) = acc;
-                            acc = make_float2(0.0f, 0.0f);
+                            ActIO<float>::st(adj + at(ua + k, c), acc);
+                            acc = vf_fill(0.0f);
                             k++;
                             k_end = __shfl_sync(FULL, off, k + 1);
                         }
-                        const float2 ga = gx < 0 ? seed_scale
-                                                 : *reinterpret_cast<const float2*>(sb + j * ROWF + c.lane * 8);
-                        const float2 sv =
+                        const VF ga = gx < 0 ? seed_scale
+                                             : ActIO<float>::ld(reinterpret_cast<const float*>(sb + j * ROWF) + c.lane * VEC);
+                        const VF sv =
                             ActIO<T>::ld(reinterpret_cast<const T*>(sb + CHUNK * ROWF + j * ROWB) + c.lane * VEC);
-                        acc.x = fmaf(ga.x, fmaf(c1, sv.x, c0), acc.x);
-                        acc.y = fmaf(ga.y, fmaf(c1, sv.y, c0), acc.y);
+#pragma unroll
+                        for (int q = 0; q < VEC; q++) acc.v[q] = fmaf(ga.v[q], fmaf(c1, sv.v[q], c0), acc.v[q]);
                     }
                 }
                 fence_async_shared();
@@ -364,8 +454,8 @@ __device__ void level_adjoint(const DevPlan& p, int lo, int hi, const T* act, fl
             }
         }
         while (k < nn) {
-            *reinterpret_cast<float2*>(adj + at(ua + k, c)) = acc;
-            acc = make_float2(0.0f, 0.0f);
+            ActIO<float>::st(adj + at(ua + k, c), acc);
+            acc = vf_fill(0.0f);
             k++;
         }
     }
@@ -391,6 +481,17 @@ __device__ __forceinline__ void input_update(const OptParams& o, float* V, float
     }
 }
 
+// Discard, from L2, this tile's adjoint rows of cone level l (level 0 = the
+// inputs); the whole CTA shares the 128-byte lines.
+__device__ __forceinline__ void discard_adj_rows(const DevPlan& p, int l, const float* adj) {
+    const int lo = l == 0 ? 0 : __ldg(&p.c_level_off[l]);
+    const int hi = l == 0 ? p.n_cone_pi : __ldg(&p.c_level_off[l + 1]);
+    const char* b = reinterpret_cast<const char*>(adj);
+    constexpr int LINES_PER_ROW = TILE * 4 / 128;
+    const int n = (hi - lo) * LINES_PER_ROW;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) discard_l2_line(b + (size_t)lo * TILE * 4 + (size_t)i * 128);
+}
+
 // Backward pass of one tile over levels n_clev..0.  The input level's adjoints
 // (of P) are turned into dL/dV and either stored (gV) or applied by the
 // optimiser, UBATCH rows at a time.
@@ -398,58 +499,67 @@ template <typename T, bool UPDATE>
 __device__ void tile_backward(const DevPlan& p, const OptParams& o, float* V, float* m, float* v, float* gV,
                               int64_t ldv, const T* act, float* adj, const float* grad_loss, double p1, double p2,
                               Stage& st, const TileCtx& c) {
-    float2 seed_scale = make_float2(1.0f, 1.0f);
-    if (grad_loss != nullptr) {
-        seed_scale.x = c.ok0 ? grad_loss[c.b] : 0.0f;
-        seed_scale.y = c.ok1 ? grad_loss[c.b + 1] : 0.0f;
-    }
+    VF seed_scale = vf_fill(1.0f);
+    if (grad_loss != nullptr)
+#pragma unroll
+        for (int q = 0; q < VEC; q++) seed_scale.v[q] = q < c.nvalid ? grad_loss[c.b + q] : 0.0f;
     for (int l = p.n_clev; l >= 0; l--) {
         const int lo = l == 0 ? 0 : __ldg(&p.c_level_off[l]);
         const int hi = l == 0 ? p.n_cone_pi : __ldg(&p.c_level_off[l + 1]);
         level_adjoint<T>(p, lo, hi, act, adj, seed_scale, st, c);
         fence_async_global();
         __syncthreads();
+        // Adjoint rows of level l + span have no reader below level l.
+        if (l + p.max_span <= p.n_clev) discard_adj_rows(p, l + p.max_span, adj);
     }
     float step_size = 0.0f, bc2s = 1.0f;
-    if (UPDATE && o.opt == 0) adam_bias(o, p1, p2, step_size, bc2s);
     const bool adam = UPDATE && o.opt == 0;
+    if (adam) adam_bias(o, p1, p2, step_size, bc2s);
     for (int i0 = c.warp * UBATCH; i0 < p.n_cone_pi; i0 += c.nw * UBATCH) {
-        float2 vv[UBATCH], pb[UBATCH], mm[UBATCH], ss[UBATCH];
+        VF vv[UBATCH], pb[UBATCH], mm[UBATCH], ss[UBATCH];
         int64_t r[UBATCH];
 #pragma unroll
         for (int u = 0; u < UBATCH; u++) {
             const int i = i0 + u;
+            r[u] = 0;
+            vv[u] = mm[u] = ss[u] = pb[u] = vf_fill(0.0f);
             if (i < p.n_cone_pi) {
                 r[u] = (int64_t)__ldg(&p.cone_pi_row[i]) * ldv + c.b;
-                pb[u] = *reinterpret_cast<const float2*>(adj + at(i, c));
-                vv[u] = mm[u] = ss[u] = make_float2(0.0f, 0.0f);
-                if (c.ok0) {
-                    vv[u].x = V[r[u]];
-                    if (adam) { mm[u].x = m[r[u]]; ss[u].x = v[r[u]]; }
-                }
-                if (c.ok1) {
-                    vv[u].y = V[r[u] + 1];
-                    if (adam) { mm[u].y = m[r[u] + 1]; ss[u].y = v[r[u] + 1]; }
+                pb[u] = ActIO<float>::ld(adj + at(i, c));
+#pragma unroll
+                for (int q = 0; q < VEC; q++) {
+                    if (q < c.nvalid) {
+                        vv[u].v[q] = V[r[u] + q];
+                        if (adam) {
+                            mm[u].v[q] = m[r[u] + q];
+                            ss[u].v[q] = v[r[u] + q];
+                        }
+                    }
                 }
             }
         }
 #pragma unroll
         for (int u = 0; u < UBATCH; u++) {
             if (i0 + u >= p.n_cone_pi) continue;
-            if (c.ok0) input_update<UPDATE>(o, V, m, v, gV, r[u], vv[u].x, pb[u].x, mm[u].x, ss[u].x, step_size, bc2s);
-            if (c.ok1) input_update<UPDATE>(o, V, m, v, gV, r[u] + 1, vv[u].y, pb[u].y, mm[u].y, ss[u].y, step_size, bc2s);
+#pragma unroll
+            for (int q = 0; q < VEC; q++)
+                if (q < c.nvalid)
+                    input_update<UPDATE>(o, V, m, v, gV, r[u] + q, vv[u].v[q], pb[u].v[q], mm[u].v[q], ss[u].v[q],
+                                         step_size, bc2s);
         }
     }
     __syncthreads();
+    for (int l = 0; l < p.max_span && l <= p.n_clev; l++) discard_adj_rows(p, l, adj);
 }
 
 // Scratch of tile t: act / adj rows [n_cone][TILE] starting at element t * n_cone * TILE.
 // Dynamic shared memory: warp_stage_bytes<T>() per warp (slots + mbarriers).
 template <typename T>
-__device__ __forceinline__ Stage init_stage(char* smem, const DevPlan& p, const TileCtx& c) {
+__device__ __forceinline__ Stage init_stage(char* smem, const DevPlan& p, float4* gcoef, const TileCtx& c) {
     Stage st = make_stage<T>(smem, p.status, c);
     if (c.lane == 0)
         for (int s = 0; s < NSLOT; s++) mbar_init(st.bar + s, 1);
+    if (threadIdx.x < 16) gcoef[threadIdx.x] = gate_coeffs(threadIdx.x);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     __syncthreads();
     return st;
@@ -459,10 +569,11 @@ template <typename T>
 __global__ void __launch_bounds__(STEP_THREADS, 1) forward_kernel(DevPlan p, const float* V, int64_t ldv, T* act,
                                                                   float* loss, int64_t B) {
     extern __shared__ __align__(128) char smem[];
+    __shared__ float4 gcoef[16];
     const TileCtx c = tile_ctx(B);
-    Stage st = init_stage<T>(smem, p, c);
+    Stage st = init_stage<T>(smem, p, gcoef, c);
     T* a = act + (size_t)blockIdx.x * (size_t)p.n_cone * TILE;
-    tile_forward<T>(p, V, ldv, a, st, c);
+    tile_forward<T>(p, V, ldv, a, st, gcoef, c);
     if (loss) tile_loss<T>(p, a, loss, c);
 }
 
@@ -471,8 +582,9 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) backward_kernel(DevPlan p, co
                                                                    const T* act, float* adj, const float* grad_loss,
                                                                    float* gV, int64_t B) {
     extern __shared__ __align__(128) char smem[];
+    __shared__ float4 gcoef[16];
     const TileCtx c = tile_ctx(B);
-    Stage st = init_stage<T>(smem, p, c);
+    Stage st = init_stage<T>(smem, p, gcoef, c);
     const size_t off = (size_t)blockIdx.x * (size_t)p.n_cone * TILE;
     OptParams o;
     tile_backward<T, false>(p, o, const_cast<float*>(V), nullptr, nullptr, gV, ldv, act + off, adj + off, grad_loss,
@@ -486,8 +598,9 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) steps_kernel(DevPlan p, OptPa
                                                                 int64_t ldv, T* act, float* adj, float* loss,
                                                                 double p1, double p2, int n_steps, int64_t B) {
     extern __shared__ __align__(128) char smem[];
+    __shared__ float4 gcoef[16];
     const TileCtx c = tile_ctx(B);
-    Stage st = init_stage<T>(smem, p, c);
+    Stage st = init_stage<T>(smem, p, gcoef, c);
     const size_t off = (size_t)blockIdx.x * (size_t)p.n_cone * TILE;
     T* a = act + off;
     float* g = adj + off;
@@ -495,7 +608,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) steps_kernel(DevPlan p, OptPa
     for (int s = 0; s < n_steps; s++) {
         p1 *= (double)o.b1;
         p2 *= (double)o.b2;
-        tile_forward<T>(p, V, ldv, a, st, c);
+        tile_forward<T>(p, V, ldv, a, st, gcoef, c);
         if (loss && s == n_steps - 1) tile_loss<T>(p, a, loss, c);
         tile_backward<T, true>(p, o, V, m, v, nullptr, ldv, a, g, nullptr, p1, p2, st, c);
     }
