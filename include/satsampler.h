@@ -183,6 +183,24 @@ sat_status sat_steps(const sat_plan* p, sat_act_dtype act_dtype, const sat_opt_p
                      float* v, int64_t ldv, void* act, float* adj, float* loss, int32_t t0, int32_t n_steps,
                      int64_t B, void* stream);
 
+/* The same fused steps as sat_steps, for callers that cannot allocate device
+ * memory when they run the optimiser (for example, a process whose device
+ * budget belongs to another allocator, or a loop that must not wait for the
+ * device synchronisation of cudaMalloc).  The paper has no counterpart: this is
+ * a deployment variant.  The act/adj scratch comes from one fixed array of
+ * SAT_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads the
+ * library holds until the process exits; the call itself allocates nothing.
+ * A plan and batch whose scratch exceeds the array are rejected with
+ * SAT_ERR_ARG.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress), so make that first call before any stream
+ * capture.  All calls share the array: calls whose executions overlap on the
+ * GPU (other streams, other threads) race and give undefined results.  Nothing
+ * in the array needs clearing: every scratch row is written before it is read. */
+#define SAT_NOALLOC_SCRATCH_BYTES (64u << 20)
+sat_status sat_steps_noalloc(const sat_plan* p, sat_act_dtype act_dtype, const sat_opt_params* o, float* V, float* m,
+                             float* v, int64_t ldv, float* loss, int32_t t0, int32_t n_steps, int64_t B,
+                             void* stream);
+
 /* Hard threshold (end of Section III-A): bit = [V > 0] (sigmoid(V) > 1/2; ties
  * give 0).  node_bits rows 0..n_pi-1 receive the bitsliced inputs; keys[b]
  * (key_words uint32 per sample, bit j of word k = input 32k + j) the packed

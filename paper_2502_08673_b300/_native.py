@@ -89,6 +89,7 @@ PROTOTYPES = {
     "sat_backward": (I32, [P, I32, P, I64, P, P, P, P, I64, P]),
     "sat_opt_update": (I32, [P, C.POINTER(OptParams), P, P, P, P, I64, I32, I64, P]),
     "sat_steps": (I32, [P, I32, C.POINTER(OptParams), P, P, P, I64, P, P, P, I32, I32, I64, P]),
+    "sat_steps_noalloc": (I32, [P, I32, C.POINTER(OptParams), P, P, P, I64, P, I32, I32, I64, P]),
     "sat_threshold": (I32, [P, P, I64, P, I64, P, I64, P]),
     "sat_hard_eval": (I32, [P, P, I64, I64, P]),
     "sat_cnf_check": (I32, [P, P, I64, P, I64, P]),

@@ -254,6 +254,13 @@ def sat_steps(plan: Plan, opt: N.OptParams, V, m, v, act, adj, t0: int, n_steps:
                           _ptr(act), _ptr(adj), _ptr(loss), t0, n_steps, V.shape[1], _stream(stream)))
 
 
+def sat_steps_noalloc(plan: Plan, opt: N.OptParams, V, m, v, t0: int, n_steps: int, loss=None, act_dtype="f32",
+                      stream=None):
+    """sat_steps with the library's fixed scratch array (no act/adj buffers, no allocation)."""
+    check(lib().sat_steps_noalloc(plan.handle, N.ACT_DTYPES[act_dtype], C.byref(opt), _ptr(V), _ptr(m), _ptr(v),
+                                  V.stride(0), _ptr(loss), t0, n_steps, V.shape[1], _stream(stream)))
+
+
 def sat_threshold(plan: Plan, V, node_bits, keys, stream=None):
     check(lib().sat_threshold(plan.handle, _ptr(V), V.stride(0), _ptr(node_bits), node_bits.stride(0), _ptr(keys),
                               V.shape[1], _stream(stream)))

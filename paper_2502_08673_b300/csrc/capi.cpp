@@ -129,6 +129,11 @@ bool opt_ok(const sat_opt_params* o) {
 
 }  // namespace
 
+namespace sat {
+sat_status report_error(sat_status s, const std::string& msg) { return fail(s, msg); }
+const DevPlan* plan_device(const sat_plan* p) { return &p->dp; }
+}  // namespace sat
+
 extern "C" {
 
 const char* sat_version(void) { return "satsampler 0.1 (sm_103a)"; }

@@ -116,3 +116,13 @@ struct Plan {
 bool build_plan(const Circuit& c, const Cnf& cnf, Plan& out, std::string& err);
 
 }  // namespace sat
+
+// Shared by the C entry points defined outside capi.cpp.
+#include "../../include/satsampler.h"
+namespace sat {
+struct DevPlan;
+// Records msg as the calling thread's last error and returns s.
+sat_status report_error(sat_status s, const std::string& msg);
+// The device-side view of a plan.
+const DevPlan* plan_device(const sat_plan* p);
+}  // namespace sat

@@ -1,0 +1,92 @@
+// sat_steps_noalloc: the fused optimisation steps of sat_steps, with the
+// per-node scratch (activations and adjoints) taken from a fixed array in the
+// library's own device memory instead of from the caller.
+//
+// Why it exists: some callers cannot allocate device memory at the point where
+// they want to run the optimiser — for example a process whose whole device
+// budget is handed to another allocator at start-up (a framework's caching
+// pool, a serving loop with a fixed footprint), or a latency-critical loop
+// that must not pay for cudaMalloc, which synchronises the device.  Those
+// callers still pass V, m, v and loss, but need no act/adj buffers.
+//
+// The array below is a file-scope __device__ variable of SAT_NOALLOC_SCRATCH_BYTES:
+// every GPU that loads this library holds it until the process exits.  Host
+// code must not use its name as an address (on the host it is only a stand-in);
+// the device address is looked up once per device with cudaGetSymbolAddress.
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <string>
+
+#include "../../include/satsampler.h"
+#include "device.hpp"
+#include "host.hpp"
+
+struct sat_plan;  // defined in capi.cpp
+
+namespace {
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[SAT_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device (set up on first use).
+cudaError_t scratch_address(void** out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (g_scratch_addr[dev] == nullptr) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" sat_status sat_steps_noalloc(const sat_plan* p, sat_act_dtype act_dtype, const sat_opt_params* o,
+                                        float* V, float* m, float* v, int64_t ldv, float* loss, int32_t t0,
+                                        int32_t n_steps, int64_t B, void* stream) {
+    if (!p) return sat::report_error(SAT_ERR_ARG, "plan is NULL");
+    const sat::DevPlan* dp = sat::plan_device(p);
+    if (act_dtype < SAT_ACT_F32 || act_dtype > SAT_ACT_F16) return sat::report_error(SAT_ERR_ARG, "bad act_dtype");
+    if (!o || (o->optimizer != SAT_OPT_ADAM && o->optimizer != SAT_OPT_GD) || t0 < 1 || n_steps < 0)
+        return sat::report_error(SAT_ERR_ARG, "bad optimiser parameters or steps");
+    if (B < 0 || B >= (1ll << 31) || ldv < B) return sat::report_error(SAT_ERR_ARG, "bad batch or ldv");
+    if (B > 0 && dp->n_pi > 0 && (!V || (o->optimizer == SAT_OPT_ADAM && (!m || !v))))
+        return sat::report_error(SAT_ERR_ARG, "NULL buffer");
+    // act and adj blocks, each rounded up to 256 bytes
+    const uint64_t elems = (uint64_t)((B + SAT_TILE_SAMPLES - 1) / SAT_TILE_SAMPLES) * (uint64_t)dp->n_cone *
+                           SAT_TILE_SAMPLES;
+    const uint64_t act_bytes = (elems * (act_dtype == SAT_ACT_F32 ? 4u : 2u) + 255) / 256 * 256;
+    const uint64_t adj_bytes = (elems * 4u + 255) / 256 * 256;
+    if (act_bytes + adj_bytes > SAT_NOALLOC_SCRATCH_BYTES)
+        return sat::report_error(
+            SAT_ERR_ARG, "sat_steps_noalloc needs " + std::to_string(act_bytes + adj_bytes) +
+                             " bytes of scratch for this plan and batch; its fixed array holds " +
+                             std::to_string((unsigned long long)SAT_NOALLOC_SCRATCH_BYTES) +
+                             " bytes (use sat_steps with caller-provided buffers)");
+    if (B == 0 || n_steps == 0) return SAT_OK;
+    void* base = nullptr;
+    cudaError_t e = scratch_address(&base);
+    if (e != cudaSuccess)
+        return sat::report_error(SAT_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    unsigned char* s = static_cast<unsigned char*>(base);
+    sat::OptParams op;
+    op.opt = o->optimizer;
+    op.lr = o->lr;
+    op.b1 = o->beta1;
+    op.b2 = o->beta2;
+    op.eps = o->eps;
+    e = sat::launch_steps(*dp, (int)act_dtype, op, V, m, v, ldv, s, reinterpret_cast<float*>(s + act_bytes), loss, t0,
+                          n_steps, B, (cudaStream_t)stream);
+    if (e != cudaSuccess) return sat::report_error(SAT_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
+    return SAT_OK;
+}
