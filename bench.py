@@ -39,6 +39,8 @@ WORKLOADS = {
                             batch=65536, steps=500, lr=0.1, init_scale=1.0, act_dtype="bf16"),
     "tseitin80k_bf16": dict(kind="tseitin", n_pi=5000, n_gates=80000, depth=80, n_out=32, seed=1,
                             batch=262144, steps=500, lr=0.1, init_scale=1.0, act_dtype="bf16"),
+    "tseitin80k_f16": dict(kind="tseitin", n_pi=5000, n_gates=80000, depth=80, n_out=32, seed=1,
+                           batch=262144, steps=500, lr=0.1, init_scale=1.0, act_dtype="f16"),
     "planted3sat": dict(kind="planted3sat", n_vars=50, n_clauses=200, seed=1,
                         batch=1024, steps=200, lr=0.1, init_scale=1.0, act_dtype="f32"),
 }
@@ -290,6 +292,8 @@ def main():
     achieved = alg / (kavg / 1e3) / 1e9
     dram_per_sample_step, prof = profile_traffic(args.workload, ad)
 
+    del ws, dedup
+    torch.cuda.empty_cache()
     e2e = None
     if not args.no_e2e:
         # the user-facing call with host inputs: plan upload, rounds, key download

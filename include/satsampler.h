@@ -240,6 +240,23 @@ sat_status sat_dedup_copy_keys(const sat_dedup* d, uint64_t first, uint64_t coun
 sat_status sat_dedup_clear(sat_dedup* d, void* stream);
 void sat_dedup_free(sat_dedup* d);
 
+/* ------------------------------------------------- proposal network ---
+ * Learned proposal (not in the paper; a deployment option of this library):
+ * an MLP maps Gaussian noise to initial logits V0.  Its layers run on the
+ * tensor cores through this BF16 GEMM (tcgen05, FP32 accumulation in tensor
+ * memory) with a fused epilogue:
+ *   D[m][n] = sum_k A[m][k] B[n][k]  (A: [M][lda], B: [N][ldb], bf16, K-major,
+ *                                     16-byte aligned, lda/ldb multiples of 8)
+ *   x = alpha * epi(D + bias[n]),  epi: 0 identity, 1 GELU (erf form; D+bias
+ *   is stored to pre[m][n] when pre != NULL), 2 multiply by GELU'(pre[m][n]).
+ * x goes to any of out_f32 / out_bf16 ([M][ldo]) and out_t_bf16 / out_t_f32
+ * (transposed, [N][ldt]); NULL outputs are skipped.  status (device uint32)
+ * gets bit 3 if a bounded wait expired.  All pointers are device pointers. */
+sat_status sat_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A, int64_t lda, const void* B, int64_t ldb,
+                         const float* bias, int32_t epilogue, float* pre, int64_t ldpre, float alpha, float* out_f32,
+                         void* out_bf16, int64_t ldo, void* out_t_bf16, float* out_t_f32, int64_t ldt,
+                         uint32_t* status, void* stream);
+
 /* -------------------------------------------------------- end to end ---
  * Rounds of: init (or caller logits) -> `steps` fused steps -> threshold ->
  * Boolean pass -> CNF check -> dedup, until n_wanted distinct solutions or

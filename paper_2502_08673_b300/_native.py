@@ -99,6 +99,7 @@ PROTOTYPES = {
     "sat_dedup_copy_keys": (I32, [P, U64, U64, P, P]),
     "sat_dedup_clear": (I32, [P, P]),
     "sat_dedup_free": (None, [P]),
+    "sat_gemm_bf16": (I32, [I32, I32, I32, P, I64, P, I64, P, I32, P, I64, F32, P, P, I64, P, P, I64, P, P]),
     "sat_sample_opts_default": (None, [C.POINTER(SampleOpts)]),
     "sat_sample": (I32, [P, P, C.POINTER(SampleOpts), U64, PP, C.POINTER(SampleStats)]),
     "sat_sample_plan": (I32, [P, P, C.POINTER(SampleOpts), U64, C.POINTER(SampleStats)]),

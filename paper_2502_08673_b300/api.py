@@ -274,6 +274,19 @@ def sat_cnf_check(plan: Plan, node_bits, valid, B: int, stream=None):
     check(lib().sat_cnf_check(plan.handle, _ptr(node_bits), node_bits.stride(0), _ptr(valid), B, _stream(stream)))
 
 
+def sat_gemm_bf16(A, B, bias=None, epilogue=0, pre=None, alpha=1.0, out_f32=None, out_bf16=None, out_t_bf16=None,
+                  out_t_f32=None, status=None, stream=None):
+    """D = A B^T on the tensor cores with the fused epilogue (see satsampler.h)."""
+    M, K = A.shape
+    N = B.shape[0]
+    ldo = (out_f32 if out_f32 is not None else out_bf16).stride(0) if (out_f32 is not None or out_bf16 is not None) else 0
+    ldt = (out_t_bf16 if out_t_bf16 is not None else out_t_f32).stride(0) \
+        if (out_t_bf16 is not None or out_t_f32 is not None) else 0
+    check(lib().sat_gemm_bf16(M, N, K, _ptr(A), A.stride(0), _ptr(B), B.stride(0), _ptr(bias), epilogue, _ptr(pre),
+                              0 if pre is None else pre.stride(0), alpha, _ptr(out_f32), _ptr(out_bf16), ldo,
+                              _ptr(out_t_bf16), _ptr(out_t_f32), ldt, _ptr(status), _stream(stream)))
+
+
 @dataclass
 class Workspace:
     """Device buffers of one sampling round (torch-allocated)."""
