@@ -11,6 +11,7 @@ Contents (each function cites the passage of the paper it restates):
 * ``relax.c``    — FP64 relaxation, l2 loss, adjoint, GD/Adam, threshold, Boolean
                    evaluation, CNF check, Philox4x32-10 (Table 1, Eqs. 5-9).
 * ``sampler``    — orchestration of rounds, verification and deduplication.
+* ``mlp``        — FP64 proposal network: forward, BCE, gradients, IMLE selection.
 """
 from __future__ import annotations
 

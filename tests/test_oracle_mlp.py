@@ -1,0 +1,65 @@
+"""Pins of the proposal-network oracle: closed forms, central differences, brute-force IMLE."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlp as M
+
+
+def test_gelu_closed_forms():
+    assert M.gelu(np.array(0.0)) == 0.0
+    assert abs(M.gelu_grad(np.array(0.0)) - 0.5) < 1e-15
+    x = np.array([-3.0, -0.5, 0.7, 4.0])
+    phi = np.array([0.5 * (1 + math.erf(v / math.sqrt(2))) for v in x])
+    np.testing.assert_allclose(M.gelu(x), x * phi, rtol=1e-14)
+    h = 1e-6
+    np.testing.assert_allclose(M.gelu_grad(x), (M.gelu(x + h) - M.gelu(x - h)) / (2 * h), rtol=1e-8)
+
+
+def test_bce_closed_form():
+    y = np.array([-30.0, -1.0, 0.0, 2.0, 30.0])
+    for t in (0.0, 1.0):
+        p = 1 / (1 + np.exp(-y))
+        direct = -(t * np.log(p) + (1 - t) * np.log1p(-p))
+        ok = np.isfinite(direct)
+        np.testing.assert_allclose(M.bce_terms(y, t)[ok], direct[ok], rtol=1e-10)
+    assert abs(M.bce_terms(np.array(0.0), 1.0) - math.log(2)) < 1e-15
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_gradient_central_differences(seed):
+    n_in, h, n_out, S = 5, 7, 6, 4
+    rng = np.random.default_rng(seed)
+    theta = M.init_params(n_in, h, n_out, seed) * 2.0
+    Z = rng.normal(size=(S, n_in))
+    T = rng.integers(0, 2, (S, n_out)).astype(np.float64)
+    g = M.grad(theta, Z, T, n_in, h, n_out)
+    eps = 1e-6
+    fd = np.zeros_like(theta)
+    for i in range(theta.size):
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += eps
+        tm[i] -= eps
+        fd[i] = (M.loss(tp, Z, T, n_in, h, n_out) - M.loss(tm, Z, T, n_in, h, n_out)) / (2 * eps)
+    assert np.abs(fd - g).max() <= 1e-6 * np.abs(g).max()
+
+
+def test_imle_select_is_brute_force_argmin():
+    n_in, h, n_out, S, K = 4, 6, 5, 3, 8
+    rng = np.random.default_rng(3)
+    theta = M.init_params(n_in, h, n_out, 3)
+    Zc = rng.normal(size=(S * K, n_in))
+    T = rng.integers(0, 2, (S, n_out)).astype(np.float64)
+    choice, d = M.imle_select(theta, Zc, T, K, n_in, h, n_out)
+    for s in range(S):
+        losses = [M.loss(theta, Zc[s * K + k][None], T[s][None], n_in, h, n_out) * n_out for k in range(K)]
+        assert choice[s] == int(np.argmin(losses))
+        np.testing.assert_allclose(d[s * K:(s + 1) * K], losses, rtol=1e-12)
+
+
+def test_param_layout():
+    assert M.n_params(64, 256, 2000) == 64 * 256 + 256 + 256 * 256 + 256 + 2000 * 256 + 2000
+    th = np.arange(M.n_params(2, 3, 4), dtype=float)
+    W1, b1, W2, b2, W3, b3 = M.unpack(th, 2, 3, 4)
+    assert W1.shape == (3, 2) and W1[0, 1] == 1 and b1[0] == 6 and W3.shape == (4, 3) and b3[-1] == th[-1]
