@@ -257,6 +257,45 @@ sat_status sat_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A, int64_t
                          void* out_bf16, int64_t ldo, void* out_t_bf16, float* out_t_f32, int64_t ldt,
                          uint32_t* status, void* stream);
 
+/* The proposal network: z (n_in) -> GELU(W1 z + b1) -> GELU(W2 . + b2) ->
+ * W3 . + b3 = logits of the n_out primary inputs.  FP32 master weights with
+ * BF16 copies; BF16 activations; FP32 accumulation; PyTorch's nn.Linear
+ * initialisation from `seed`.  max_rows bounds every batch the object handles
+ * (inference rows, or training targets x candidates).  Training is implicit
+ * maximum likelihood (IMLE): for each training solution draw K noise vectors,
+ * keep the one whose logits have the least summed binary cross-entropy to the
+ * solution's input bits, and take an Adam step on the mean BCE at the kept
+ * vectors.  Solutions are passed as dedup keys (device uint32 [S][key_words],
+ * bit i = primary input i).  Parameter vector order: W1 [h][n_in], b1, W2
+ * [h][h], b2, W3 [n_out][h], b3. */
+typedef struct sat_mlp sat_mlp;
+sat_status sat_mlp_create(uint32_t n_in, uint32_t n_hidden, uint32_t n_out, int64_t max_rows, uint64_t seed,
+                          sat_mlp** out);
+sat_status sat_mlp_num_params(const sat_mlp* m, uint64_t* n);
+sat_status sat_mlp_get_params(const sat_mlp* m, float* host);            /* host [n_params] */
+sat_status sat_mlp_set_params(sat_mlp* m, const float* host);            /* also resets Adam state */
+/* z [rows][n_in] bf16 ~ N(0,1): Philox4x32-10 counter (row, j, round, 1), Box-Muller. */
+sat_status sat_mlp_draw_noise(sat_mlp* m, uint64_t seed, uint32_t round, void* z, int64_t rows, void* stream);
+/* V[i][b] = tau * logit_i(z_b) for rows b < rows (V: float [n_out][ldv], the sampler's layout). */
+sat_status sat_mlp_forward(sat_mlp* m, const void* z, int64_t rows, float tau, float* V, int64_t ldv, void* stream);
+/* Draw noise and write tau * logits into V: the proposal's initial logits for a round. */
+sat_status sat_mlp_propose(sat_mlp* m, uint64_t seed, uint32_t round, float tau, float* V, int64_t ldv, int64_t B,
+                           void* stream);
+/* IMLE selection: candidate k of target s is row s*K+k of zc; dist[s*K+k] =
+ * summed BCE (device, nullable), choice[s] = first argmin (device, nullable). */
+sat_status sat_mlp_imle_select(sat_mlp* m, const void* zc, const uint32_t* keys, int32_t key_words, int64_t S,
+                               int32_t K, float* dist, int32_t* choice, void* stream);
+/* Mean BCE and its gradient at noise rows z [S][n_in] (device bf16); loss_host
+ * and grad_host ([n_params]) are host pointers (nullable).  Synchronises. */
+sat_status sat_mlp_loss_grad(sat_mlp* m, const void* z, const uint32_t* keys, int32_t key_words, int64_t S,
+                             float* loss_host, float* grad_host, void* stream);
+/* One IMLE step with K candidates per target and Adam (lr, PyTorch defaults otherwise). */
+sat_status sat_mlp_train_step(sat_mlp* m, const uint32_t* keys, int32_t key_words, int64_t S, int32_t K, float lr,
+                              uint64_t seed, uint32_t round, float* loss_host, void* stream);
+/* Status word of the network's kernels (bit 3: a bounded GEMM wait expired). */
+sat_status sat_mlp_status(const sat_mlp* m, uint32_t* status);
+void sat_mlp_free(sat_mlp* m);
+
 /* -------------------------------------------------------- end to end ---
  * Rounds of: init (or caller logits) -> `steps` fused steps -> threshold ->
  * Boolean pass -> CNF check -> dedup, until n_wanted distinct solutions or

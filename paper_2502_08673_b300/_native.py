@@ -100,6 +100,18 @@ PROTOTYPES = {
     "sat_dedup_clear": (I32, [P, P]),
     "sat_dedup_free": (None, [P]),
     "sat_gemm_bf16": (I32, [I32, I32, I32, P, I64, P, I64, P, I32, P, I64, F32, P, P, I64, P, P, I64, P, P]),
+    "sat_mlp_create": (I32, [U32, U32, U32, I64, U64, PP]),
+    "sat_mlp_num_params": (I32, [P, C.POINTER(U64)]),
+    "sat_mlp_get_params": (I32, [P, P]),
+    "sat_mlp_set_params": (I32, [P, P]),
+    "sat_mlp_draw_noise": (I32, [P, U64, U32, P, I64, P]),
+    "sat_mlp_forward": (I32, [P, P, I64, F32, P, I64, P]),
+    "sat_mlp_propose": (I32, [P, U64, U32, F32, P, I64, I64, P]),
+    "sat_mlp_imle_select": (I32, [P, P, P, I32, I64, I32, P, P, P]),
+    "sat_mlp_loss_grad": (I32, [P, P, P, I32, I64, P, P, P]),
+    "sat_mlp_train_step": (I32, [P, P, I32, I64, I32, F32, U64, U32, P, P]),
+    "sat_mlp_status": (I32, [P, C.POINTER(U32)]),
+    "sat_mlp_free": (None, [P]),
     "sat_sample_opts_default": (None, [C.POINTER(SampleOpts)]),
     "sat_sample": (I32, [P, P, C.POINTER(SampleOpts), U64, PP, C.POINTER(SampleStats)]),
     "sat_sample_plan": (I32, [P, P, C.POINTER(SampleOpts), U64, C.POINTER(SampleStats)]),

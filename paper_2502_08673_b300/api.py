@@ -200,6 +200,77 @@ class Solutions(_Handle):
         return bits[:, : self.n_vars]
 
 
+class Mlp(_Handle):
+    """The learned proposal network (see sat_mlp_* in include/satsampler.h)."""
+    _free = "sat_mlp_free"
+
+    @classmethod
+    def create(cls, n_in: int, n_hidden: int, n_out: int, max_rows: int, seed: int = 0) -> "Mlp":
+        h = C.c_void_p()
+        check(lib().sat_mlp_create(n_in, n_hidden, n_out, max_rows, seed, C.byref(h)))
+        m = cls(h)
+        m.n_in, m.n_hidden, m.n_out, m.max_rows = n_in, n_hidden, n_out, max_rows
+        n = C.c_uint64()
+        check(lib().sat_mlp_num_params(h, C.byref(n)))
+        m.n_params = n.value
+        return m
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(self.n_params, np.float32)
+        check(lib().sat_mlp_get_params(self._h, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def set_params(self, theta):
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        assert th.size == self.n_params
+        check(lib().sat_mlp_set_params(self._h, th.ctypes.data_as(C.c_void_p)))
+
+    def draw_noise(self, rows: int, seed: int, round_: int = 0, device="cuda", stream=None):
+        import torch
+        z = torch.empty((rows, self.n_in), dtype=torch.bfloat16, device=device)
+        check(lib().sat_mlp_draw_noise(self._h, seed, round_, _ptr(z), rows, _stream(stream)))
+        return z
+
+    def forward(self, z, tau: float = 1.0, V=None, stream=None):
+        """tau * logits as [n_out, rows] float32 (the sampler's V layout)."""
+        import torch
+        rows = z.shape[0]
+        if V is None:
+            V = torch.empty((self.n_out, rows), dtype=torch.float32, device=z.device)
+        check(lib().sat_mlp_forward(self._h, _ptr(z), rows, tau, _ptr(V), V.stride(0), _stream(stream)))
+        return V
+
+    def propose(self, V, seed: int, round_: int, tau: float = 1.0, stream=None):
+        check(lib().sat_mlp_propose(self._h, seed, round_, tau, _ptr(V), V.stride(0), V.shape[1], _stream(stream)))
+
+    def imle_select(self, zc, keys, S: int, K: int, stream=None):
+        import torch
+        dist = torch.empty(S * K, dtype=torch.float32, device=zc.device)
+        choice = torch.empty(S, dtype=torch.int32, device=zc.device)
+        check(lib().sat_mlp_imle_select(self._h, _ptr(zc), _ptr(keys), keys.shape[1], S, K, _ptr(dist), _ptr(choice),
+                                        _stream(stream)))
+        return dist, choice
+
+    def loss_grad(self, z, keys, stream=None):
+        S = z.shape[0]
+        loss = C.c_float()
+        g = np.zeros(self.n_params, np.float32)
+        check(lib().sat_mlp_loss_grad(self._h, _ptr(z), _ptr(keys), keys.shape[1], S, C.byref(loss),
+                                      g.ctypes.data_as(C.c_void_p), _stream(stream)))
+        return loss.value, g
+
+    def train_step(self, keys, S: int, K: int, lr: float, seed: int, round_: int, stream=None) -> float:
+        loss = C.c_float()
+        check(lib().sat_mlp_train_step(self._h, _ptr(keys), keys.shape[1], S, K, lr, seed, round_, C.byref(loss),
+                                       _stream(stream)))
+        return loss.value
+
+    def status(self) -> int:
+        v = C.c_uint32()
+        check(lib().sat_mlp_status(self._h, C.byref(v)))
+        return v.value
+
+
 # --------------------------------------------------------- kernel calls ---
 def opt_params(optimizer="adam", lr=0.1, beta1=0.9, beta2=0.999, eps=1e-8) -> N.OptParams:
     return N.OptParams(N.OPTIMIZERS[optimizer], lr, beta1, beta2, eps)

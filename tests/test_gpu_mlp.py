@@ -1,0 +1,121 @@
+"""Proposal network on the GPU (tcgen05 GEMMs) against the FP64 oracle.
+
+The GPU rounds activations (and the output gradient) to BF16 and accumulates
+in FP32; the oracle runs in FP64 on the same BF16-rounded weights and noise.
+Bounds: logits within 4 * 2^-8 of the magnitude sum |H2| |W3|^T + |b3| (two
+BF16 roundings feed the last layer); gradients within 3e-2 of the largest
+gradient entry of their block, with cosine similarity > 0.999 (the backward adds
+roundings of dY and of both hidden-layer adjoints).
+"""
+import numpy as np
+import pytest
+
+from oracle import mlp as M
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _bf16(x):
+    return torch.tensor(np.asarray(x, dtype=np.float32)).to(torch.bfloat16).double().numpy()
+
+
+def _rounded_theta(theta, n_in, h, n_out):
+    """Weights as the GPU uses them (bf16), biases as they are (fp32)."""
+    W1, b1, W2, b2, W3, b3 = M.unpack(theta, n_in, h, n_out)
+    return np.concatenate([_bf16(W1).ravel(), b1, _bf16(W2).ravel(), b2, _bf16(W3).ravel(), b3])
+
+
+def _keys(bits):
+    S, n = bits.shape
+    kw = (n + 31) // 32
+    words = np.zeros((S, kw), np.uint32)
+    for i in range(n):
+        words[:, i // 32] |= bits[:, i].astype(np.uint32) << np.uint32(i % 32)
+    return torch.tensor(words.view(np.int32))
+
+
+@pytest.mark.parametrize("n_out", [64, 200, 2000])
+def test_forward_matches_oracle(gpu, n_out):
+    import paper_2502_08673_b300 as P
+    n_in, h, R = 64, 256, 300
+    mlp = P.Mlp.create(n_in, h, n_out, max_rows=512, seed=3)
+    theta = mlp.params().astype(np.float64)
+    z = mlp.draw_noise(R, seed=11)
+    V = mlp.forward(z, tau=1.5)
+    torch.cuda.synchronize()
+    assert mlp.status() == 0
+    zr = z.double().cpu().numpy()
+    th = _rounded_theta(theta, n_in, h, n_out)
+    y, (_, p1, h1, p2, h2) = M.forward(th, zr, n_in, h, n_out)
+    W3 = M.unpack(th, n_in, h, n_out)[4]
+    mag = np.abs(h2) @ np.abs(W3).T + np.abs(theta[-n_out:])
+    got = V.cpu().double().numpy().T / 1.5
+    assert (np.abs(got - y) <= 4 * 2 ** -8 * mag + 1e-6).all(), float(np.abs(got - y).max())
+    # the noise is standard normal (moments) and reproducible
+    zz = mlp.draw_noise(20000, seed=11).float()
+    assert abs(zz.mean().item()) < 0.01 and abs(zz.std().item() - 1) < 0.01
+    assert torch.equal(mlp.draw_noise(R, seed=11), z)
+
+
+def test_loss_and_gradient_match_oracle(gpu):
+    import paper_2502_08673_b300 as P
+    n_in, h, n_out, S = 64, 256, 200, 384
+    mlp = P.Mlp.create(n_in, h, n_out, max_rows=1024, seed=5)
+    theta = mlp.params().astype(np.float64)
+    rng = np.random.default_rng(0)
+    bits = rng.integers(0, 2, (S, n_out))
+    keys = _keys(bits).to(gpu)
+    z = mlp.draw_noise(S, seed=2)
+    loss, g = mlp.loss_grad(z, keys)
+    th = _rounded_theta(theta, n_in, h, n_out)
+    zr = z.double().cpu().numpy()
+    T = bits.astype(np.float64)
+    assert abs(loss - M.loss(th, zr, T, n_in, h, n_out)) < 2e-3 * abs(loss) + 1e-6
+    gref = M.grad(th, zr, T, n_in, h, n_out)
+    sizes = [h * n_in, h, h * h, h, n_out * h, n_out]
+    o = 0
+    for sz in sizes:
+        a, b = g[o:o + sz].astype(np.float64), gref[o:o + sz]
+        assert np.abs(a - b).max() <= 3e-2 * np.abs(b).max(), (o, np.abs(a - b).max(), np.abs(b).max())
+        assert a @ b / (np.linalg.norm(a) * np.linalg.norm(b)) > 0.999
+        o += sz
+    assert mlp.status() == 0
+
+
+def test_imle_selection_matches_oracle(gpu):
+    import paper_2502_08673_b300 as P
+    n_in, h, n_out, S, K = 64, 256, 120, 40, 16
+    mlp = P.Mlp.create(n_in, h, n_out, max_rows=S * K, seed=8)
+    theta = mlp.params().astype(np.float64)
+    rng = np.random.default_rng(1)
+    bits = rng.integers(0, 2, (S, n_out))
+    zc = mlp.draw_noise(S * K, seed=4)
+    dist, choice = mlp.imle_select(zc, _keys(bits).to(gpu), S, K)
+    torch.cuda.synchronize()
+    th = _rounded_theta(theta, n_in, h, n_out)
+    cref, dref = M.imle_select(th, zc.double().cpu().numpy(), bits.astype(np.float64), K, n_in, h, n_out)
+    d = dist.cpu().double().numpy()
+    tol = 2e-3 * np.abs(dref) + 1e-3
+    assert (np.abs(d - dref) <= tol).all()
+    ch = choice.cpu().numpy()
+    for s in range(S):
+        row = dref[s * K:(s + 1) * K]
+        # the kernel's pick is the oracle's argmin, or ties with it within the distance tolerance
+        assert ch[s] == cref[s] or row[ch[s]] - row[cref[s]] <= 2 * tol[s * K + cref[s]]
+
+
+def test_imle_training_reduces_loss(gpu):
+    import paper_2502_08673_b300 as P
+    n_in, h, n_out, S, K = 64, 256, 96, 256, 8
+    mlp = P.Mlp.create(n_in, h, n_out, max_rows=S * K, seed=1)
+    rng = np.random.default_rng(2)
+    # targets drawn from two prototypes with 5% noise: a learnable distribution
+    proto = rng.integers(0, 2, (2, n_out))
+    bits = proto[rng.integers(0, 2, S)] ^ (rng.random((S, n_out)) < 0.05)
+    keys = _keys(bits).to(gpu)
+    losses = [mlp.train_step(keys, S, K, lr=3e-3, seed=7, round_=r) for r in range(60)]
+    torch.cuda.synchronize()
+    assert mlp.status() == 0
+    assert np.isfinite(losses).all()
+    assert np.mean(losses[-5:]) < 0.5 * np.mean(losses[:5])
