@@ -47,11 +47,54 @@ WORKLOADS = {
 ACT_BYTES = {"f32": 4, "bf16": 2, "f16": 2}
 
 
-def instance_text(w):
+def instance_text(w, planted_seed=None):
     from workloads import tseitin_random_circuit, planted_3sat
     if w["kind"] == "tseitin":
-        return tseitin_random_circuit(w["n_pi"], w["n_gates"], w["depth"], w["n_out"], seed=w["seed"]).dimacs()
+        return tseitin_random_circuit(w["n_pi"], w["n_gates"], w["depth"], w["n_out"], seed=w["seed"],
+                                      planted_seed=planted_seed).dimacs()
     return planted_3sat(w["n_vars"], w["n_clauses"], w["seed"]).dimacs()
+
+
+def train_proposal(P, torch, plan, w, mode, B, opt, ad, log, train_steps=0, rounds=0):
+    """Train the proposal network on distinct solutions of the plain sampler (untimed).
+
+    mode "same": solutions of the benchmarked instance itself (rounds on Philox
+    streams disjoint from the timed ones).  mode "heldout": solutions of 16
+    instances of the same topology with other planted inputs (planted seeds
+    1..16); the benchmarked instance (planted seed 17) is never seen.
+    """
+    t0 = time.perf_counter()
+    texts = [None] if mode == "same" else [instance_text(w, planted_seed=k) for k in range(1, 17)]
+    rounds_per = rounds or (4 if mode == "same" else 2)
+    keys = []
+    for ti, text in enumerate(texts):
+        if text is None:
+            p2 = plan
+        else:
+            c2 = P.Cnf.from_dimacs(text)
+            p2 = P.Plan.create(P.Circuit.build(c2), c2)
+        ws2 = P.new_workspace(p2, B, ad)
+        dd2 = P.Dedup.create(p2, max_keys=B * rounds_per, max_batch=B)
+        for r in range(rounds_per):
+            P.run_round(p2, ws2, opt, w["collect_steps"], seed=1, round_=(1 << 28) + ti * 64 + r,
+                        init_scale=w["init_scale"], dedup=dd2)
+        keys.append(dd2.keys())
+        del ws2, dd2
+    keys = torch.tensor(np.concatenate(keys).view(np.int32), device="cuda")
+    n = keys.shape[0]
+    S, K = 4096, 16
+    mlp = P.Mlp.create(64, 256, plan.info["n_pi"], max_rows=max(B, S * K), seed=0)
+    steps = train_steps or max(64, min(512, 2 * n // S))
+    g = torch.Generator(device="cuda").manual_seed(0)
+    losses = []
+    for it in range(steps):
+        idx = torch.randint(0, n, (S,), device="cuda", generator=g)
+        losses.append(mlp.train_step(keys[idx].contiguous(), S, K, lr=1e-3, seed=2, round_=it))
+    torch.cuda.synchronize()
+    log.update({"proposal_mode": mode, "proposal_training_solutions": int(n), "proposal_train_steps": steps,
+                "proposal_loss_first": float(np.mean(losses[:8])), "proposal_loss_last": float(np.mean(losses[-8:])),
+                "proposal_setup_s": time.perf_counter() - t0})
+    return mlp
 
 
 def algorithmic_bytes_per_step(info, B, act_dtype):
@@ -206,8 +249,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-samples", type=int, default=16)
+    ap.add_argument("--proposal", default="none", choices=["none", "same", "heldout"],
+                    help="initial logits from the learned proposal (trained untimed) instead of N(0,1)")
+    ap.add_argument("--tau", type=float, default=1.0)
+    ap.add_argument("--proposal-steps", type=int, default=0,
+                    help="optimisation steps per round when starting from the proposal (default: the workload's)")
+    ap.add_argument("--proposal-train-steps", type=int, default=0, help="IMLE steps (default: 2 epochs, 64..512)")
+    ap.add_argument("--proposal-rounds", type=int, default=0, help="plain rounds per training instance")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
+    w["collect_steps"] = w["steps"]  # training data for the proposal always comes from full-length rounds
     if args.batch:
         w["batch"] = args.batch
     if args.gd_steps:
@@ -226,7 +277,7 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    text = instance_text(w)
+    text = instance_text(w, planted_seed=17 if args.proposal == "heldout" else None)
     cnf = P.Cnf.from_dimacs(text)
     t0 = time.perf_counter()
     circ = P.Circuit.build(cnf)
@@ -237,17 +288,27 @@ def main():
     opt = P.opt_params("adam", lr=w["lr"])
     ws = P.new_workspace(plan, B, ad)
     n_rounds = args.warmup + args.steps
-    dedup = P.Dedup.create(plan, max_keys=B * (n_rounds + 1), max_batch=B)
+    dedup = P.Dedup.create(plan, max_keys=B * (n_rounds + 1 + (args.steps if args.proposal != "none" else 0)),
+                           max_batch=B)
     stream = torch.cuda.current_stream()
     round_base = rank << 20
 
-    def one_round(k, ev=None):
-        P.sat_init_normal(plan, ws.V, seed=0, round_=round_base + k, scale=w["init_scale"])
+    prop_log = {}
+    mlp = (train_proposal(P, torch, plan, w, args.proposal, B, opt, ad, prop_log, args.proposal_train_steps,
+                          args.proposal_rounds) if args.proposal != "none" else None)
+    prop_steps = args.proposal_steps or steps
+
+    def one_round(k, ev=None, use_mlp=True):
+        if mlp is not None and use_mlp:
+            mlp.propose(ws.V, seed=0, round_=round_base + k, tau=args.tau)
+        else:
+            P.sat_init_normal(plan, ws.V, seed=0, round_=round_base + k, scale=w["init_scale"])
         ws.m.zero_()
         ws.v.zero_()
         if ev is not None:
             ev[0].record(stream)
-        P.sat_steps(plan, opt, ws.V, ws.m, ws.v, ws.act, ws.adj, 1, steps, act_dtype=ad)
+        P.sat_steps(plan, opt, ws.V, ws.m, ws.v, ws.act, ws.adj, 1, prop_steps if (mlp is not None and use_mlp) else steps,
+                    act_dtype=ad)
         if ev is not None:
             ev[1].record(stream)
         P.sat_threshold(plan, ws.V, ws.bits, ws.keys)
@@ -285,13 +346,29 @@ def main():
         dist.all_reduce(cnt)
         t_max, uniq_all, valid_all = float(tt.item()), int(cnt[0].item()), int(cnt[1].item())
     value = uniq_all / (t_max / 1e3)
-    gate_evals = info["n_cone_gates"] * B * steps * args.steps * world
+    run_steps = prop_steps if mlp is not None else steps
+    gate_evals = info["n_cone_gates"] * B * run_steps * args.steps * world
     peak, peak_kind = measured_peaks()
-    alg = algorithmic_bytes_per_step(info, B, ad) * steps
+    alg = algorithmic_bytes_per_step(info, B, ad) * run_steps
     kavg = statistics.mean(kernel_ms)
     achieved = alg / (kavg / 1e3) / 1e9
     dram_per_sample_step, prof = profile_traffic(args.workload, ad)
 
+    plain_cmp = None
+    if mlp is not None:
+        # the plain form on the same instance, same batch and steps, fresh streams
+        before_p = dedup.count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        vp = 0
+        e0.record(stream)
+        for k in range(args.steps):
+            one_round(n_rounds + 64 + k, use_mlp=False)
+            vp += int(P.valid_mask(ws.valid, B).sum())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tp = e0.elapsed_time(e1)
+        plain_cmp = {"value": (dedup.count() - before_p) / (tp / 1e3), "valid_fraction": vp / (B * args.steps),
+                     "ms_per_step": tp / args.steps}
     del ws, dedup
     torch.cuda.empty_cache()
     e2e = None
@@ -343,6 +420,10 @@ def main():
             "cpu_baseline": cpu,
             "e2e": e2e,
         }
+        if mlp is not None:
+            line["config"]["proposal"] = {"mode": args.proposal, "tau": args.tau, "steps_per_round": prop_steps,
+                                          **prop_log}
+            line["plain_same_run"] = plain_cmp
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

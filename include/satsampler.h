@@ -65,6 +65,7 @@ typedef struct sat_circuit sat_circuit;
 typedef struct sat_plan sat_plan;
 typedef struct sat_dedup sat_dedup;
 typedef struct sat_solutions sat_solutions;
+typedef struct sat_mlp sat_mlp;
 
 /* Library version string and the last error of the calling thread. */
 const char* sat_version(void);
@@ -268,7 +269,6 @@ sat_status sat_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A, int64_t
  * vectors.  Solutions are passed as dedup keys (device uint32 [S][key_words],
  * bit i = primary input i).  Parameter vector order: W1 [h][n_in], b1, W2
  * [h][h], b2, W3 [n_out][h], b3. */
-typedef struct sat_mlp sat_mlp;
 sat_status sat_mlp_create(uint32_t n_in, uint32_t n_hidden, uint32_t n_out, int64_t max_rows, uint64_t seed,
                           sat_mlp** out);
 sat_status sat_mlp_num_params(const sat_mlp* m, uint64_t* n);
@@ -297,10 +297,10 @@ sat_status sat_mlp_status(const sat_mlp* m, uint32_t* status);
 void sat_mlp_free(sat_mlp* m);
 
 /* -------------------------------------------------------- end to end ---
- * Rounds of: init (or caller logits) -> `steps` fused steps -> threshold ->
- * Boolean pass -> CNF check -> dedup, until n_wanted distinct solutions or
- * max_rounds.  Round r draws its initial logits with round counter
- * first_round + r.  Returns SAT_PARTIAL (with what was found) when the budget
+ * Rounds of: init (or caller logits, or the proposal network) -> `steps`
+ * fused steps -> threshold -> Boolean pass -> CNF check -> dedup, until
+ * n_wanted distinct solutions or max_rounds.  Round r draws its initial logits
+ * (or the proposal's noise) with round counter first_round + r.  Returns SAT_PARTIAL (with what was found) when the budget
  * ends first. */
 typedef struct sat_sample_opts {
     int64_t batch;
@@ -315,6 +315,8 @@ typedef struct sat_sample_opts {
     const float* init_logits;   /* nullable device [n_pi][init_ld]: used instead of init for round 0 */
     int64_t init_ld;
     void* stream;
+    sat_mlp* proposal;          /* nullable: initial logits from the proposal network (max_rows >= batch) */
+    float proposal_tau;         /* scale of the proposal's logits */
 } sat_sample_opts;
 
 typedef struct sat_sample_stats {

@@ -53,7 +53,8 @@ class SampleOpts(C.Structure):
     _fields_ = [("batch", C.c_int64), ("steps", C.c_int32), ("max_rounds", C.c_int32), ("opt", OptParams),
                 ("seed", C.c_uint64), ("first_round", C.c_uint32), ("init_scale", C.c_float),
                 ("act_dtype", C.c_int32), ("steps_per_launch", C.c_int32), ("init_logits", C.c_void_p),
-                ("init_ld", C.c_int64), ("stream", C.c_void_p)]
+                ("init_ld", C.c_int64), ("stream", C.c_void_p), ("proposal", C.c_void_p),
+                ("proposal_tau", C.c_float)]
 
 
 class SampleStats(C.Structure):

@@ -387,12 +387,16 @@ def new_workspace(plan: Plan, B: int, act_dtype: str = "f32", device="cuda") -> 
 
 
 def run_round(plan: Plan, ws: Workspace, opt: N.OptParams, steps: int, seed: int, round_: int,
-              init_scale: float = 1.0, dedup: Dedup | None = None, init_logits=None, stream=None):
-    """One round on device-resident buffers: init, steps, threshold, Boolean pass, CNF check, dedup."""
-    if init_logits is None:
-        sat_init_normal(plan, ws.V, seed, round_, init_scale, stream)
-    else:
+              init_scale: float = 1.0, dedup: Dedup | None = None, init_logits=None, proposal: "Mlp | None" = None,
+              tau: float = 1.0, stream=None):
+    """One round on device-resident buffers: init (Philox, caller logits or the
+    proposal network), steps, threshold, Boolean pass, CNF check, dedup."""
+    if init_logits is not None:
         ws.V.copy_(init_logits)
+    elif proposal is not None:
+        proposal.propose(ws.V, seed, round_, tau, stream)
+    else:
+        sat_init_normal(plan, ws.V, seed, round_, init_scale, stream)
     ws.m.zero_()
     ws.v.zero_()
     if steps > 0:
@@ -413,7 +417,7 @@ def valid_mask(valid_words, B: int) -> np.ndarray:
 
 def sample(circuit: Circuit, cnf: Cnf, n_wanted: int, batch=1024, steps=200, max_rounds=1, optimizer="adam",
            lr=0.1, beta1=0.9, beta2=0.999, eps=1e-8, seed=0, first_round=0, init_scale=1.0, act_dtype="f32",
-           steps_per_launch=0, stream=None):
+           steps_per_launch=0, proposal: "Mlp | None" = None, tau: float = 1.0, stream=None):
     """End to end from host objects (the C call sat_sample)."""
     o = N.SampleOpts()
     lib().sat_sample_opts_default(C.byref(o))
@@ -422,6 +426,8 @@ def sample(circuit: Circuit, cnf: Cnf, n_wanted: int, batch=1024, steps=200, max
     o.seed, o.first_round, o.init_scale = seed, first_round, init_scale
     o.act_dtype, o.steps_per_launch = N.ACT_DTYPES[act_dtype], steps_per_launch
     o.stream = None if stream is None else stream.cuda_stream
+    o.proposal = None if proposal is None else proposal.handle
+    o.proposal_tau = tau
     h = C.c_void_p()
     st = N.SampleStats()
     status = check(lib().sat_sample(circuit.handle, cnf.handle, C.byref(o), n_wanted, C.byref(h), C.byref(st)),

@@ -594,6 +594,8 @@ void sat_sample_opts_default(sat_sample_opts* o) {
     o->init_logits = nullptr;
     o->init_ld = 0;
     o->stream = nullptr;
+    o->proposal = nullptr;
+    o->proposal_tau = 1.0f;
 }
 
 namespace {
@@ -664,6 +666,10 @@ sat_status sat_sample_plan(const sat_plan* p, sat_dedup* d, const sat_sample_opt
         CK(cudaEventRecord(ev[0], str));
         if (r == 0 && o->init_logits) {
             CK(cudaMemcpy2DAsync(w.V, B * 4, o->init_logits, o->init_ld * 4, B * 4, npi, cudaMemcpyDeviceToDevice, str));
+        } else if (o->proposal) {
+            if ((s = sat_mlp_propose(o->proposal, o->seed, o->first_round + (uint32_t)r, o->proposal_tau, w.V, B, B,
+                                     o->stream)) != SAT_OK)
+                return s;
         } else {
             CK(sat::launch_init_normal(dp, o->seed, o->first_round + (uint32_t)r, o->init_scale, w.V, B, B, str));
         }
