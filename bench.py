@@ -236,6 +236,31 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+def run_mlp(args, w):
+    """Proposal network inference, 64 -> 256 -> 256 -> n_PI at the workload's batch (tensor-core GEMMs)."""
+    import torch
+    import paper_2502_08673_b300 as P
+    B, n_out = w["batch"], w.get("n_pi", w.get("n_vars"))
+    mlp = P.Mlp.create(64, 256, n_out, max_rows=B, seed=0)
+    V = torch.empty((n_out, B), dtype=torch.float32, device="cuda")
+    for k in range(args.warmup):
+        mlp.propose(V, seed=0, round_=k)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(args.steps):
+        mlp.propose(V, seed=0, round_=100 + k)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    flops = 2.0 * B * (64 * 256 + 256 * 256 + 256 * n_out)
+    peak = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()).get("bf16_tflops", 1800.0) \
+        if (ROOT / "MEASURED_PEAKS.json").exists() else 1800.0
+    print(json.dumps({"metric": "proposal inference (noise + 3 GEMM layers)", "batch": B, "n_out": n_out,
+                      "ms_per_call": ms, "tflops": flops / (ms / 1e3) / 1e12,
+                      "frac_of_bf16_peak": flops / (ms / 1e3) / 1e12 / peak, "status": mlp.status()}))
+
+
 # --------------------------------------------------------------------------
 def main():
     ap = argparse.ArgumentParser()
@@ -256,6 +281,8 @@ def main():
                     help="optimisation steps per round when starting from the proposal (default: the workload's)")
     ap.add_argument("--proposal-train-steps", type=int, default=0, help="IMLE steps (default: 2 epochs, 64..512)")
     ap.add_argument("--proposal-rounds", type=int, default=0, help="plain rounds per training instance")
+    ap.add_argument("--mlp", action="store_true",
+                    help="time only the proposal network's inference GEMMs (tcgen05) at the workload's batch")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     w["collect_steps"] = w["steps"]  # training data for the proposal always comes from full-length rounds
@@ -265,6 +292,8 @@ def main():
         w["steps"] = args.gd_steps
     if args.impl == "reference":
         return run_reference(args, w)
+    if args.mlp:
+        return run_mlp(args, w)
 
     import torch
     import torch.distributed as dist

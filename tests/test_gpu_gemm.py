@@ -70,3 +70,46 @@ def test_gemm_epilogues(gpu):
     gp = 0.5 * (1 + erf(p / math.sqrt(2))) + p * np.exp(-0.5 * p * p) / math.sqrt(2 * math.pi)
     assert (np.abs(out2.cpu().double().numpy() - ref * gp) <= 1.5 * tol + 1e-6).all()
     assert int(st.item()) == 0
+
+
+@pytest.mark.parametrize("M,N,K,out", [(70001, 300, 136, "f32"), (20000, 2000, 256, "t_f32"),
+                                       (65536, 256, 64, "bf16"), (9000, 520, 36, "f32")])
+def test_gemm_persistent_many_tiles(gpu, M, N, K, out):
+    """Far more tiles than SMs (accumulator and stage rings wrap many times), ragged M/N/K
+    (K = 36 leaves part of an 8-column TMA box and a whole box out of range); rows sampled."""
+    import paper_2502_08673_b300 as P
+    g = torch.Generator().manual_seed(M + N + K)
+    A, B = _rand((M, K), g), _rand((N, K), g)
+    bias = torch.randn(N, generator=g)
+    st = torch.zeros(1, dtype=torch.int32, device=gpu)
+    kw = {}
+    if out == "f32":
+        o = torch.full((M, N), float("nan"), device=gpu)
+        kw["out_f32"] = o
+    elif out == "bf16":
+        o = torch.zeros((M, N), dtype=torch.bfloat16, device=gpu)
+        kw["out_bf16"] = o
+    else:
+        o = torch.full((N, M), float("nan"), device=gpu)
+        kw["out_t_f32"] = o
+    ld = (K + 7) // 8 * 8  # leading dimensions must be multiples of 8; K itself need not be
+    dA = torch.zeros((M, ld), dtype=torch.bfloat16, device=gpu)
+    dB = torch.zeros((N, ld), dtype=torch.bfloat16, device=gpu)
+    dA[:, :K] = A.to(gpu)
+    dB[:, :K] = B.to(gpu)
+    if ld > K:  # the padding holds garbage that must not be read
+        dA[:, K:] = 1e4
+        dB[:, K:] = 1e4
+    P.sat_gemm_bf16(dA[:, :K], dB[:, :K], bias=bias.to(gpu), status=st, **kw)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    rows = torch.cat([torch.arange(0, 130), torch.randint(0, M, (400,), generator=g), torch.arange(M - 130, M)])
+    got = (o.t() if out == "t_f32" else o)[rows.to(gpu)].cpu().double().numpy()
+    a = A[rows].double().numpy()
+    ref = a @ B.double().numpy().T + bias.double().numpy()[None, :]
+    mag = np.abs(a) @ np.abs(B.double().numpy()).T + np.abs(bias.double().numpy())[None, :]
+    tol = 1e-5 * mag + 1e-6
+    if out == "bf16":
+        tol = 2 ** -8 * np.abs(ref) + tol
+    d = np.abs(got - ref)
+    assert (d <= tol).all(), float(d.max())
