@@ -274,7 +274,8 @@ sat_status sat_mlp_create(uint32_t n_in, uint32_t n_hidden, uint32_t n_out, int6
 sat_status sat_mlp_num_params(const sat_mlp* m, uint64_t* n);
 sat_status sat_mlp_get_params(const sat_mlp* m, float* host);            /* host [n_params] */
 sat_status sat_mlp_set_params(sat_mlp* m, const float* host);            /* also resets Adam state */
-/* z [rows][n_in] bf16 ~ N(0,1): Philox4x32-10 counter (row, j, round, 1), Box-Muller. */
+/* z [rows][n_in] bf16 ~ N(0,1): the Philox4x32-10 block at counter (row, c, round, 1) gives
+ * z[row][4c .. 4c+3] as two Box-Muller pairs (cos, sin) of its words (x, y) and (z, w). */
 sat_status sat_mlp_draw_noise(sat_mlp* m, uint64_t seed, uint32_t round, void* z, int64_t rows, void* stream);
 /* V[i][b] = tau * logit_i(z_b) for rows b < rows (V: float [n_out][ldv], the sampler's layout). */
 sat_status sat_mlp_forward(sat_mlp* m, const void* z, int64_t rows, float tau, float* V, int64_t ldv, void* stream);

@@ -11,14 +11,17 @@
 //   warp 1      MMA issuer: one thread issues tcgen05.mma (M = 128, N = BN,
 //               K = 16) per K slice into a TMEM accumulator, and commits each
 //               stage back to the producer;
-//   warps 2..9  epilogue: tcgen05.ld of the finished accumulator, bias /
-//               activation / scale, 16-byte stores.
+//   warps 2..17 epilogue: tcgen05.ld of the finished accumulator, bias /
+//               activation / scale, then each 128 x 16 chunk is staged in
+//               shared memory and written by a TMA tensor store (16-byte
+//               direct stores where an output is not 16-byte aligned).
 // Two TMEM accumulators alternate between tiles, so the epilogue of tile i
 // runs while the MMAs of tile i+1 execute.  Operands sit in shared memory in
-// the canonical no-swizzle K-major layout, written directly by TMA: one box of
-// 8 K-elements (16 bytes) x rows per 8-column group, so a core matrix (8 rows x
-// 16 B) is contiguous, 8-row groups are 128 B apart and adjacent K groups are
-// rows x 16 B apart.  Out-of-range rows and K columns are zero-filled by TMA.
+// the 128-byte-swizzled K-major layout that one TMA box of 64 K-elements x rows
+// writes (each row's 128 bytes in 16-byte granules permuted by row mod 8, 8-row
+// groups 1 KB apart); the 16-deep K slices of a chunk start 32 bytes apart
+// inside that swizzle atom.  Out-of-range rows and K columns are zero-filled by
+// TMA.
 // Every mbarrier wait is bounded in time; an expired wait sets bit 3 of the
 // status word and every role of the CTA stops, after letting its own copies
 // and MMAs in flight finish.
@@ -28,6 +31,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 
 #include "gemm.hpp"
 
@@ -35,8 +39,10 @@ namespace sat {
 namespace {
 
 constexpr int BM = 128;
-constexpr int BK = 64;                               // K elements per stage: 8 groups of 16 bytes
-constexpr int N_EPI_WARPS = 8;                       // two per TMEM lane quarter, one per half of the columns
+constexpr int BK = 64;                               // K elements per stage: one 128-byte swizzle row
+constexpr int EPI_GROUPS = 4;                        // column groups of the epilogue, 4 warps (128 rows) each
+constexpr int N_EPI_WARPS = 4 * EPI_GROUPS;
+constexpr int W = 16;                                // columns per epilogue chunk
 constexpr int GEMM_THREADS = 64 + 32 * N_EPI_WARPS;  // + producer warp + MMA warp
 constexpr uint64_t WAIT_NS = 2000000000ull;          // bound of one mbarrier wait (2 s)
 
@@ -45,11 +51,12 @@ struct Cfg {
     static constexpr int A_BYTES = BM * BK * 2;
     static constexpr int B_BYTES = BN * BK * 2;
     static constexpr int STAGE = A_BYTES + B_BYTES;  // a multiple of 1024
-    static constexpr int STAGES = BN == 256 ? 4 : (BN == 128 ? 6 : 8);
+    static constexpr int STAGES = BN == 256 ? 3 : (BN == 128 ? 4 : 6);
     static constexpr int RING = STAGES * STAGE;
+    static constexpr int STAGING = EPI_GROUPS * 2 * 128 * W * 4;  // two FP32 chunk buffers per column group
     // barriers: full[STAGES], empty[STAGES], tmem_full[2], tmem_empty[2], done
     static constexpr int N_BAR = 2 * STAGES + 5;
-    static constexpr int SMEM = 1024 + RING + 8 * N_BAR + 16;  // + slack to align the ring to 1 KB
+    static constexpr int SMEM = 1024 + RING + STAGING + 8 * N_BAR + 16;  // + slack to align the ring to 1 KB
     static constexpr int TMEM_COLS = 2 * BN;
 };
 
@@ -112,15 +119,17 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-// No-swizzle K-major shared-memory matrix descriptor: start address, LBO = step
-// between core matrices adjacent in K, SBO = step between 8-row groups,
-// descriptor version 1.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+// Shared-memory matrix descriptor, K-major with 128-byte swizzle: start address,
+// leading offset 16 B (unused when one MMA's K extent lies inside the swizzle
+// row), stride between 8-row groups 1024 B, descriptor version 1, layout type 2
+// (128-byte swizzle).  The tile base must be 1 KB aligned (base offset 0).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1u << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
     d |= (uint64_t)1u << 46;
+    d |= (uint64_t)2u << 61;
     return d;
 }
 
@@ -135,39 +144,128 @@ __device__ __forceinline__ float gelu_grad(float x) {
 }
 
 struct Flags {
-    bool vec_f32, vec_bf16, vec_pre;  // row-major outputs / pre allow 16-byte accesses
+    bool vec_f32, vec_bf16, vec_pre;                       // direct stores: 16-byte accesses allowed
+    bool tma_pre, tma_f32, tma_bf16, tma_tbf16, tma_tf32;  // staged TMA stores available
 };
 
-// Epilogue of one 32-column chunk of row m (columns n .. n+31), x = accumulator.
-__device__ __forceinline__ void epilogue_chunk(const GemmArgs& g, Flags f, int m, int n, float (&x)[32]) {
-    const bool row_ok = m < g.M;
-    const bool full = n + 32 <= g.N;
+// Store tensor maps of the outputs that take the staged path.
+struct StoreMaps {
+    CUtensorMap pre, f32, bf16, tbf16, tf32;
+};
+
+// Staged epilogue: a 128-row x W-column chunk is written to a shared-memory
+// buffer in the layout of the output's TMA box, then stored by one thread with
+// cp.async.bulk.tensor.  Each column group of the epilogue warps (4 warps: 128
+// threads, all 128 rows) owns two such buffers and alternates between them.
+enum OutKind { OUT_R32 = 0, OUT_R16 = 1, OUT_T32 = 2, OUT_T16 = 3 };
+constexpr int STG_BYTES = 128 * W * 4;
+
+struct Stager {
+    uint32_t base;  // two buffers of STG_BYTES, 1 KB aligned
+    int buf;
+    int bar_id;     // named barrier of the column group
+    bool issuer;    // the thread that issues the group's TMA stores
+};
+
+__device__ __forceinline__ void named_sync(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
+
+__device__ __forceinline__ void st_shared_v4(uint32_t a, uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w) : "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// Row r (0..127) of the chunk holds x[0..15].  Layouts of the buffer, matching the boxes:
+//   OUT_R32  [128 rows][16 f32]   rows of 64 B, 16-byte granule k of row r at k ^ ((r / 2) mod 4)  (64-byte swizzle)
+//   OUT_R16  [128 rows][16 bf16]  rows of 32 B, granule k of row r at k ^ ((r / 4) mod 2)        (32-byte swizzle)
+//   OUT_T32  [16 cols][128 f32]   transposed, no swizzle
+//   OUT_T16  [16 cols][128 bf16]  transposed, no swizzle
+// Every thread of the group executes this (it contains two named barriers);
+// `live` = false skips only the store itself.
+template <int KIND>
+__device__ __forceinline__ void staged_store(Stager& s, const CUtensorMap* map, int r, const float (&x)[W], int cx,
+                                             int cy, bool live) {
+    const uint32_t b = s.base + (uint32_t)(s.buf * STG_BYTES);
+    if (s.issuer) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");  // this buffer's last store has read it
+    named_sync(s.bar_id);
+    if (KIND == OUT_R32) {
+        const uint32_t row = b + (uint32_t)r * 64u;
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            st_shared_v4(row + ((uint32_t)(k ^ ((r >> 1) & 3)) << 4), __float_as_uint(x[4 * k]),
+                         __float_as_uint(x[4 * k + 1]), __float_as_uint(x[4 * k + 2]), __float_as_uint(x[4 * k + 3]));
+    } else if (KIND == OUT_R16) {
+        const uint32_t row = b + (uint32_t)r * 32u;
+#pragma unroll
+        for (int k = 0; k < 2; k++)
+            st_shared_v4(row + ((uint32_t)(k ^ ((r >> 2) & 1)) << 4), pack_bf16(x[8 * k], x[8 * k + 1]),
+                         pack_bf16(x[8 * k + 2], x[8 * k + 3]), pack_bf16(x[8 * k + 4], x[8 * k + 5]),
+                         pack_bf16(x[8 * k + 6], x[8 * k + 7]));
+    } else if (KIND == OUT_T32) {
+#pragma unroll
+        for (int j = 0; j < W; j++)
+            asm volatile("st.shared.b32 [%0], %1;" ::"r"(b + (uint32_t)(j * 512 + r * 4)), "r"(__float_as_uint(x[j]))
+                         : "memory");
+    } else {
+#pragma unroll
+        for (int j = 0; j < W; j++) {
+            const __nv_bfloat16 h = __float2bfloat16_rn(x[j]);
+            asm volatile("st.shared.b16 [%0], %1;" ::"r"(b + (uint32_t)(j * 256 + r * 2)),
+                         "h"(*reinterpret_cast<const unsigned short*>(&h))
+                         : "memory");
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    named_sync(s.bar_id);
+    if (s.issuer && live) {
+        asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                         reinterpret_cast<uint64_t>(map)),
+                     "r"(b), "r"(cx), "r"(cy)
+                     : "memory");
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    }
+    s.buf ^= 1;
+}
+
+// Epilogue of one W-column chunk: rows m0 + r, columns n .. n+W-1, x = accumulator.
+__device__ __forceinline__ void epilogue_chunk(const GemmArgs& g, const StoreMaps& sm, const Flags& f, Stager& st,
+                                               int m0, int r, int n, float (&x)[W], bool live) {
+    const int m = m0 + r;
+    const bool row_ok = live && m < g.M;
+    const bool full = n + W <= g.N;
     if (g.bias) {
 #pragma unroll
-        for (int j = 0; j < 32; j++)
+        for (int j = 0; j < W; j++)
             if (n + j < g.N) x[j] += __ldg(g.bias + n + j);
     }
     if (g.epi == EPI_GELU) {
-        if (g.pre && row_ok) {
-            float* p = g.pre + (int64_t)m * g.ldpre + n;
-            if (full && f.vec_pre) {
+        if (g.pre) {
+            if (f.tma_pre) {
+                staged_store<OUT_R32>(st, &sm.pre, r, x, n, m0, live);
+            } else if (row_ok) {
+                float* p = g.pre + (int64_t)m * g.ldpre + n;
+                if (full && f.vec_pre) {
 #pragma unroll
-                for (int j = 0; j < 32; j += 4)
-                    *reinterpret_cast<float4*>(p + j) = make_float4(x[j], x[j + 1], x[j + 2], x[j + 3]);
-            } else {
+                    for (int j = 0; j < W; j += 4)
+                        *reinterpret_cast<float4*>(p + j) = make_float4(x[j], x[j + 1], x[j + 2], x[j + 3]);
+                } else {
 #pragma unroll
-                for (int j = 0; j < 32; j++)
-                    if (n + j < g.N) p[j] = x[j];
+                    for (int j = 0; j < W; j++)
+                        if (n + j < g.N) p[j] = x[j];
+                }
             }
         }
 #pragma unroll
-        for (int j = 0; j < 32; j++) x[j] = gelu_exact(x[j]);
+        for (int j = 0; j < W; j++) x[j] = gelu_exact(x[j]);
     } else if (g.epi == EPI_GELU_GRAD) {
         if (row_ok) {
             const float* p = g.pre + (int64_t)m * g.ldpre + n;
             if (full && f.vec_pre) {
 #pragma unroll
-                for (int j = 0; j < 32; j += 4) {
+                for (int j = 0; j < W; j += 4) {
                     const float4 v = __ldg(reinterpret_cast<const float4*>(p + j));
                     x[j] *= gelu_grad(v.x);
                     x[j + 1] *= gelu_grad(v.y);
@@ -176,74 +274,89 @@ __device__ __forceinline__ void epilogue_chunk(const GemmArgs& g, Flags f, int m
                 }
             } else {
 #pragma unroll
-                for (int j = 0; j < 32; j++)
+                for (int j = 0; j < W; j++)
                     if (n + j < g.N) x[j] *= gelu_grad(__ldg(p + j));
             }
         }
     }
 #pragma unroll
-    for (int j = 0; j < 32; j++) x[j] *= g.alpha;
-    if (row_ok && g.out_f32) {
-        float* o = g.out_f32 + (int64_t)m * g.ldo + n;
-        if (full && f.vec_f32) {
+    for (int j = 0; j < W; j++) x[j] *= g.alpha;
+    if (g.out_f32) {
+        if (f.tma_f32) {
+            staged_store<OUT_R32>(st, &sm.f32, r, x, n, m0, live);
+        } else if (row_ok) {
+            float* o = g.out_f32 + (int64_t)m * g.ldo + n;
+            if (full && f.vec_f32) {
 #pragma unroll
-            for (int j = 0; j < 32; j += 4)
-                *reinterpret_cast<float4*>(o + j) = make_float4(x[j], x[j + 1], x[j + 2], x[j + 3]);
-        } else {
+                for (int j = 0; j < W; j += 4)
+                    *reinterpret_cast<float4*>(o + j) = make_float4(x[j], x[j + 1], x[j + 2], x[j + 3]);
+            } else {
 #pragma unroll
-            for (int j = 0; j < 32; j++)
-                if (n + j < g.N) o[j] = x[j];
-        }
-    }
-    if (row_ok && g.out_bf16) {
-        __nv_bfloat16* o = g.out_bf16 + (int64_t)m * g.ldo + n;
-        if (full && f.vec_bf16) {
-#pragma unroll
-            for (int j = 0; j < 32; j += 8) {
-                uint4 v;
-                __nv_bfloat162 h0 = __floats2bfloat162_rn(x[j], x[j + 1]), h1 = __floats2bfloat162_rn(x[j + 2], x[j + 3]);
-                __nv_bfloat162 h2 = __floats2bfloat162_rn(x[j + 4], x[j + 5]), h3 = __floats2bfloat162_rn(x[j + 6], x[j + 7]);
-                v.x = *reinterpret_cast<uint32_t*>(&h0);
-                v.y = *reinterpret_cast<uint32_t*>(&h1);
-                v.z = *reinterpret_cast<uint32_t*>(&h2);
-                v.w = *reinterpret_cast<uint32_t*>(&h3);
-                *reinterpret_cast<uint4*>(o + j) = v;
+                for (int j = 0; j < W; j++)
+                    if (n + j < g.N) o[j] = x[j];
             }
-        } else {
-#pragma unroll
-            for (int j = 0; j < 32; j++)
-                if (n + j < g.N) o[j] = __float2bfloat16_rn(x[j]);
         }
     }
-    // transposed stores: lanes hold consecutive m, so each column is one coalesced warp store
-    if (row_ok && g.out_t_bf16) {
+    if (g.out_bf16) {
+        if (f.tma_bf16) {
+            staged_store<OUT_R16>(st, &sm.bf16, r, x, n, m0, live);
+        } else if (row_ok) {
+            __nv_bfloat16* o = g.out_bf16 + (int64_t)m * g.ldo + n;
+            if (full && f.vec_bf16) {
 #pragma unroll
-        for (int j = 0; j < 32; j++)
-            if (n + j < g.N) g.out_t_bf16[(int64_t)(n + j) * g.ldt + m] = __float2bfloat16_rn(x[j]);
+                for (int j = 0; j < W; j += 8) {
+                    uint4 v;
+                    v.x = pack_bf16(x[j], x[j + 1]);
+                    v.y = pack_bf16(x[j + 2], x[j + 3]);
+                    v.z = pack_bf16(x[j + 4], x[j + 5]);
+                    v.w = pack_bf16(x[j + 6], x[j + 7]);
+                    *reinterpret_cast<uint4*>(o + j) = v;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < W; j++)
+                    if (n + j < g.N) o[j] = __float2bfloat16_rn(x[j]);
+            }
+        }
     }
-    if (row_ok && g.out_t_f32) {
+    // direct transposed stores: lanes hold consecutive m, so each column is one coalesced warp store
+    if (g.out_t_bf16) {
+        if (f.tma_tbf16) {
+            staged_store<OUT_T16>(st, &sm.tbf16, r, x, m0, n, live);
+        } else if (row_ok) {
 #pragma unroll
-        for (int j = 0; j < 32; j++)
-            if (n + j < g.N) g.out_t_f32[(int64_t)(n + j) * g.ldt + m] = x[j];
+            for (int j = 0; j < W; j++)
+                if (n + j < g.N) g.out_t_bf16[(int64_t)(n + j) * g.ldt + m] = __float2bfloat16_rn(x[j]);
+        }
+    }
+    if (g.out_t_f32) {
+        if (f.tma_tf32) {
+            staged_store<OUT_T32>(st, &sm.tf32, r, x, m0, n, live);
+        } else if (row_ok) {
+#pragma unroll
+            for (int j = 0; j < W; j++)
+                if (n + j < g.N) g.out_t_f32[(int64_t)(n + j) * g.ldt + m] = x[j];
+        }
     }
 }
 
 template <int BN>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
-                const __grid_constant__ GemmArgs g, const Flags f) {
+                const __grid_constant__ GemmArgs g, const __grid_constant__ StoreMaps sm, const Flags f) {
     using C = Cfg<BN>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const uint32_t pad = ((su32(smem_raw) + 1023u) & ~1023u) - su32(smem_raw);
     unsigned char* smem = smem_raw + pad;
     const uint32_t ring = su32(smem);
-    const uint32_t bars = ring + C::RING;
+    const uint32_t staging = ring + C::RING;
+    const uint32_t bars = staging + C::STAGING;
     auto full_bar = [&](int s) { return bars + 8u * (uint32_t)s; };
     auto empty_bar = [&](int s) { return bars + 8u * (uint32_t)(C::STAGES + s); };
     auto tfull_bar = [&](int a) { return bars + 8u * (uint32_t)(2 * C::STAGES + a); };
     auto tempty_bar = [&](int a) { return bars + 8u * (uint32_t)(2 * C::STAGES + 2 + a); };
     const uint32_t done_bar = bars + 8u * (uint32_t)(2 * C::STAGES + 4);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::RING + 8 * C::N_BAR);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::RING + C::STAGING + 8 * C::N_BAR);
     volatile uint32_t* abort = tmem_slot + 1;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -288,11 +401,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                 if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort, g.status)) break;
                 const uint32_t a_dst = ring + (uint32_t)(stage * C::STAGE), b_dst = a_dst + C::A_BYTES;
                 mbar_expect_tx(full_bar(stage), (uint32_t)C::STAGE);
-#pragma unroll
-                for (int c = 0; c < BK / 8; c++) {
-                    tma_load_2d(a_dst + (uint32_t)(c * BM * 16), &map_a, kc * BK + 8 * c, m0, full_bar(stage));
-                    tma_load_2d(b_dst + (uint32_t)(c * BN * 16), &map_b, kc * BK + 8 * c, n0, full_bar(stage));
-                }
+                tma_load_2d(a_dst, &map_a, kc * BK, m0, full_bar(stage));
+                tma_load_2d(b_dst, &map_b, kc * BK, n0, full_bar(stage));
                 used |= 1u << stage;
                 last_par = (last_par & ~(1u << stage)) | (phase << stage);
                 if (++stage == C::STAGES) {
@@ -326,8 +436,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                 const uint32_t a0 = ring + (uint32_t)(stage * C::STAGE), b0 = a0 + C::A_BYTES;
 #pragma unroll
                 for (int s = 0; s < BK / 16; s++) {
-                    const uint64_t ad = smem_desc(a0 + (uint32_t)(s * 2 * BM * 16), BM * 16, 128);
-                    const uint64_t bd = smem_desc(b0 + (uint32_t)(s * 2 * BN * 16), BN * 16, 128);
+                    const uint64_t ad = smem_desc_sw128(a0 + (uint32_t)(s * 32));
+                    const uint64_t bd = smem_desc_sw128(b0 + (uint32_t)(s * 32));
                     const uint32_t accumulate = (kc > 0 || s > 0) ? 1u : 0u;
                     asm volatile(
                         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -349,8 +459,18 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         mbar_wait(done_bar, 0u, abort, g.status, false);
     } else if (warp >= 2) {
         // ---------------------------------------------------------------- epilogue
+        // Every thread of a column group runs the same sequence of chunks and
+        // staged stores (their named barriers must match), also after an abort,
+        // when it skips the TMEM reads and the stores themselves.
         const int q = warp & 3;              // TMEM lane quarter this warp may access
-        const int half = (warp - 2) >> 2;    // which half of the tile's columns
+        const int grp = (warp - 2) >> 2;     // column group: columns [grp, grp + 1) * BN / EPI_GROUPS
+        const int r = 32 * q + lane;         // row within the tile
+        Stager st;
+        st.base = staging + (uint32_t)(grp * 2 * STG_BYTES);
+        st.buf = 0;
+        st.bar_id = 1 + grp;
+        st.issuer = ((warp - 2) & 3) == 0 && lane == 0;
+        constexpr int COLS = BN / EPI_GROUPS;
         int i = 0;
         for (int t = blockIdx.x; t < tiles; t += gridDim.x, i++) {
             const int acc = i & 1;
@@ -358,33 +478,35 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             int ok = 1;
             if (lane == 0) ok = mbar_wait(tfull_bar(acc), use & 1u, abort, g.status) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
-            if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int m = (t / n_tiles_n) * BM + 32 * q + lane, n0 = (t % n_tiles_n) * BN;
-            for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 32) {
+            const int m0 = (t / n_tiles_n) * BM, n0 = (t % n_tiles_n) * BN;
+            for (int c = grp * COLS; c < (grp + 1) * COLS; c += W) {
                 if (n0 + c >= g.N) break;
-                uint32_t r[32];
-                const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * BN + c);
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
-                    "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
-                    "[%32];"
-                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                      "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                      "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                      "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                    : "r"(taddr));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                float x[32];
+                float x[W];
+                if (ok) {
+                    uint32_t v[W];
+                    const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * BN + c);
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+                        "%12, %13, %14, %15}, [%16];"
+                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                          "=r"(v[14]), "=r"(v[15])
+                        : "r"(taddr));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                for (int j = 0; j < 32; j++) x[j] = __uint_as_float(r[j]);
-                epilogue_chunk(g, f, m, n0 + c, x);
+                    for (int j = 0; j < W; j++) x[j] = __uint_as_float(v[j]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < W; j++) x[j] = 0.0f;
+                }
+                epilogue_chunk(g, sm, f, st, m0, r, n0 + c, x, ok != 0 && !*abort);
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(tempty_bar(acc));
         }
+        if (st.issuer) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -407,17 +529,25 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// 2-D map over a K-major bf16 matrix [rows][ld] (K contiguous); box = 8 K-elements x box_rows.
-bool make_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, int K, int64_t ld, int box_rows) {
+// 2-D map over a row-major matrix [rows][ld] of `cols` used columns (element type `dt`,
+// `esize` bytes), box = box_cols x box_rows.
+bool encode(CUtensorMap* map, const void* base, CUtensorMapDataType dt, int esize, int64_t rows, int64_t cols,
+            int64_t ld, int box_cols, int box_rows, CUtensorMapSwizzle sw) {
     auto fn = encode_fn();
     if (!fn) return false;
-    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-    cuuint32_t box[2] = {8u, (cuuint32_t)box_rows};
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * esize)};
+    cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1u, 1u};
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    return fn(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Operand map: K-major bf16 [rows][ld]; box = 64 K-elements (128 B) x box_rows, written to shared
+// memory with the 128-byte swizzle.
+bool make_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, int K, int64_t ld, int box_rows) {
+    return encode(map, base, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, rows, K, ld, BK, box_rows,
+                  CU_TENSOR_MAP_SWIZZLE_128B);
 }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
@@ -435,9 +565,22 @@ cudaError_t gemm_launch(const GemmArgs& g, int sms, cudaStream_t s) {
     f.vec_f32 = aligned16(g.out_f32) && g.ldo % 4 == 0;
     f.vec_bf16 = aligned16(g.out_bf16) && g.ldo % 8 == 0;
     f.vec_pre = aligned16(g.pre) && g.ldpre % 4 == 0;
+    // Staged TMA stores wherever the output's base and row stride are 16-byte aligned.
+    StoreMaps sm;
+    memset(&sm, 0, sizeof(sm));
+    const auto F32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const auto B16 = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    f.tma_pre = g.epi == EPI_GELU && f.vec_pre &&
+                encode(&sm.pre, g.pre, F32, 4, g.M, g.N, g.ldpre, W, BM, CU_TENSOR_MAP_SWIZZLE_64B);
+    f.tma_f32 = f.vec_f32 && encode(&sm.f32, g.out_f32, F32, 4, g.M, g.N, g.ldo, W, BM, CU_TENSOR_MAP_SWIZZLE_64B);
+    f.tma_bf16 = f.vec_bf16 && encode(&sm.bf16, g.out_bf16, B16, 2, g.M, g.N, g.ldo, W, BM, CU_TENSOR_MAP_SWIZZLE_32B);
+    f.tma_tbf16 = aligned16(g.out_t_bf16) && g.ldt % 8 == 0 &&
+                  encode(&sm.tbf16, g.out_t_bf16, B16, 2, g.N, g.M, g.ldt, BM, W, CU_TENSOR_MAP_SWIZZLE_NONE);
+    f.tma_tf32 = aligned16(g.out_t_f32) && g.ldt % 4 == 0 &&
+                 encode(&sm.tf32, g.out_t_f32, F32, 4, g.N, g.M, g.ldt, BM, W, CU_TENSOR_MAP_SWIZZLE_NONE);
     const int tiles = ((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN);
     const int grid = tiles < sms ? tiles : sms;
-    gemm_kernel<BN><<<grid, GEMM_THREADS, C::SMEM, s>>>(ma, mb, g, f);
+    gemm_kernel<BN><<<grid, GEMM_THREADS, C::SMEM, s>>>(ma, mb, g, sm, f);
     return cudaGetLastError();
 }
 

@@ -70,16 +70,52 @@ __device__ __forceinline__ uint4 philox(uint4 ctr, uint2 key) {
     return ctr;
 }
 
-// z[r][j] ~ N(0, 1) from Philox4x32-10 at counter (r, j, round, 1), Box-Muller, rounded to bf16.
+// z[r][4c + i] ~ N(0, 1), i = 0..3: one Philox4x32-10 block at counter (r, c, round, 1)
+// gives two Box-Muller pairs, (x, y) -> i = 0, 1 (cos, sin) and (z, w) -> i = 2, 3;
+// rounded to bf16.
 __global__ void noise_kernel(uint64_t seed, uint32_t round, int64_t rows, int n_in, bf16* z) {
-    const int64_t n = rows * n_in;
+    const uint32_t groups = (uint32_t)(n_in + 3) / 4u;
+    const int64_t n = rows * groups;
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = k / n_in, j = k % n_in;
-        const uint4 o = philox(make_uint4((uint32_t)r, (uint32_t)j, round, 1u), key);
-        const float u1 = (float)((o.x >> 8) + 1u) * (1.0f / 16777216.0f);
-        const float u2 = (float)(o.y >> 8) * (1.0f / 16777216.0f);
-        z[k] = __float2bfloat16_rn(sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2));
+        uint32_t r, c;
+        if (n <= 0x7fffffff) {  // 32-bit index arithmetic whenever it suffices
+            r = (uint32_t)k / groups;
+            c = (uint32_t)k - r * groups;
+        } else {
+            r = (uint32_t)(k / groups);
+            c = (uint32_t)(k % groups);
+        }
+        const uint4 o = philox(make_uint4(r, c, round, 1u), key);
+        float g[4];
+        {
+            const float u1 = (float)((o.x >> 8) + 1u) * (1.0f / 16777216.0f);
+            const float u2 = (float)(o.y >> 8) * (1.0f / 16777216.0f);
+            const float rad = sqrtf(-2.0f * logf(u1));
+            float sn, cs;
+            sincospif(2.0f * u2, &sn, &cs);
+            g[0] = rad * cs;
+            g[1] = rad * sn;
+        }
+        {
+            const float u1 = (float)((o.z >> 8) + 1u) * (1.0f / 16777216.0f);
+            const float u2 = (float)(o.w >> 8) * (1.0f / 16777216.0f);
+            const float rad = sqrtf(-2.0f * logf(u1));
+            float sn, cs;
+            sincospif(2.0f * u2, &sn, &cs);
+            g[2] = rad * cs;
+            g[3] = rad * sn;
+        }
+        bf16* zr = z + (int64_t)r * n_in + 4 * c;
+        if (4 * (int)c + 4 <= n_in && (n_in & 3) == 0 && ((uintptr_t)z & 7) == 0) {
+            __nv_bfloat162 lo = __floats2bfloat162_rn(g[0], g[1]), hi = __floats2bfloat162_rn(g[2], g[3]);
+            uint2 v;
+            v.x = *reinterpret_cast<uint32_t*>(&lo);
+            v.y = *reinterpret_cast<uint32_t*>(&hi);
+            *reinterpret_cast<uint2*>(zr) = v;
+        } else {
+            for (int i = 0; i < 4 && 4 * (int)c + i < n_in; i++) zr[i] = __float2bfloat16_rn(g[i]);
+        }
     }
 }
 
@@ -345,7 +381,8 @@ sat_status sat_mlp_set_params(sat_mlp* m, const float* host) {
 sat_status sat_mlp_draw_noise(sat_mlp* m, uint64_t seed, uint32_t round, void* z, int64_t rows, void* stream) {
     if (!m || (!z && rows > 0) || rows < 0) return sat::report_error(SAT_ERR_ARG, "bad argument");
     if (rows == 0) return SAT_OK;
-    noise_kernel<<<std::min<unsigned>(blocks(rows * m->n_in, 256), 148 * 16), 256, 0, (cudaStream_t)stream>>>(
+    noise_kernel<<<std::min<unsigned>(blocks(rows * ((m->n_in + 3) / 4), 256), 148 * 16), 256, 0,
+                   (cudaStream_t)stream>>>(
         seed, round, rows, m->n_in, (bf16*)z);
     if (cudaGetLastError() != cudaSuccess) return sat::report_error(SAT_ERR_CUDA, "noise launch failed");
     return SAT_OK;

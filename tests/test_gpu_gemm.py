@@ -113,3 +113,27 @@ def test_gemm_persistent_many_tiles(gpu, M, N, K, out):
         tol = 2 ** -8 * np.abs(ref) + tol
     d = np.abs(got - ref)
     assert (d <= tol).all(), float(d.max())
+
+
+def test_gemm_unaligned_outputs(gpu):
+    """Outputs whose row stride is not a multiple of 16 bytes take the direct-store path;
+    aligned ones in the same call take the staged tensor stores."""
+    import paper_2502_08673_b300 as P
+    g = torch.Generator().manual_seed(11)
+    M, N, K = 301, 99, 64
+    A, B = _rand((M, K), g), _rand((N, K), g)
+    bias = torch.randn(N, generator=g)
+    ref, mag = _ref(A, B)
+    ref = ref + bias.double().numpy()[None, :]
+    tol = 1e-5 * (mag + np.abs(bias.double().numpy())[None, :]) + 1e-6
+    st = torch.zeros(1, dtype=torch.int32, device=gpu)
+    out = torch.full((M, N), float("nan"), device=gpu)            # ldo = 99: direct
+    out_t = torch.zeros((N, M), dtype=torch.bfloat16, device=gpu)  # ldt = 301: direct
+    out_tf = torch.full((N, 304), float("nan"), device=gpu)[:, :M]  # ldt = 304: staged
+    P.sat_gemm_bf16(A.to(gpu), B.to(gpu), bias=bias.to(gpu), out_f32=out, out_t_bf16=out_t, status=st)
+    P.sat_gemm_bf16(A.to(gpu), B.to(gpu), bias=bias.to(gpu), out_t_f32=out_tf, status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    assert (np.abs(out.cpu().double().numpy() - ref) <= tol).all()
+    assert (np.abs(out_tf.cpu().double().numpy().T - ref) <= tol).all()
+    assert (np.abs(out_t.cpu().double().numpy().T - ref) <= 2 ** -8 * np.abs(ref) + tol).all()
