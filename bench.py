@@ -281,6 +281,9 @@ def main():
                     help="optimisation steps per round when starting from the proposal (default: the workload's)")
     ap.add_argument("--proposal-train-steps", type=int, default=0, help="IMLE steps (default: 2 epochs, 64..512)")
     ap.add_argument("--proposal-rounds", type=int, default=0, help="plain rounds per training instance")
+    ap.add_argument("--check-every", type=int, default=0,
+                    help="early exit: verify every K steps, harvest valid samples and restart their slots")
+    ap.add_argument("--max-age", type=int, default=0, help="early exit: restart samples unsolved after this many steps")
     ap.add_argument("--mlp", action="store_true",
                     help="time only the proposal network's inference GEMMs (tcgen05) at the workload's batch")
     args = ap.parse_args()
@@ -317,8 +320,10 @@ def main():
     opt = P.opt_params("adam", lr=w["lr"])
     ws = P.new_workspace(plan, B, ad)
     n_rounds = args.warmup + args.steps
-    dedup = P.Dedup.create(plan, max_keys=B * (n_rounds + 1 + (args.steps if args.proposal != "none" else 0)),
-                           max_batch=B)
+    harvest_rounds = n_rounds + 1 + (args.steps if args.proposal != "none" else 0)
+    if args.check_every > 0:  # up to one harvest per sample and epoch
+        harvest_rounds *= -(-steps // args.check_every)
+    dedup = P.Dedup.create(plan, max_keys=B * harvest_rounds, max_batch=B)
     stream = torch.cuda.current_stream()
     round_base = rank << 20
 
@@ -327,7 +332,17 @@ def main():
                           args.proposal_rounds) if args.proposal != "none" else None)
     prop_steps = args.proposal_steps or steps
 
+    ee_events = []
+    max_age = args.max_age or steps
+
     def one_round(k, ev=None, use_mlp=True):
+        if args.check_every > 0:
+            # early exit: one bench step = `steps` descent steps of the batch in epochs; the batch
+            # carries over between bench steps (a continuous sampler); kernel events per launch
+            P.run_epochs(plan, ws, opt, steps, args.check_every, max_age, seed=0, round_=round_base + 4096 * k,
+                         dedup=dedup, init_scale=w["init_scale"], fresh=(k == 0 or k == n_rounds + 64), stream=None,
+                         proposal=mlp if use_mlp else None, tau=args.tau, events=ee_events if ev is not None else None)
+            return
         if mlp is not None and use_mlp:
             mlp.propose(ws.V, seed=0, round_=round_base + k, tau=args.tau)
         else:
@@ -359,14 +374,21 @@ def main():
         start.record(stream)
         for k in range(args.steps):
             one_round(args.warmup + k, kev[k])
-            valid_total += int(P.valid_mask(ws.valid, B).sum())
+            if args.check_every <= 0:
+                valid_total += int(P.valid_mask(ws.valid, B).sum())
         end.record(stream)
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     elapsed_ms = start.elapsed_time(end)
     uniq = dedup.count() - before
-    kernel_ms = [a.elapsed_time(b) for a, b in kev]
+    if args.check_every > 0:
+        # per launch of the fused steps kernel (check_every steps each)
+        kernel_ms = [a.elapsed_time(b) for _, (a, b) in ee_events]
+        launch_steps = statistics.mean(steps_k for steps_k, _ in ee_events)
+    else:
+        kernel_ms = [a.elapsed_time(b) for a, b in kev]
+        launch_steps = None
     t_max, uniq_all, valid_all = elapsed_ms, uniq, valid_total
     if world > 1:
         tt = torch.tensor([elapsed_ms], device="cuda")
@@ -375,10 +397,10 @@ def main():
         dist.all_reduce(cnt)
         t_max, uniq_all, valid_all = float(tt.item()), int(cnt[0].item()), int(cnt[1].item())
     value = uniq_all / (t_max / 1e3)
-    run_steps = prop_steps if mlp is not None else steps
+    run_steps = prop_steps if (mlp is not None and args.check_every <= 0) else steps
     gate_evals = info["n_cone_gates"] * B * run_steps * args.steps * world
     peak, peak_kind = measured_peaks()
-    alg = algorithmic_bytes_per_step(info, B, ad) * run_steps
+    alg = algorithmic_bytes_per_step(info, B, ad) * (launch_steps or run_steps)
     kavg = statistics.mean(kernel_ms)
     achieved = alg / (kavg / 1e3) / 1e9
     dram_per_sample_step, prof = profile_traffic(args.workload, ad)
@@ -392,7 +414,8 @@ def main():
         e0.record(stream)
         for k in range(args.steps):
             one_round(n_rounds + 64 + k, use_mlp=False)
-            vp += int(P.valid_mask(ws.valid, B).sum())
+            if args.check_every <= 0:
+                vp += int(P.valid_mask(ws.valid, B).sum())
         e1.record(stream)
         torch.cuda.synchronize()
         tp = e0.elapsed_time(e1)
@@ -409,7 +432,8 @@ def main():
         d2h = 0
         for k in range(e2e_steps):
             sols = P.sample(circ, cnf, n_wanted=10 ** 12, batch=B, steps=steps, max_rounds=1, lr=w["lr"], seed=0,
-                            first_round=round_base + n_rounds + k, init_scale=w["init_scale"], act_dtype=ad)
+                            first_round=round_base + (n_rounds + k) * 4096, init_scale=w["init_scale"], act_dtype=ad,
+                            check_every=max(0, args.check_every), max_age=args.max_age)
             ucount += len(sols)
             d2h += len(sols) * info["key_words"] * 4 + B // 8 + 16
         e2e_s = time.perf_counter() - t1
@@ -433,7 +457,7 @@ def main():
                        (info["n_cone"] * B * ACT_BYTES[ad] / 1e9),
                        "parallelism": f"replicas x{world} (disjoint Philox streams)"},
             "gate_evals_per_s": gate_evals / (t_max / 1e3),
-            "valid_fraction": valid_all / (B * args.steps * world),
+            "valid_fraction": (valid_all / (B * args.steps * world)) if args.check_every <= 0 else None,
             "unique_in_timed_steps": uniq_all,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
@@ -441,7 +465,7 @@ def main():
                          "algorithmic_bytes_per_launch": alg,
                          "traffic": (dram_per_sample_step * B * steps) if dram_per_sample_step else None,
                          "traffic_source": prof},
-            "gpu_launches": 8 * args.steps,
+            "gpu_launches": (8 * args.steps if args.check_every <= 0 else 9 * len(ee_events)),
             "transform_s": transform_s,
             "plan": {k: info[k] for k in ("n_pi", "n_cone_pi", "n_cone_gates", "n_gates", "n_clauses",
                                           "n_cone_levels", "max_span")},
@@ -449,6 +473,11 @@ def main():
             "cpu_baseline": cpu,
             "e2e": e2e,
         }
+        if args.check_every > 0:
+            line["config"]["early_exit"] = {"check_every": args.check_every, "max_age": max_age,
+                                            "epochs_per_step": -(-steps // args.check_every),
+                                            "note": "batch carried across steps; valid samples harvested and "
+                                                    "restarted every check_every steps"}
         if mlp is not None:
             line["config"]["proposal"] = {"mode": args.proposal, "tau": args.tau, "steps_per_round": prop_steps,
                                           **prop_log}

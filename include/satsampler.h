@@ -184,6 +184,31 @@ sat_status sat_steps(const sat_plan* p, sat_act_dtype act_dtype, const sat_opt_p
                      float* v, int64_t ldv, void* act, float* adj, float* loss, int32_t t0, int32_t n_steps,
                      int64_t B, void* stream);
 
+/* sat_steps with per-sample Adam step counts, for early exit (below), where
+ * samples restart at different times: the Adam step of sample b at in-launch
+ * step s is age[b] + t0 + s (age: device int32 [B], read only; NULL = sat_steps).
+ * GD ignores age. */
+sat_status sat_steps_aged(const sat_plan* p, sat_act_dtype act_dtype, const sat_opt_params* o, float* V, float* m,
+                          float* v, int64_t ldv, void* act, float* adj, float* loss, const int32_t* age, int32_t t0,
+                          int32_t n_steps, int64_t B, void* stream);
+
+/* Early exit: verify every k steps, harvest the valid samples and give their
+ * slots (and those of samples that have not converged after max_age steps) a
+ * new start.  The paper stops "upon convergence" per sample (end of Section
+ * III-A) without saying how a batch does it; this is the batched form.
+ * sat_retire: restart bit b = valid bit b or age[b] + k >= max_age; age[b]
+ * becomes 0 where restarting, else age[b] + k.  valid, restart: device uint32
+ * [ceil(B/32)] (bit j of word w = sample 32w + j); age: device int32 [B]. */
+sat_status sat_retire(const uint32_t* valid, int32_t* age, uint32_t* restart, int32_t k, int32_t max_age, int64_t B,
+                      void* stream);
+/* New starts for the samples whose restart bit is set: V[:, b] = src[:, b] when
+ * src (device float [n_pi][lds]) is given, else init_scale * N(0,1) from the
+ * Philox stream of round `round` (exactly what sat_init_normal draws for b);
+ * m[:, b] = v[:, b] = 0.  Other samples are untouched. */
+sat_status sat_restart(const sat_plan* p, const uint32_t* restart, uint64_t seed, uint32_t round, float init_scale,
+                       const float* src, int64_t lds, float* V, float* m, float* v, int64_t ldv, int64_t B,
+                       void* stream);
+
 /* The same fused steps as sat_steps, for callers that cannot allocate device
  * memory when they run the optimiser (for example, a process whose device
  * budget belongs to another allocator, or a loop that must not wait for the
@@ -318,11 +343,14 @@ typedef struct sat_sample_opts {
     void* stream;
     sat_mlp* proposal;          /* nullable: initial logits from the proposal network (max_rows >= batch) */
     float proposal_tau;         /* scale of the proposal's logits */
+    int32_t check_every;        /* > 0: early exit, verify every check_every steps (see sat_retire);
+                                   the budget stays max_rounds x steps descent steps of the batch */
+    int32_t max_age;            /* early exit: restart samples unsolved after max_age steps (0 = steps) */
 } sat_sample_opts;
 
 typedef struct sat_sample_stats {
-    uint32_t rounds;
-    uint64_t samples, valid, unique;
+    uint32_t rounds;                   /* rounds, or verification epochs under early exit */
+    uint64_t samples, valid, unique;   /* samples started, valid harvests (with repeats), distinct */
     double ms_init, ms_steps, ms_verify, ms_dedup, ms_total;   /* device time per phase (CUDA events) */
     double ms_upload, ms_download;                              /* sat_sample only */
 } sat_sample_stats;

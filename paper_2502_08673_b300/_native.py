@@ -54,7 +54,7 @@ class SampleOpts(C.Structure):
                 ("seed", C.c_uint64), ("first_round", C.c_uint32), ("init_scale", C.c_float),
                 ("act_dtype", C.c_int32), ("steps_per_launch", C.c_int32), ("init_logits", C.c_void_p),
                 ("init_ld", C.c_int64), ("stream", C.c_void_p), ("proposal", C.c_void_p),
-                ("proposal_tau", C.c_float)]
+                ("proposal_tau", C.c_float), ("check_every", C.c_int32), ("max_age", C.c_int32)]
 
 
 class SampleStats(C.Structure):
@@ -91,6 +91,9 @@ PROTOTYPES = {
     "sat_opt_update": (I32, [P, C.POINTER(OptParams), P, P, P, P, I64, I32, I64, P]),
     "sat_steps": (I32, [P, I32, C.POINTER(OptParams), P, P, P, I64, P, P, P, I32, I32, I64, P]),
     "sat_steps_noalloc": (I32, [P, I32, C.POINTER(OptParams), P, P, P, I64, P, I32, I32, I64, P]),
+    "sat_steps_aged": (I32, [P, I32, C.POINTER(OptParams), P, P, P, I64, P, P, P, P, I32, I32, I64, P]),
+    "sat_retire": (I32, [P, P, P, I32, I32, I64, P]),
+    "sat_restart": (I32, [P, P, U64, U32, F32, P, I64, P, P, P, I64, I64, P]),
     "sat_threshold": (I32, [P, P, I64, P, I64, P, I64, P]),
     "sat_hard_eval": (I32, [P, P, I64, I64, P]),
     "sat_cnf_check": (I32, [P, P, I64, P, I64, P]),

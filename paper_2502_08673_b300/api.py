@@ -320,9 +320,26 @@ def sat_opt_update(plan: Plan, opt: N.OptParams, V, m, v, gV, t: int, stream=Non
 
 
 def sat_steps(plan: Plan, opt: N.OptParams, V, m, v, act, adj, t0: int, n_steps: int, loss=None,
-              act_dtype="f32", stream=None):
-    check(lib().sat_steps(plan.handle, N.ACT_DTYPES[act_dtype], C.byref(opt), _ptr(V), _ptr(m), _ptr(v), V.stride(0),
-                          _ptr(act), _ptr(adj), _ptr(loss), t0, n_steps, V.shape[1], _stream(stream)))
+              act_dtype="f32", stream=None, age=None):
+    """Fused steps; with `age` (int32 [B]) the Adam step of sample b is age[b] + t0 + s (sat_steps_aged)."""
+    if age is None:
+        check(lib().sat_steps(plan.handle, N.ACT_DTYPES[act_dtype], C.byref(opt), _ptr(V), _ptr(m), _ptr(v),
+                              V.stride(0), _ptr(act), _ptr(adj), _ptr(loss), t0, n_steps, V.shape[1],
+                              _stream(stream)))
+    else:
+        check(lib().sat_steps_aged(plan.handle, N.ACT_DTYPES[act_dtype], C.byref(opt), _ptr(V), _ptr(m), _ptr(v),
+                                   V.stride(0), _ptr(act), _ptr(adj), _ptr(loss), _ptr(age), t0, n_steps,
+                                   V.shape[1], _stream(stream)))
+
+
+def sat_retire(valid, age, restart, k: int, max_age: int, B: int, stream=None):
+    check(lib().sat_retire(_ptr(valid), _ptr(age), _ptr(restart), k, max_age, B, _stream(stream)))
+
+
+def sat_restart(plan: Plan, restart, seed: int, round_: int, V, m, v, scale: float = 1.0, src=None, stream=None):
+    check(lib().sat_restart(plan.handle, _ptr(restart), seed, round_, scale, _ptr(src),
+                            0 if src is None else src.stride(0), _ptr(V), _ptr(m), _ptr(v), V.stride(0), V.shape[1],
+                            _stream(stream)))
 
 
 def sat_steps_noalloc(plan: Plan, opt: N.OptParams, V, m, v, t0: int, n_steps: int, loss=None, act_dtype="f32",
@@ -372,6 +389,9 @@ class Workspace:
     valid: object
     loss: object
     act_dtype: str = "f32"
+    age: object = None      # early exit (run_epochs): int32 [B] steps since each sample's start
+    restart: object = None  # early exit: restart bits [ceil(B/32)]
+    src: object = None      # early exit with a proposal: new starts [n_pi][B]
 
 
 def new_workspace(plan: Plan, B: int, act_dtype: str = "f32", device="cuda") -> Workspace:
@@ -409,6 +429,53 @@ def run_round(plan: Plan, ws: Workspace, opt: N.OptParams, steps: int, seed: int
         dedup.insert(ws.keys, ws.valid, ws.B, stream=stream)
 
 
+def run_epochs(plan: Plan, ws: Workspace, opt: N.OptParams, steps: int, check_every: int, max_age: int, seed: int,
+               round_: int, dedup: Dedup, init_scale: float = 1.0, proposal: "Mlp | None" = None, tau: float = 1.0,
+               fresh: bool = True, stream=None, events=None):
+    """Early exit on device-resident buffers: `steps` descent steps of the batch in
+    epochs of `check_every`; after each epoch the valid samples go to `dedup` and
+    they (and samples older than max_age) restart (sat_retire, sat_restart) from
+    the Philox stream of round round_ + 1 + epoch, or from the proposal.  With
+    fresh = False the batch continues from the state of a previous call (V, m, v,
+    ws.age) instead of new starts of round round_.  `events` (list): a pair of
+    CUDA events recorded around each fused-steps launch is appended.  Returns the
+    epochs run."""
+    import torch
+    if fresh or getattr(ws, "age", None) is None:
+        if proposal is not None:
+            proposal.propose(ws.V, seed, round_, tau, stream)
+        else:
+            sat_init_normal(plan, ws.V, seed, round_, init_scale, stream)
+        ws.m.zero_()
+        ws.v.zero_()
+        ws.age = torch.zeros(ws.B, dtype=torch.int32, device=ws.V.device)
+        ws.restart = torch.zeros_like(ws.valid)
+        ws.src = torch.empty_like(ws.V) if proposal is not None else None
+    e, done = 0, 0
+    while done < steps:
+        kk = min(check_every, steps - done)
+        if events is not None:
+            ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            ev[0].record(stream)
+        sat_steps(plan, opt, ws.V, ws.m, ws.v, ws.act, ws.adj, 1, kk, act_dtype=ws.act_dtype, stream=stream,
+                  age=ws.age)
+        if events is not None:
+            ev[1].record(stream)
+            events.append((kk, ev))
+        sat_threshold(plan, ws.V, ws.bits, ws.keys, stream)
+        sat_hard_eval(plan, ws.bits, ws.B, stream)
+        sat_cnf_check(plan, ws.bits, ws.valid, ws.B, stream)
+        dedup.insert(ws.keys, ws.valid, ws.B, stream=stream)
+        sat_retire(ws.valid, ws.age, ws.restart, kk, max_age, ws.B, stream)
+        r = round_ + 1 + e
+        if proposal is not None:
+            proposal.propose(ws.src, seed, r, tau, stream)
+        sat_restart(plan, ws.restart, seed, r, ws.V, ws.m, ws.v, init_scale, ws.src, stream)
+        done += kk
+        e += 1
+    return e
+
+
 def valid_mask(valid_words, B: int) -> np.ndarray:
     w = valid_words.cpu().numpy().view(np.uint32)
     bits = np.unpackbits(w.view(np.uint8), bitorder="little")
@@ -417,8 +484,9 @@ def valid_mask(valid_words, B: int) -> np.ndarray:
 
 def sample(circuit: Circuit, cnf: Cnf, n_wanted: int, batch=1024, steps=200, max_rounds=1, optimizer="adam",
            lr=0.1, beta1=0.9, beta2=0.999, eps=1e-8, seed=0, first_round=0, init_scale=1.0, act_dtype="f32",
-           steps_per_launch=0, proposal: "Mlp | None" = None, tau: float = 1.0, stream=None):
-    """End to end from host objects (the C call sat_sample)."""
+           steps_per_launch=0, proposal: "Mlp | None" = None, tau: float = 1.0, check_every=0, max_age=0,
+           stream=None):
+    """End to end from host objects (the C call sat_sample); check_every > 0 = early exit."""
     o = N.SampleOpts()
     lib().sat_sample_opts_default(C.byref(o))
     o.batch, o.steps, o.max_rounds = batch, steps, max_rounds
@@ -428,6 +496,7 @@ def sample(circuit: Circuit, cnf: Cnf, n_wanted: int, batch=1024, steps=200, max
     o.stream = None if stream is None else stream.cuda_stream
     o.proposal = None if proposal is None else proposal.handle
     o.proposal_tau = tau
+    o.check_every, o.max_age = check_every, max_age
     h = C.c_void_p()
     st = N.SampleStats()
     status = check(lib().sat_sample(circuit.handle, cnf.handle, C.byref(o), n_wanted, C.byref(h), C.byref(st)),

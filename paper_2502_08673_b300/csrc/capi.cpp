@@ -451,6 +451,40 @@ sat_status sat_steps(const sat_plan* p, sat_act_dtype t, const sat_opt_params* o
     return SAT_OK;
 }
 
+sat_status sat_steps_aged(const sat_plan* p, sat_act_dtype t, const sat_opt_params* o, float* V, float* m, float* v,
+                          int64_t ldv, void* act, float* adj, float* loss, const int32_t* age, int32_t t0,
+                          int32_t n_steps, int64_t B, void* stream) {
+    sat_status s = check_layout(p, B, ldv);
+    if (s != SAT_OK) return s;
+    if (t < SAT_ACT_F32 || t > SAT_ACT_F16) return fail(SAT_ERR_ARG, "bad act_dtype");
+    if (!opt_ok(o) || t0 < 1 || n_steps < 0) return fail(SAT_ERR_ARG, "bad optimiser parameters or steps");
+    if (B > 0 && ((p->dp.n_pi > 0 && (!V || (o->optimizer == SAT_OPT_ADAM && (!m || !v)))) ||
+                  (p->dp.n_cone > 0 && (!act || !adj))))
+        return fail(SAT_ERR_ARG, "NULL buffer");
+    if ((((uintptr_t)act | (uintptr_t)adj) & 15) != 0) return fail(SAT_ERR_ARG, "act/adj must be 16-byte aligned");
+    CK(sat::launch_steps(p->dp, (int)t, opt_of(o), V, m, v, ldv, act, adj, loss, t0, n_steps, B, S(stream), age));
+    return SAT_OK;
+}
+
+sat_status sat_retire(const uint32_t* valid, int32_t* age, uint32_t* restart, int32_t k, int32_t max_age, int64_t B,
+                      void* stream) {
+    if (B < 0 || k < 0 || max_age < 1) return fail(SAT_ERR_ARG, "bad k / max_age / batch");
+    if (B > 0 && (!valid || !age || !restart)) return fail(SAT_ERR_ARG, "NULL buffer");
+    CK(sat::launch_retire(valid, age, restart, k, max_age, B, S(stream)));
+    return SAT_OK;
+}
+
+sat_status sat_restart(const sat_plan* p, const uint32_t* restart, uint64_t seed, uint32_t round, float init_scale,
+                       const float* src, int64_t lds, float* V, float* m, float* v, int64_t ldv, int64_t B,
+                       void* stream) {
+    sat_status s = check_layout(p, B, ldv);
+    if (s != SAT_OK) return s;
+    if (src && lds < B) return fail(SAT_ERR_ARG, "lds < batch");
+    if (B > 0 && p->dp.n_pi > 0 && (!restart || !V || !m || !v)) return fail(SAT_ERR_ARG, "NULL buffer");
+    CK(sat::launch_restart(p->dp, restart, seed, round, init_scale, src, lds, V, m, v, ldv, B, S(stream)));
+    return SAT_OK;
+}
+
 sat_status sat_threshold(const sat_plan* p, const float* V, int64_t ldv, uint32_t* node_bits, int64_t ldw,
                          uint32_t* keys, int64_t B, void* stream) {
     sat_status s = check_layout(p, B, ldv);
@@ -596,6 +630,8 @@ void sat_sample_opts_default(sat_sample_opts* o) {
     o->stream = nullptr;
     o->proposal = nullptr;
     o->proposal_tau = 1.0f;
+    o->check_every = 0;
+    o->max_age = 0;
 }
 
 namespace {
@@ -628,12 +664,120 @@ size_t scratch_elems(const sat::DevPlan& dp, int64_t B) {
 
 }  // namespace
 
+// Early exit: epochs of check_every steps over the whole batch; after each, the
+// valid samples are harvested into the dedup set and they (and samples older
+// than max_age) restart from new starts drawn on the Philox stream of round
+// first_round + 1 + epoch (or from the proposal network).
+static sat_status sample_early_exit(const sat_plan* p, sat_dedup* d, const sat_sample_opts* o, uint64_t n_wanted,
+                                    sat_sample_stats* st, Workspace& w, cudaStream_t str) {
+    const sat::DevPlan& dp = p->dp;
+    const int64_t B = o->batch;
+    const size_t npi = (size_t)dp.n_pi;
+    int32_t* age = nullptr;
+    uint32_t* restart = nullptr;
+    float* Vp = nullptr;
+    if (!w.alloc((void**)&age, (size_t)B * 4) || !w.alloc((void**)&restart, (size_t)w.ldw * 4) ||
+        (o->proposal && !w.alloc((void**)&Vp, npi * B * 4)))
+        return fail(SAT_ERR_OOM, "cudaMalloc failed for the early-exit state");
+    cudaEvent_t ev[5];
+    for (auto& e : ev) CK(cudaEventCreate(&e));
+    struct EvGuard {
+        cudaEvent_t* e;
+        ~EvGuard() { for (int i = 0; i < 5; i++) cudaEventDestroy(e[i]); }
+    } guard{ev};
+    sat_status s;
+    const sat::OptParams op = opt_of(&o->opt);
+    const int k = o->check_every;
+    const int max_age = o->max_age > 0 ? o->max_age : std::max(1, o->steps);
+    const int spl = o->steps_per_launch > 0 ? o->steps_per_launch : k;
+    const int64_t budget = (int64_t)o->max_rounds * o->steps;
+    sat_sample_stats acc{};
+    std::vector<uint32_t> hvalid(w.ldw), hrestart(w.ldw);
+    uint64_t have = 0;
+    sat_status result = SAT_PARTIAL;
+    // initial starts (round first_round)
+    CK(cudaEventRecord(ev[0], str));
+    if (o->init_logits) {
+        CK(cudaMemcpy2DAsync(w.V, B * 4, o->init_logits, o->init_ld * 4, B * 4, npi, cudaMemcpyDeviceToDevice, str));
+    } else if (o->proposal) {
+        if ((s = sat_mlp_propose(o->proposal, o->seed, o->first_round, o->proposal_tau, w.V, B, B, o->stream)) !=
+            SAT_OK)
+            return s;
+    } else {
+        CK(sat::launch_init_normal(dp, o->seed, o->first_round, o->init_scale, w.V, B, B, str));
+    }
+    CK(cudaMemsetAsync(w.m, 0, npi * B * 4, str));
+    CK(cudaMemsetAsync(w.v, 0, npi * B * 4, str));
+    CK(cudaMemsetAsync(age, 0, (size_t)B * 4, str));
+    CK(cudaEventRecord(ev[1], str));
+    float ms0 = 0.0f;
+    CK(cudaEventSynchronize(ev[1]));
+    CK(cudaEventElapsedTime(&ms0, ev[0], ev[1]));
+    acc.ms_init += ms0;
+    acc.ms_total += ms0;
+    acc.samples = (uint64_t)B;
+    for (int64_t done = 0, e = 0; done < budget; e++) {
+        const int kk = (int)std::min<int64_t>(k, budget - done);
+        CK(cudaEventRecord(ev[0], str));
+        for (int t0 = 1; t0 <= kk; t0 += spl)
+            CK(sat::launch_steps(dp, o->act_dtype, op, w.V, w.m, w.v, B, w.act, w.adj, nullptr, t0,
+                                 std::min(spl, kk - t0 + 1), B, str, age));
+        CK(cudaEventRecord(ev[1], str));
+        CK(sat::launch_threshold(dp, w.V, B, w.bits, w.ldw, w.keys, B, str));
+        CK(sat::launch_hard_eval(dp, w.bits, w.ldw, B, str));
+        CK(sat::launch_cnf_check(dp, w.bits, w.ldw, w.valid, B, str));
+        CK(cudaEventRecord(ev[2], str));
+        uint64_t n = 0;
+        if ((s = sat_dedup_count(d, &n, str)) != SAT_OK) return s;
+        if (n + (uint64_t)B > d->d.pool_capacity) return fail(SAT_ERR_TABLE_FULL, "dedup table is full");
+        CK(sat::launch_dedup_insert(d->d, w.keys, w.valid, B, nullptr, nullptr, d->slot_of, str));
+        CK(cudaEventRecord(ev[3], str));
+        CK(sat::launch_retire(w.valid, age, restart, kk, max_age, B, str));
+        const uint32_t round = o->first_round + 1u + (uint32_t)e;
+        if (o->proposal && (s = sat_mlp_propose(o->proposal, o->seed, round, o->proposal_tau, Vp, B, B, o->stream)) !=
+                               SAT_OK)
+            return s;
+        CK(sat::launch_restart(dp, restart, o->seed, round, o->init_scale, Vp, B, w.V, w.m, w.v, B, B, str));
+        CK(cudaEventRecord(ev[4], str));
+        CK(cudaMemcpyAsync(hvalid.data(), w.valid, w.ldw * 4, cudaMemcpyDeviceToHost, str));
+        CK(cudaMemcpyAsync(hrestart.data(), restart, w.ldw * 4, cudaMemcpyDeviceToHost, str));
+        unsigned int status = 0;
+        CK(cudaMemcpyAsync(&status, d->d.status, sizeof(status), cudaMemcpyDeviceToHost, str));
+        CK(cudaStreamSynchronize(str));
+        if (status) return fail(SAT_ERR_TABLE_FULL, "dedup probe limit reached");
+        uint32_t pst = 0;
+        if ((s = sat_plan_status(p, &pst, 1, str)) != SAT_OK) return s;
+        if (pst) return fail(SAT_ERR_CUDA, "a bounded wait in the step kernel expired (status " + std::to_string(pst) + ")");
+        float ms[4];
+        for (int i = 0; i < 4; i++) CK(cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]));
+        acc.ms_steps += ms[0];
+        acc.ms_verify += ms[1];
+        acc.ms_dedup += ms[2];
+        acc.ms_init += ms[3];
+        acc.ms_total += ms[0] + ms[1] + ms[2] + ms[3];
+        acc.rounds++;
+        for (uint32_t x : hvalid) acc.valid += (uint64_t)__builtin_popcount(x);
+        for (uint32_t x : hrestart) acc.samples += (uint64_t)__builtin_popcount(x);
+        done += kk;
+        if ((s = sat_dedup_count(d, &have, str)) != SAT_OK) return s;
+        if (have >= n_wanted) {
+            result = SAT_OK;
+            break;
+        }
+    }
+    acc.unique = have;
+    if (st) *st = acc;
+    if (result == SAT_PARTIAL) g_err = "budget ended before n_wanted distinct solutions";
+    return result;
+}
+
 sat_status sat_sample_plan(const sat_plan* p, sat_dedup* d, const sat_sample_opts* o, uint64_t n_wanted,
                            sat_sample_stats* st) {
     if (!p || !d || !o) return fail(SAT_ERR_ARG, "NULL argument");
     const int64_t B = o->batch;
     if (B <= 0 || B > d->max_batch) return fail(SAT_ERR_ARG, "batch must be in 1..dedup max_batch");
     if (o->steps < 0 || o->max_rounds < 1 || !opt_ok(&o->opt)) return fail(SAT_ERR_ARG, "bad steps/rounds/optimiser");
+    if (o->check_every < 0 || o->max_age < 0) return fail(SAT_ERR_ARG, "bad check_every / max_age");
     if (o->act_dtype < SAT_ACT_F32 || o->act_dtype > SAT_ACT_F16) return fail(SAT_ERR_ARG, "bad act_dtype");
     if (o->init_logits && o->init_ld < B) return fail(SAT_ERR_ARG, "init_ld < batch");
     sat_status s = check_device(p->device);
@@ -650,6 +794,7 @@ sat_status sat_sample_plan(const sat_plan* p, sat_dedup* d, const sat_sample_opt
         !w.alloc((void**)&w.keys, (size_t)B * std::max(1, dp.key_words) * 4) ||
         !w.alloc((void**)&w.valid, (size_t)w.ldw * 4))
         return fail(SAT_ERR_OOM, "cudaMalloc failed for the sampling workspace");
+    if (o->check_every > 0) return sample_early_exit(p, d, o, n_wanted, st, w, str);
     cudaEvent_t ev[5];
     for (auto& e : ev) CK(cudaEventCreate(&e));
     struct EvGuard {
@@ -732,7 +877,15 @@ sat_status sat_sample(const sat_circuit* c, const sat_cnf* cnf, const sat_sample
         sat_dedup* d = nullptr;
         ~PG() { sat_dedup_free(d); sat_plan_free(p); }
     } pg{p};
-    const uint64_t max_keys = (uint64_t)o->batch * (uint64_t)std::max(1, o->max_rounds);
+    // Early exit can harvest more than one solution per slot and round: room for
+    // n_wanted (capped by the budget's sample-epochs) plus one batch.
+    uint64_t max_keys = (uint64_t)o->batch * (uint64_t)std::max(1, o->max_rounds);
+    if (o->check_every > 0) {
+        const uint64_t epochs = ((uint64_t)std::max(1, o->max_rounds) * (uint64_t)std::max(0, o->steps) +
+                                 (uint64_t)o->check_every - 1) / (uint64_t)o->check_every;
+        max_keys = std::min<uint64_t>(n_wanted, (uint64_t)o->batch * std::max<uint64_t>(1, epochs)) +
+                   (uint64_t)o->batch;
+    }
     if ((s = sat_dedup_create(p, max_keys, o->batch, &pg.d)) != SAT_OK) return s;
     auto t1 = std::chrono::steady_clock::now();
     sat_sample_stats acc{};

@@ -55,9 +55,19 @@ cudaError_t launch_forward(const DevPlan& p, int act_type, const float* V, int64
                            int64_t B, cudaStream_t s);
 cudaError_t launch_backward(const DevPlan& p, int act_type, const float* V, int64_t ldv, const void* act, float* adj,
                             const float* grad_loss, float* gV, int64_t B, cudaStream_t s);
+// Adam step of sample b at in-launch step s: t0 + s, plus age[b] when age is given.
 cudaError_t launch_steps(const DevPlan& p, int act_type, const OptParams& o, float* V, float* m, float* v,
                          int64_t ldv, void* act, float* adj, float* loss, int t0, int n_steps, int64_t B,
-                         cudaStream_t s);
+                         cudaStream_t s, const int32_t* age = nullptr);
+// Early exit: restart[b] = valid(b) or age[b] + k >= max_age (bit-packed like valid);
+// age[b] = 0 where restarting, else age[b] + k.
+cudaError_t launch_retire(const uint32_t* valid, int32_t* age, uint32_t* restart, int k, int max_age, int64_t B,
+                          cudaStream_t s);
+// Restarted samples get a new start: V[:, b] = src[:, b] (src non-null) or scale * N(0, 1)
+// from the init stream of `round` (the values launch_init_normal would draw); m = v = 0.
+cudaError_t launch_restart(const DevPlan& p, const uint32_t* restart, uint64_t seed, uint32_t round, float scale,
+                           const float* src, int64_t lds, float* V, float* m, float* v, int64_t ldv, int64_t B,
+                           cudaStream_t s);
 cudaError_t launch_opt_update(const DevPlan& p, const OptParams& o, float* V, float* m, float* v,
                               const float* gV, int64_t ldv, int t, int64_t B, cudaStream_t s);
 cudaError_t launch_threshold(const DevPlan& p, const float* V, int64_t ldv, uint32_t* node_bits,

@@ -141,11 +141,36 @@ __device__ __forceinline__ uint32_t at(int row, const TileCtx& c) {
     return (uint32_t)row * TILE + (uint32_t)(c.lane * VEC);
 }
 
-// Adam bias corrections (PyTorch: step_size = lr / (1 - b1^t), sqrt(1 - b2^t)),
-// from the running powers b1^t, b2^t kept in double like its host scalars.
-__device__ __forceinline__ void adam_bias(const OptParams& o, double p1, double p2, float& step_size, float& bc2s) {
-    step_size = (float)((double)o.lr / (1.0 - p1));
-    bc2s = (float)sqrt(1.0 - p2);
+// Adam bias corrections at step t >= 1 (PyTorch: step_size = lr / (1 - b1^t),
+// sqrt(1 - b2^t)) in FP32: 1 - b^t = -expm1(t log1p(b - 1)).  b - 1 is exact in
+// FP32 for b in [1/2, 2], so both corrections keep ~1e-7 relative accuracy even
+// where b^t is within 1e-3 of 1 (b2 = 0.999 at t = 1).
+__device__ __forceinline__ void adam_bias(const OptParams& o, int t, float& step_size, float& bc2s) {
+    const float tf = (float)t;
+    step_size = o.lr / -expm1f(tf * log1pf(o.b1 - 1.0f));
+    bc2s = sqrtf(-expm1f(tf * log1pf(o.b2 - 1.0f)));
+}
+
+// Per-sample corrections of this lane's samples: step t, plus age[b] when
+// samples restart at different steps (early exit), else the same t for all.
+struct AdamCorr {
+    float step[VEC], bc2s[VEC];
+};
+__device__ __forceinline__ AdamCorr adam_corr(const OptParams& o, const int32_t* age, int t, const TileCtx& c) {
+    AdamCorr a;
+    if (age == nullptr) {
+        float st, bc;
+        adam_bias(o, t, st, bc);
+#pragma unroll
+        for (int q = 0; q < VEC; q++) {
+            a.step[q] = st;
+            a.bc2s[q] = bc;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < VEC; q++) adam_bias(o, t + (q < c.nvalid ? __ldg(age + c.b + q) : 0), a.step[q], a.bc2s[q]);
+    }
+    return a;
 }
 
 // ------------------------------------------------------ async row copies --
@@ -497,7 +522,7 @@ __device__ __forceinline__ void discard_adj_rows(const DevPlan& p, int l, const 
 // optimiser, UBATCH rows at a time.
 template <typename T, bool UPDATE>
 __device__ void tile_backward(const DevPlan& p, const OptParams& o, float* V, float* m, float* v, float* gV,
-                              int64_t ldv, const T* act, float* adj, const float* grad_loss, double p1, double p2,
+                              int64_t ldv, const T* act, float* adj, const float* grad_loss, const AdamCorr& ac,
                               Stage& st, const TileCtx& c) {
     VF seed_scale = vf_fill(1.0f);
     if (grad_loss != nullptr)
@@ -512,9 +537,7 @@ __device__ void tile_backward(const DevPlan& p, const OptParams& o, float* V, fl
         // Adjoint rows of level l + span have no reader below level l.
         if (l + p.max_span <= p.n_clev) discard_adj_rows(p, l + p.max_span, adj);
     }
-    float step_size = 0.0f, bc2s = 1.0f;
     const bool adam = UPDATE && o.opt == 0;
-    if (adam) adam_bias(o, p1, p2, step_size, bc2s);
     for (int i0 = c.warp * UBATCH; i0 < p.n_cone_pi; i0 += c.nw * UBATCH) {
         VF vv[UBATCH], pb[UBATCH], mm[UBATCH], ss[UBATCH];
         int64_t r[UBATCH];
@@ -545,7 +568,7 @@ __device__ void tile_backward(const DevPlan& p, const OptParams& o, float* V, fl
             for (int q = 0; q < VEC; q++)
                 if (q < c.nvalid)
                     input_update<UPDATE>(o, V, m, v, gV, r[u] + q, vv[u].v[q], pb[u].v[q], mm[u].v[q], ss[u].v[q],
-                                         step_size, bc2s);
+                                         ac.step[q], ac.bc2s[q]);
         }
     }
     __syncthreads();
@@ -587,8 +610,11 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) backward_kernel(DevPlan p, co
     Stage st = init_stage<T>(smem, p, gcoef, c);
     const size_t off = (size_t)blockIdx.x * (size_t)p.n_cone * TILE;
     OptParams o;
+    AdamCorr ac;
+#pragma unroll
+    for (int q = 0; q < VEC; q++) ac.step[q] = ac.bc2s[q] = 1.0f;
     tile_backward<T, false>(p, o, const_cast<float*>(V), nullptr, nullptr, gV, ldv, act + off, adj + off, grad_loss,
-                            0.0, 0.0, st, c);
+                            ac, st, c);
 }
 
 // The fused hot loop: n_steps x (forward, loss, adjoint, update) for one tile;
@@ -596,7 +622,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) backward_kernel(DevPlan p, co
 template <typename T>
 __global__ void __launch_bounds__(STEP_THREADS, 1) steps_kernel(DevPlan p, OptParams o, float* V, float* m, float* v,
                                                                 int64_t ldv, T* act, float* adj, float* loss,
-                                                                double p1, double p2, int n_steps, int64_t B) {
+                                                                int t0, const int32_t* age, int n_steps, int64_t B) {
     extern __shared__ __align__(128) char smem[];
     __shared__ float4 gcoef[16];
     const TileCtx c = tile_ctx(B);
@@ -606,11 +632,11 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) steps_kernel(DevPlan p, OptPa
     float* g = adj + off;
 #pragma unroll 1
     for (int s = 0; s < n_steps; s++) {
-        p1 *= (double)o.b1;
-        p2 *= (double)o.b2;
+        AdamCorr ac;
+        if (o.opt == 0) ac = adam_corr(o, age, t0 + s, c);
         tile_forward<T>(p, V, ldv, a, st, gcoef, c);
         if (loss && s == n_steps - 1) tile_loss<T>(p, a, loss, c);
-        tile_backward<T, true>(p, o, V, m, v, nullptr, ldv, a, g, nullptr, p1, p2, st, c);
+        tile_backward<T, true>(p, o, V, m, v, nullptr, ldv, a, g, nullptr, ac, st, c);
     }
 }
 
@@ -635,10 +661,10 @@ cudaError_t prepare_tile_kernels() {
 }
 
 __global__ void opt_update_kernel(DevPlan p, OptParams o, float* V, float* m, float* v, const float* gV, int64_t ldv,
-                                  double p1, double p2, int64_t B) {
+                                  int t, int64_t B) {
     const int64_t n = (int64_t)p.n_cone_pi * B;
     float step_size = 0.0f, bc2s = 1.0f;
-    adam_bias(o, p1, p2, step_size, bc2s);
+    if (o.opt == 0) adam_bias(o, t, step_size, bc2s);
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = k / B, b = k % B;
         const int64_t r = (int64_t)p.cone_pi_row[i] * ldv + b;
@@ -682,6 +708,42 @@ __global__ void init_normal_kernel(int32_t n_pi, uint64_t seed, uint32_t round, 
         const float u1 = (float)((o.x >> 8) + 1u) * (1.0f / 16777216.0f);
         const float u2 = (float)(o.y >> 8) * (1.0f / 16777216.0f);
         V[r * ldv + b] = scale * sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+    }
+}
+
+// ------------------------------------------------------- early exit -----
+// One thread per sample; a warp's ballot is one restart word (32 samples).
+__global__ void retire_kernel(const uint32_t* valid, int32_t* age, uint32_t* restart, int k, int max_age, int64_t B) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool r = false;
+    if (b < B) {
+        const int a = age[b];
+        r = ((valid[b >> 5] >> (b & 31)) & 1u) != 0u || a + k >= max_age;
+        age[b] = r ? 0 : a + k;
+    }
+    const unsigned w = __ballot_sync(0xffffffffu, r);
+    if ((threadIdx.x & 31) == 0 && b < B) restart[b >> 5] = w;
+}
+
+// Samples on x (coalesced within a row), rows on y (grid-stride).
+__global__ void restart_kernel(int32_t n_pi, const uint32_t* restart, uint64_t seed, uint32_t round, float scale,
+                               const float* src, int64_t lds, float* V, float* m, float* v, int64_t ldv, int64_t B) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B || ((restart[b >> 5] >> (b & 31)) & 1u) == 0u) return;
+    const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    for (int64_t r = blockIdx.y; r < n_pi; r += gridDim.y) {
+        float x;
+        if (src) {
+            x = src[r * lds + b];
+        } else {
+            const uint4 o = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)r, round, 0u), key);
+            const float u1 = (float)((o.x >> 8) + 1u) * (1.0f / 16777216.0f);
+            const float u2 = (float)(o.y >> 8) * (1.0f / 16777216.0f);
+            x = scale * sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+        }
+        V[r * ldv + b] = x;
+        m[r * ldv + b] = 0.0f;
+        v[r * ldv + b] = 0.0f;
     }
 }
 
@@ -878,12 +940,12 @@ cudaError_t backward_launch(const DevPlan& p, const float* V, int64_t ldv, const
 
 template <typename T>
 cudaError_t steps_launch(const DevPlan& p, const OptParams& o, float* V, float* m, float* v, int64_t ldv, void* act,
-                         float* adj, float* loss, int t0, int n_steps, int64_t B, cudaStream_t s) {
+                         float* adj, float* loss, int t0, const int32_t* age, int n_steps, int64_t B,
+                         cudaStream_t s) {
     cudaError_t e = prepare_tile_kernels<T>();
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)((B + TILE - 1) / TILE);
-    const double p1 = std::pow((double)o.b1, (double)(t0 - 1)), p2 = std::pow((double)o.b2, (double)(t0 - 1));
-    steps_kernel<T><<<grid, STEP_THREADS, stage_smem<T>(), s>>>(p, o, V, m, v, ldv, (T*)act, adj, loss, p1, p2,
+    steps_kernel<T><<<grid, STEP_THREADS, stage_smem<T>(), s>>>(p, o, V, m, v, ldv, (T*)act, adj, loss, t0, age,
                                                                 n_steps, B);
     return cudaGetLastError();
 }
@@ -921,12 +983,13 @@ cudaError_t launch_backward(const DevPlan& p, int act_type, const float* V, int6
 }
 
 cudaError_t launch_steps(const DevPlan& p, int act_type, const OptParams& o, float* V, float* m, float* v, int64_t ldv,
-                         void* act, float* adj, float* loss, int t0, int n_steps, int64_t B, cudaStream_t s) {
+                         void* act, float* adj, float* loss, int t0, int n_steps, int64_t B, cudaStream_t s,
+                         const int32_t* age) {
     if (B == 0 || n_steps <= 0) return cudaSuccess;
     switch (act_type) {
-    case ACT_F32: return steps_launch<float>(p, o, V, m, v, ldv, act, adj, loss, t0, n_steps, B, s);
-    case ACT_BF16: return steps_launch<__nv_bfloat16>(p, o, V, m, v, ldv, act, adj, loss, t0, n_steps, B, s);
-    default: return steps_launch<__half>(p, o, V, m, v, ldv, act, adj, loss, t0, n_steps, B, s);
+    case ACT_F32: return steps_launch<float>(p, o, V, m, v, ldv, act, adj, loss, t0, age, n_steps, B, s);
+    case ACT_BF16: return steps_launch<__nv_bfloat16>(p, o, V, m, v, ldv, act, adj, loss, t0, age, n_steps, B, s);
+    default: return steps_launch<__half>(p, o, V, m, v, ldv, act, adj, loss, t0, age, n_steps, B, s);
     }
 }
 
@@ -935,8 +998,23 @@ cudaError_t launch_opt_update(const DevPlan& p, const OptParams& o, float* V, fl
     const int64_t n = (int64_t)p.n_cone_pi * B;
     if (n == 0) return cudaSuccess;
     const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 148 * 32);
-    const double p1 = std::pow((double)o.b1, (double)t), p2 = std::pow((double)o.b2, (double)t);
-    opt_update_kernel<<<grid, 256, 0, s>>>(p, o, V, m, v, gV, ldv, p1, p2, B);
+    opt_update_kernel<<<grid, 256, 0, s>>>(p, o, V, m, v, gV, ldv, t, B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_retire(const uint32_t* valid, int32_t* age, uint32_t* restart, int k, int max_age, int64_t B,
+                          cudaStream_t s) {
+    if (B == 0) return cudaSuccess;
+    retire_kernel<<<(unsigned)((B + 255) / 256), 256, 0, s>>>(valid, age, restart, k, max_age, B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_restart(const DevPlan& p, const uint32_t* restart, uint64_t seed, uint32_t round, float scale,
+                           const float* src, int64_t lds, float* V, float* m, float* v, int64_t ldv, int64_t B,
+                           cudaStream_t s) {
+    if (B == 0 || p.n_pi == 0) return cudaSuccess;
+    const dim3 grid((unsigned)((B + 255) / 256), (unsigned)std::min<int64_t>(p.n_pi, 256));
+    restart_kernel<<<grid, 256, 0, s>>>(p.n_pi, restart, seed, round, scale, src, lds, V, m, v, ldv, B);
     return cudaGetLastError();
 }
 
