@@ -17,9 +17,12 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <cstring>
+#include <type_traits>
 #include <cmath>
 
 #include "device.hpp"
+#include "tmap.hpp"
 
 namespace sat {
 namespace {
@@ -30,7 +33,7 @@ namespace {
 constexpr int VEC = SAT_VEC;           // consecutive samples per lane
 constexpr int TILE = 32 * VEC;         // samples per CTA
 static_assert(TILE == SAT_TILE_SAMPLES, "tile width must match the ABI");
-constexpr int STEP_THREADS = 512;
+constexpr int STEP_THREADS = 640;
 constexpr int UBATCH = 2;              // input rows per warp in the input-level passes
 constexpr unsigned FULL = 0xffffffffu;
 
@@ -174,17 +177,19 @@ __device__ __forceinline__ AdamCorr adam_corr(const OptParams& o, const int32_t*
 }
 
 // ------------------------------------------------------ async row copies --
-// Rows of a tile's scratch block are staged into shared memory by the bulk
-// copy engine (cp.async.bulk, one instruction per row, completion counted in
-// bytes on an mbarrier).  Each warp owns NSLOT slots and keeps NSLOT-1 chunks
-// in flight while it computes on the oldest one.  Every mbarrier wait is
+// Rows of a tile's scratch block are staged into shared memory by the TMA
+// engine: a chunk's rows come as tile::gather4 loads (four arbitrary rows per
+// instruction through a 2-D tensor map over all tiles' rows, box = one row),
+// completion counted in bytes on an mbarrier.  Each warp owns NSLOT slots and
+// keeps NSLOT-1 chunks in flight while it computes on the oldest one.  Every mbarrier wait is
 // bounded: on expiry the kernel records STATUS_WAIT_TIMEOUT in the plan's
 // status word and carries on (results are then invalid, the GPU is not hung).
 #ifndef SAT_CHUNK
 #define SAT_CHUNK 4
 #endif
 constexpr int CHUNK = SAT_CHUNK;  // gates (forward) or fan-out edges (adjoint) per chunk
-constexpr int NSLOT = 3;   // pipeline depth per warp
+constexpr int NSLOT = 2;   // pipeline depth per warp (gathers land one chunk ahead: 93% of waits succeed at once)
+static_assert(CHUNK == 4, "a chunk is one tile::gather4 load (4 rows) per operand");
 constexpr unsigned STATUS_WAIT_TIMEOUT = 4u;
 constexpr uint32_t WAIT_LIMIT = 1u << 24;
 
@@ -205,23 +210,32 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Global -> shared bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned).
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-// Bulk copy with an L2 eviction-priority policy (streaming reads that should
-// not displace the rows reused within the next few levels).
-__device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
-                                              uint64_t policy) {
+// Rows r0..r3 (each one full tensor-map row) -> dst, dst + row, ... (dense).
+__device__ __forceinline__ void gather4(void* dst, const CUtensorMap* map, int r0, int r1, int r2, int r3,
+                                        uint64_t* bar) {
     asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
-            "r"(smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+        "%4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(smem_u32(bar))
         : "memory");
 }
+__device__ __forceinline__ void gather4_hint(void* dst, const CUtensorMap* map, int r0, int r1, int r2, int r3,
+                                             uint64_t* bar, uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes.L2::cache_hint [%0], "
+        "[%1, {%2, %3, %4, %5, %6}], [%7], %8;" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(smem_u32(bar)),
+        "l"(policy)
+        : "memory");
+}
+
+// Tensor maps over the scratch rows of all tiles (row = tile * n_cone + node).
+struct RowMaps {
+    const CUtensorMap* act;
+    const CUtensorMap* adj;
+    int row0;  // this tile's first row
+};
+
 __device__ __forceinline__ uint64_t policy_evict_first() {
     uint64_t pol;
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
@@ -289,12 +303,12 @@ __device__ __forceinline__ void stage_wait(Stage& st, int s) {
 // Forward pass of one tile: P = sigmoid(V) for the cone inputs, then every cone
 // level.  Within a level each warp takes a contiguous run of gates; 32 gate
 // records come in one coalesced load and are broadcast by shuffles; the two
-// input rows of each gate are bulk-copied into shared memory, CHUNK gates per
-// slot, NSLOT-1 chunks ahead of the computation.  gcoef: the 16 bilinear
+// input rows of each gate are gathered into shared memory (two gather4 loads
+// per CHUNK = 4 gates), NSLOT-1 chunks ahead of the computation.  gcoef: the 16 bilinear
 // coefficient sets in shared memory.
 template <typename T>
 __device__ void tile_forward(const DevPlan& p, const float* __restrict__ V, int64_t ldv, T* act, Stage& st,
-                             const float4* gcoef, const TileCtx& c) {
+                             const float4* gcoef, const RowMaps& rm, const TileCtx& c) {
     constexpr int ROWB = TILE * (int)sizeof(T);
     constexpr int SLOT = slot_bytes<T>();
     for (int i0 = c.warp * UBATCH; i0 < p.n_cone_pi; i0 += c.nw * UBATCH) {
@@ -323,27 +337,45 @@ __device__ void tile_forward(const DevPlan& p, const float* __restrict__ V, int6
     }
     fence_async_global();
     __syncthreads();
-    const char* abytes = reinterpret_cast<const char*>(act);
-    for (int l = 1; l <= p.n_clev; l++) {
+    // This warp's gate run of level l and its first 32 gate records; those of the
+    // next level are loaded before the level barrier, so that their latency
+    // overlaps the wait for the other warps.
+    auto level_run = [&](int l, int& g0, int& g1, int2& first) {
         const int lo = __ldg(&p.c_level_off[l]), hi = __ldg(&p.c_level_off[l + 1]);
         const int per = (hi - lo + c.nw - 1) / c.nw;
-        const int g0 = lo + c.warp * per, g1 = min(g0 + per, hi);
+        g0 = lo + c.warp * per;
+        g1 = min(g0 + per, hi);
+        first = make_int2(0, 0);
+        if (c.lane < g1 - g0) first = __ldg(&p.c_gate[g0 + c.lane - p.n_cone_pi]);
+    };
+    int g0 = 0, g1 = 0;
+    int2 first = make_int2(0, 0);
+    if (p.n_clev >= 1) level_run(1, g0, g1, first);
+    for (int l = 1; l <= p.n_clev; l++) {
         for (int base = g0; base < g1; base += 32) {
             const int cnt = min(32, g1 - base);
-            int2 mine = make_int2(0, 0);
-            if (c.lane < cnt) mine = __ldg(&p.c_gate[base + c.lane - p.n_cone_pi]);
+            int2 mine = first;
+            if (base != g0) {
+                mine = make_int2(0, 0);
+                if (c.lane < cnt) mine = __ldg(&p.c_gate[base + c.lane - p.n_cone_pi]);
+            }
             const int nch = (cnt + CHUNK - 1) / CHUNK;
             auto issue = [&](int ch) {
                 const int s = ch % NSLOT;
-                const int ne = min(CHUNK, cnt - ch * CHUNK);
-                const int src = ch * CHUNK + (c.lane >> 1);
-                const int x = __shfl_sync(FULL, mine.x, src & 31) & 0x0FFFFFFF;
-                const int y = __shfl_sync(FULL, mine.y, src & 31);
-                if (c.lane == 0) mbar_expect_tx(st.bar + s, (uint32_t)(2 * ne * ROWB));
-                __syncwarp();
-                if (c.lane < 2 * ne)
-                    bulk_g2s(st.buf + s * SLOT + c.lane * ROWB, abytes + (size_t)((c.lane & 1) ? y : x) * ROWB, ROWB,
-                             st.bar + s);
+                // first inputs of the chunk's 4 gates -> rows 0..3, second inputs -> rows 4..7
+                // (a partial chunk repeats its last gate)
+                int xr[CHUNK], yr[CHUNK];
+#pragma unroll
+                for (int j = 0; j < CHUNK; j++) {
+                    const int gl = min(ch * CHUNK + j, cnt - 1);
+                    xr[j] = rm.row0 + (__shfl_sync(FULL, mine.x, gl & 31) & 0x0FFFFFFF);
+                    yr[j] = rm.row0 + __shfl_sync(FULL, mine.y, gl & 31);
+                }
+                if (c.lane == 0) {
+                    mbar_expect_tx(st.bar + s, (uint32_t)(2 * CHUNK * ROWB));
+                    gather4(st.buf + s * SLOT, rm.act, xr[0], xr[1], xr[2], xr[3], st.bar + s);
+                    gather4(st.buf + s * SLOT + CHUNK * ROWB, rm.act, yr[0], yr[1], yr[2], yr[3], st.bar + s);
+                }
             };
             for (int ch = 0; ch < NSLOT - 1 && ch < nch; ch++) issue(ch);
             for (int ch = 0; ch < nch; ch++) {
@@ -357,8 +389,8 @@ __device__ void tile_forward(const DevPlan& p, const float* __restrict__ V, int6
                     const uint32_t gop = (uint32_t)__shfl_sync(FULL, mine.x, gl & 31) >> 28;
                     if (gl < cnt) {
                         const float4 k = gcoef[gop];
-                        const VF x = ActIO<T>::ld(reinterpret_cast<const T*>(sb + (2 * j) * ROWB) + c.lane * VEC);
-                        const VF y = ActIO<T>::ld(reinterpret_cast<const T*>(sb + (2 * j + 1) * ROWB) + c.lane * VEC);
+                        const VF x = ActIO<T>::ld(reinterpret_cast<const T*>(sb + j * ROWB) + c.lane * VEC);
+                        const VF y = ActIO<T>::ld(reinterpret_cast<const T*>(sb + (CHUNK + j) * ROWB) + c.lane * VEC);
                         VF z;
 #pragma unroll
                         for (int q = 0; q < VEC; q++) z.v[q] = gate_apply(k, x.v[q], y.v[q]);
@@ -369,6 +401,7 @@ __device__ void tile_forward(const DevPlan& p, const float* __restrict__ V, int6
                 __syncwarp();
             }
         }
+        if (l < p.n_clev) level_run(l + 1, g0, g1, first);
         fence_async_global();
         __syncthreads();
     }
@@ -403,48 +436,74 @@ __device__ void tile_loss(const DevPlan& p, const T* act, float* loss, const Til
 // contiguous run of nodes, whose fan-out edges are contiguous in the CSR and
 // are summed in CSR order.  An edge contributes ga * (c0 + c1 * A_sibling)
 // with ga the consumer's adjoint, or seed_scale for an output seed.  The
-// consumer-adjoint and sibling rows are bulk-copied into shared memory, CHUNK
-// edges per slot.
+// consumer-adjoint and sibling rows are gathered into shared memory (one
+// gather4 load each per CHUNK = 4 edges).
+// This warp's node run [u0, u1) of a cone level with the CSR offsets of its first
+// 31 nodes and its first 32 fan-out edges, loaded ahead (before the barrier of
+// the level above) so that the three dependent loads do not stall the level.
+struct AdjRun {
+    int u0, u1, off;
+    int4 first;
+};
+__device__ __forceinline__ AdjRun adj_run(const DevPlan& p, int l, const TileCtx& c) {
+    const int lo = l == 0 ? 0 : __ldg(&p.c_level_off[l]);
+    const int hi = l == 0 ? p.n_cone_pi : __ldg(&p.c_level_off[l + 1]);
+    const int per = (hi - lo + c.nw - 1) / c.nw;
+    AdjRun r;
+    r.u0 = lo + c.warp * per;
+    r.u1 = min(r.u0 + per, hi);
+    r.off = 0;
+    r.first = make_int4(-1, 0, 0, 0);
+    if (r.u0 < r.u1) {
+        const int nn = min(31, r.u1 - r.u0);
+        r.off = (c.lane <= nn) ? __ldg(&p.fo_off[r.u0 + c.lane]) : 0;
+        const int e_begin = __shfl_sync(FULL, r.off, 0), e_end = __shfl_sync(FULL, r.off, nn);
+        if (c.lane < min(32, e_end - e_begin)) r.first = __ldg(&p.fo_edge[e_begin + c.lane]);
+    }
+    return r;
+}
+
 template <typename T>
-__device__ void level_adjoint(const DevPlan& p, int lo, int hi, const T* act, float* adj, const VF& seed_scale,
-                              Stage& st, const TileCtx& c) {
+__device__ void level_adjoint(const DevPlan& p, const AdjRun& run, const T* act, float* adj, const VF& seed_scale,
+                              Stage& st, const RowMaps& rm, const TileCtx& c) {
     constexpr int ROWB = TILE * (int)sizeof(T);
     constexpr int ROWF = TILE * 4;
     constexpr int SLOT = slot_bytes<T>();
-    const char* abytes = reinterpret_cast<const char*>(act);
-    const char* gbytes = reinterpret_cast<const char*>(adj);
     const uint64_t stream_policy = policy_evict_first();
-    const int per = (hi - lo + c.nw - 1) / c.nw;
-    const int u0 = lo + c.warp * per, u1 = min(u0 + per, hi);
+    const int u0 = run.u0, u1 = run.u1;
     for (int ua = u0; ua < u1; ua += 31) {
         const int nn = min(31, u1 - ua);
-        const int off = (c.lane <= nn) ? __ldg(&p.fo_off[ua + c.lane]) : 0;
+        const int off = ua == u0 ? run.off : ((c.lane <= nn) ? __ldg(&p.fo_off[ua + c.lane]) : 0);
         const int e_begin = __shfl_sync(FULL, off, 0), e_end = __shfl_sync(FULL, off, nn);
         int k = 0;
         int k_end = __shfl_sync(FULL, off, 1);
         VF acc = vf_fill(0.0f);
         for (int base = e_begin; base < e_end; base += 32) {
             const int cnt = min(32, e_end - base);
-            int4 mine = make_int4(-1, 0, 0, 0);
-            if (c.lane < cnt) mine = __ldg(&p.fo_edge[base + c.lane]);
+            int4 mine = run.first;
+            if (ua != u0 || base != e_begin) {
+                mine = make_int4(-1, 0, 0, 0);
+                if (c.lane < cnt) mine = __ldg(&p.fo_edge[base + c.lane]);
+            }
             const int nch = (cnt + CHUNK - 1) / CHUNK;
             auto issue = [&](int ch) {
                 const int s = ch % NSLOT;
-                const int ne = min(CHUNK, cnt - ch * CHUNK);
-                const int j = c.lane & (CHUNK - 1);
-                const int src = (ch * CHUNK + j) & 31;
-                const int g = __shfl_sync(FULL, mine.x, src);
-                const int sib = __shfl_sync(FULL, mine.y, src);
-                const bool adj_row = c.lane < CHUNK && j < ne && g >= 0;
-                const bool act_row = c.lane >= CHUNK && c.lane < 2 * CHUNK && j < ne;
-                const uint32_t nadj = __popc(__ballot_sync(FULL, adj_row));
-                if (c.lane == 0) mbar_expect_tx(st.bar + s, nadj * ROWF + (uint32_t)ne * ROWB);
-                __syncwarp();
-                char* sb = st.buf + s * SLOT;
-                if (adj_row) bulk_g2s(sb + j * ROWF, gbytes + (size_t)g * ROWF, ROWF, st.bar + s);
-                if (act_row)
-                    bulk_g2s_hint(sb + CHUNK * ROWF + j * ROWB, abytes + (size_t)sib * ROWB, ROWB, st.bar + s,
-                                  stream_policy);
+                // consumer adjoints -> the 4 fp32 rows, siblings -> the 4 act rows; an output
+                // seed (no consumer) and the tail of a partial chunk load a stand-in row
+                int gr[CHUNK], sr[CHUNK];
+#pragma unroll
+                for (int j = 0; j < CHUNK; j++) {
+                    const int el = min(ch * CHUNK + j, cnt - 1);
+                    const int g = __shfl_sync(FULL, mine.x, el & 31);
+                    gr[j] = rm.row0 + max(g, 0);
+                    sr[j] = rm.row0 + __shfl_sync(FULL, mine.y, el & 31);
+                }
+                if (c.lane == 0) {
+                    char* sb = st.buf + s * SLOT;
+                    mbar_expect_tx(st.bar + s, (uint32_t)(CHUNK * ROWF + CHUNK * ROWB));
+                    gather4(sb, rm.adj, gr[0], gr[1], gr[2], gr[3], st.bar + s);
+                    gather4_hint(sb + CHUNK * ROWF, rm.act, sr[0], sr[1], sr[2], sr[3], st.bar + s, stream_policy);
+                }
             };
             for (int ch = 0; ch < NSLOT - 1 && ch < nch; ch++) issue(ch);
             for (int ch = 0; ch < nch; ch++) {
@@ -523,15 +582,15 @@ __device__ __forceinline__ void discard_adj_rows(const DevPlan& p, int l, const 
 template <typename T, bool UPDATE>
 __device__ void tile_backward(const DevPlan& p, const OptParams& o, float* V, float* m, float* v, float* gV,
                               int64_t ldv, const T* act, float* adj, const float* grad_loss, const AdamCorr& ac,
-                              Stage& st, const TileCtx& c) {
+                              Stage& st, const RowMaps& rm, const TileCtx& c) {
     VF seed_scale = vf_fill(1.0f);
     if (grad_loss != nullptr)
 #pragma unroll
         for (int q = 0; q < VEC; q++) seed_scale.v[q] = q < c.nvalid ? grad_loss[c.b + q] : 0.0f;
+    AdjRun run = adj_run(p, p.n_clev, c);
     for (int l = p.n_clev; l >= 0; l--) {
-        const int lo = l == 0 ? 0 : __ldg(&p.c_level_off[l]);
-        const int hi = l == 0 ? p.n_cone_pi : __ldg(&p.c_level_off[l + 1]);
-        level_adjoint<T>(p, lo, hi, act, adj, seed_scale, st, c);
+        level_adjoint<T>(p, run, act, adj, seed_scale, st, rm, c);
+        if (l > 0) run = adj_run(p, l - 1, c);
         fence_async_global();
         __syncthreads();
         // Adjoint rows of level l + span have no reader below level l.
@@ -590,20 +649,24 @@ __device__ __forceinline__ Stage init_stage(char* smem, const DevPlan& p, float4
 
 template <typename T>
 __global__ void __launch_bounds__(STEP_THREADS, 1) forward_kernel(DevPlan p, const float* V, int64_t ldv, T* act,
-                                                                  float* loss, int64_t B) {
+                                                                  float* loss, int64_t B,
+                                                                  const __grid_constant__ CUtensorMap amap) {
     extern __shared__ __align__(128) char smem[];
     __shared__ float4 gcoef[16];
     const TileCtx c = tile_ctx(B);
     Stage st = init_stage<T>(smem, p, gcoef, c);
     T* a = act + (size_t)blockIdx.x * (size_t)p.n_cone * TILE;
-    tile_forward<T>(p, V, ldv, a, st, gcoef, c);
+    const RowMaps rm{&amap, &amap, (int)(blockIdx.x * (int64_t)p.n_cone)};
+    tile_forward<T>(p, V, ldv, a, st, gcoef, rm, c);
     if (loss) tile_loss<T>(p, a, loss, c);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(STEP_THREADS, 1) backward_kernel(DevPlan p, const float* V, int64_t ldv,
                                                                    const T* act, float* adj, const float* grad_loss,
-                                                                   float* gV, int64_t B) {
+                                                                   float* gV, int64_t B,
+                                                                   const __grid_constant__ CUtensorMap amap,
+                                                                   const __grid_constant__ CUtensorMap gmap) {
     extern __shared__ __align__(128) char smem[];
     __shared__ float4 gcoef[16];
     const TileCtx c = tile_ctx(B);
@@ -613,16 +676,19 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) backward_kernel(DevPlan p, co
     AdamCorr ac;
 #pragma unroll
     for (int q = 0; q < VEC; q++) ac.step[q] = ac.bc2s[q] = 1.0f;
+    const RowMaps rm{&amap, &gmap, (int)(blockIdx.x * (int64_t)p.n_cone)};
     tile_backward<T, false>(p, o, const_cast<float*>(V), nullptr, nullptr, gV, ldv, act + off, adj + off, grad_loss,
-                            ac, st, c);
+                            ac, st, rm, c);
 }
 
-// The fused hot loop: n_steps x (forward, loss, adjoint, update) for one tile;
-// p1, p2 = b1^(t0-1), b2^(t0-1).
+// The fused hot loop: n_steps x (forward, loss, adjoint, update) for one tile,
+// at Adam steps t0 + s (+ age[b] per sample when age is given).
 template <typename T>
 __global__ void __launch_bounds__(STEP_THREADS, 1) steps_kernel(DevPlan p, OptParams o, float* V, float* m, float* v,
                                                                 int64_t ldv, T* act, float* adj, float* loss,
-                                                                int t0, const int32_t* age, int n_steps, int64_t B) {
+                                                                int t0, const int32_t* age, int n_steps, int64_t B,
+                                                                const __grid_constant__ CUtensorMap amap,
+                                                                const __grid_constant__ CUtensorMap gmap) {
     extern __shared__ __align__(128) char smem[];
     __shared__ float4 gcoef[16];
     const TileCtx c = tile_ctx(B);
@@ -630,13 +696,14 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) steps_kernel(DevPlan p, OptPa
     const size_t off = (size_t)blockIdx.x * (size_t)p.n_cone * TILE;
     T* a = act + off;
     float* g = adj + off;
+    const RowMaps rm{&amap, &gmap, (int)(blockIdx.x * (int64_t)p.n_cone)};
 #pragma unroll 1
     for (int s = 0; s < n_steps; s++) {
         AdamCorr ac;
         if (o.opt == 0) ac = adam_corr(o, age, t0 + s, c);
-        tile_forward<T>(p, V, ldv, a, st, gcoef, c);
+        tile_forward<T>(p, V, ldv, a, st, gcoef, rm, c);
         if (loss && s == n_steps - 1) tile_loss<T>(p, a, loss, c);
-        tile_backward<T, true>(p, o, V, m, v, nullptr, ldv, a, g, nullptr, ac, st, c);
+        tile_backward<T, true>(p, o, V, m, v, nullptr, ldv, a, g, nullptr, ac, st, rm, c);
     }
 }
 
@@ -919,12 +986,41 @@ __global__ void dedup_commit_kernel(DevDedup d, const uint32_t* keys, int64_t B,
 }
 
 template <typename T>
+constexpr CUtensorMapDataType tmap_type() {
+    return sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                          : (std::is_same<T, __half>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                            : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+}
+
+// Maps over the act (type T) and adj (fp32) scratch of `tiles` tiles: one row per
+// (tile, cone node), TILE elements wide, box = one row (for tile::gather4).
+// With an empty cone the maps stay zero and unused.
+template <typename T>
+cudaError_t row_maps(const DevPlan& p, const void* act, const float* adj, unsigned tiles, CUtensorMap* amap,
+                     CUtensorMap* gmap) {
+    memset(amap, 0, sizeof(*amap));
+    memset(gmap, 0, sizeof(*gmap));
+    if (p.n_cone == 0 || tiles == 0) return cudaSuccess;
+    const int64_t rows = (int64_t)tiles * p.n_cone;
+    if (rows > 0x7fffffff) return cudaErrorInvalidValue;  // row coordinates are int32
+    if (act && !encode_2d(amap, act, tmap_type<T>(), (int)sizeof(T), rows, TILE, TILE, TILE, 1,
+                          CU_TENSOR_MAP_SWIZZLE_NONE))
+        return cudaErrorInvalidValue;
+    if (adj && !encode_2d(gmap, adj, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, rows, TILE, TILE, TILE, 1,
+                          CU_TENSOR_MAP_SWIZZLE_NONE))
+        return cudaErrorInvalidValue;
+    return cudaSuccess;
+}
+
+template <typename T>
 cudaError_t forward_launch(const DevPlan& p, const float* V, int64_t ldv, void* act, float* loss, int64_t B,
                            cudaStream_t s) {
     cudaError_t e = prepare_tile_kernels<T>();
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)((B + TILE - 1) / TILE);
-    forward_kernel<T><<<grid, STEP_THREADS, stage_smem<T>(), s>>>(p, V, ldv, (T*)act, loss, B);
+    CUtensorMap amap, gmap;
+    if ((e = row_maps<T>(p, act, nullptr, grid, &amap, &gmap)) != cudaSuccess) return e;
+    forward_kernel<T><<<grid, STEP_THREADS, stage_smem<T>(), s>>>(p, V, ldv, (T*)act, loss, B, amap);
     return cudaGetLastError();
 }
 
@@ -934,7 +1030,10 @@ cudaError_t backward_launch(const DevPlan& p, const float* V, int64_t ldv, const
     cudaError_t e = prepare_tile_kernels<T>();
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)((B + TILE - 1) / TILE);
-    backward_kernel<T><<<grid, STEP_THREADS, stage_smem<T>(), s>>>(p, V, ldv, (const T*)act, adj, grad_loss, gV, B);
+    CUtensorMap amap, gmap;
+    if ((e = row_maps<T>(p, act, adj, grid, &amap, &gmap)) != cudaSuccess) return e;
+    backward_kernel<T><<<grid, STEP_THREADS, stage_smem<T>(), s>>>(p, V, ldv, (const T*)act, adj, grad_loss, gV, B,
+                                                                   amap, gmap);
     return cudaGetLastError();
 }
 
@@ -945,8 +1044,10 @@ cudaError_t steps_launch(const DevPlan& p, const OptParams& o, float* V, float* 
     cudaError_t e = prepare_tile_kernels<T>();
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)((B + TILE - 1) / TILE);
+    CUtensorMap amap, gmap;
+    if ((e = row_maps<T>(p, act, adj, grid, &amap, &gmap)) != cudaSuccess) return e;
     steps_kernel<T><<<grid, STEP_THREADS, stage_smem<T>(), s>>>(p, o, V, m, v, ldv, (T*)act, adj, loss, t0, age,
-                                                                n_steps, B);
+                                                                n_steps, B, amap, gmap);
     return cudaGetLastError();
 }
 
