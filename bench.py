@@ -43,6 +43,8 @@ WORKLOADS = {
                            batch=262144, steps=500, lr=0.1, init_scale=1.0, act_dtype="f16"),
     "planted3sat": dict(kind="planted3sat", n_vars=50, n_clauses=200, seed=1,
                         batch=1024, steps=200, lr=0.1, init_scale=1.0, act_dtype="f32"),
+    "tseitin1m_bf16": dict(kind="tseitin", n_pi=50000, n_gates=1000000, depth=200, n_out=256, seed=1,
+                           batch=8192, steps=500, lr=0.1, init_scale=1.0, act_dtype="bf16"),
 }
 ACT_BYTES = {"f32": 4, "bf16": 2, "f16": 2}
 
@@ -181,10 +183,11 @@ def kernel_source_hash():
 def oracle_sample(text, w, n_samples, n_steps):
     """Time the CPU oracle on a bounded sample: n_samples x n_steps + verification."""
     import oracle
-    orc = oracle.Oracle(text)
+    orc = oracle.Oracle(text, direct=w.get("direct", False))
     V0 = oracle.init_normal(n_samples, orc.n_pi, seed=0, rnd=0, scale=w["init_scale"])
     t0 = time.perf_counter()
-    res = oracle.sample_round(orc.flat, orc.n_vars, orc.clauses, V0, steps=n_steps, lr=w["lr"])
+    res = oracle.sample_round(orc.flat, orc.n_vars, orc.clauses, V0, steps=n_steps, lr=w["lr"],
+                              opt=w.get("optimizer", "adam"))
     dt = time.perf_counter() - t0
     n_cone_gates = sum(1 for _ in orc.flat.ins_out)  # oracle instructions evaluated per sample-step
     return {"seconds": dt, "valid": int(res["valid"].sum()), "unique": len(res["unique"]),
@@ -201,7 +204,7 @@ def cpu_baseline_entry(text, w, budget_s=15.0):
     r = oracle_sample(text, w, n, steps)
     return {"value": r["unique"] / r["seconds"], "unit": "unique valid solutions/s", "cores": r["threads"],
             "kind": "oracle",
-            "sample": f"{n} samples x {steps} Adam steps (+verify) of the same workload, FP64, "
+            "sample": f"{n} samples x {steps} {w.get('optimizer', 'adam')} steps (+verify) of the same workload, FP64, "
                       f"{r['valid']} valid / {r['unique']} unique in {r['seconds']:.1f} s",
             "sample_steps_per_s": n * steps / r["seconds"]}
 
@@ -261,6 +264,40 @@ def run_mlp(args, w):
                       "frac_of_bf16_peak": flops / (ms / 1e3) / 1e12 / peak, "status": mlp.status()}))
 
 
+def run_curve(P, torch, plan, ws, opt, args, w, info):
+    """Distinct valid solutions against the number of descent iterations per round
+    (the unique-vs-iterations view of the paper's Fig. 3 on the synthetic workload)."""
+    B = w["batch"]
+    steps_list = [int(x) for x in args.curve.split(",") if x]
+    dedup = P.Dedup.create(plan, max_keys=B * (2 + args.steps) * len(steps_list), max_batch=B)
+    stream = torch.cuda.current_stream()
+    points, r = [], 0
+    for n in steps_list:
+        def one(k):
+            P.run_round(plan, ws, opt, n, seed=0, round_=k, init_scale=w["init_scale"], dedup=dedup)
+        one(r)
+        r += 1
+        torch.cuda.synchronize()
+        before, valid = dedup.count(), 0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            one(r)
+            r += 1
+            valid += int(P.valid_mask(ws.valid, B).sum())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        uniq = dedup.count() - before
+        points.append({"iterations": n, "unique_per_round": uniq / args.steps, "valid_fraction": valid / (B * args.steps),
+                       "unique_per_s": uniq / (ms / 1e3), "ms_per_round": ms / args.steps})
+    print(json.dumps({"metric": "unique CNF-valid solutions vs descent iterations", "workload": args.workload,
+                      "batch": B, "optimizer": args.optimizer, "lr": w["lr"], "act_dtype": w["act_dtype"],
+                      "relaxation": "direct CNF" if args.direct else "Algorithm 1", "rounds_per_point": args.steps,
+                      "plan": {k: info[k] for k in ("n_pi", "n_cone_gates", "n_cone_levels")}, "points": points}),
+          flush=True)
+
+
 # --------------------------------------------------------------------------
 def main():
     ap = argparse.ArgumentParser()
@@ -284,6 +321,12 @@ def main():
     ap.add_argument("--check-every", type=int, default=0,
                     help="early exit: verify every K steps, harvest valid samples and restart their slots")
     ap.add_argument("--max-age", type=int, default=0, help="early exit: restart samples unsolved after this many steps")
+    ap.add_argument("--direct", action="store_true",
+                    help="relax the CNF directly (one OR output per clause, no factorization): the ablation")
+    ap.add_argument("--optimizer", default="adam", choices=["adam", "gd"])
+    ap.add_argument("--lr", type=float, default=0.0, help="override the workload's learning rate")
+    ap.add_argument("--curve", default="",
+                    help="comma-separated step counts: unique solutions vs iterations (one JSON line)")
     ap.add_argument("--mlp", action="store_true",
                     help="time only the proposal network's inference GEMMs (tcgen05) at the workload's batch")
     args = ap.parse_args()
@@ -293,6 +336,9 @@ def main():
         w["batch"] = args.batch
     if args.gd_steps:
         w["steps"] = args.gd_steps
+    if args.lr:
+        w["lr"] = args.lr
+    w["optimizer"], w["direct"] = args.optimizer, args.direct
     if args.impl == "reference":
         return run_reference(args, w)
     if args.mlp:
@@ -312,13 +358,15 @@ def main():
     text = instance_text(w, planted_seed=17 if args.proposal == "heldout" else None)
     cnf = P.Cnf.from_dimacs(text)
     t0 = time.perf_counter()
-    circ = P.Circuit.build(cnf)
+    circ = P.Circuit.build(cnf, direct=args.direct)
     transform_s = time.perf_counter() - t0
     plan = P.Plan.create(circ, cnf)
     info = plan.info
     B, steps, ad = w["batch"], w["steps"], w["act_dtype"]
-    opt = P.opt_params("adam", lr=w["lr"])
+    opt = P.opt_params(args.optimizer, lr=w["lr"])
     ws = P.new_workspace(plan, B, ad)
+    if args.curve:
+        return run_curve(P, torch, plan, ws, opt, args, w, info)
     n_rounds = args.warmup + args.steps
     harvest_rounds = n_rounds + 1 + (args.steps if args.proposal != "none" else 0)
     if args.check_every > 0:  # up to one harvest per sample and epoch
@@ -433,7 +481,7 @@ def main():
         for k in range(e2e_steps):
             sols = P.sample(circ, cnf, n_wanted=10 ** 12, batch=B, steps=steps, max_rounds=1, lr=w["lr"], seed=0,
                             first_round=round_base + (n_rounds + k) * 4096, init_scale=w["init_scale"], act_dtype=ad,
-                            check_every=max(0, args.check_every), max_age=args.max_age)
+                            check_every=max(0, args.check_every), max_age=args.max_age, optimizer=args.optimizer)
             ucount += len(sols)
             d2h += len(sols) * info["key_words"] * 4 + B // 8 + 16
         e2e_s = time.perf_counter() - t1
@@ -453,7 +501,8 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": ad,
             "data": "synthetic (seeded Tseitin random circuit)" if w["kind"] == "tseitin" else "synthetic (planted 3-SAT)",
             "config": {"workload": args.workload, **{k: v for k, v in w.items() if k != "kind"},
-                       "optimizer": "adam", "l2_flush": "working set > L2 (activations %.1f GB)" %
+                       "optimizer": args.optimizer, "relaxation": "direct CNF" if args.direct else "Algorithm 1",
+                       "l2_flush": "working set > L2 (activations %.1f GB)" %
                        (info["n_cone"] * B * ACT_BYTES[ad] / 1e9),
                        "parallelism": f"replicas x{world} (disjoint Philox streams)"},
             "gate_evals_per_s": gate_evals / (t_max / 1e3),

@@ -95,6 +95,9 @@ void sat_cnf_free(sat_cnf* cnf);
 typedef struct sat_build_opts {
     uint32_t max_support;
     uint32_t max_window;
+    uint32_t direct;   /* nonzero: no factorization, every (cleaned) clause is an OR output
+                          constrained to 1 and every variable a primary input (the CNF side of
+                          the paper's Fig. 5 comparison, for the direct-relaxation ablation) */
 } sat_build_opts;
 
 typedef struct sat_build_stats {

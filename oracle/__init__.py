@@ -73,7 +73,7 @@ def ptr(a: np.ndarray):
 
 
 from .dimacs import parse_dimacs, cnf_satisfied, DimacsError  # noqa: E402,F401
-from .transform import factorize, Circuit, Definition  # noqa: E402,F401
+from .transform import factorize, direct_circuit, Circuit, Definition  # noqa: E402,F401
 from .sampler import (  # noqa: E402,F401
     FlatCircuit, flatten, forward, backward, adam_step, gd_step, hard_eval,
     full_assignment, cnf_check, solution_hash, philox4x32_10, init_normal,

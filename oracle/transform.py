@@ -216,6 +216,14 @@ def _clean(clauses):
     return out
 
 
+def direct_circuit(n_vars: int, clauses) -> Circuit:
+    """No factorization: every clause is an OR output constrained to 1 and every
+    variable a primary input -- the CNF itself relaxed clause by clause (the
+    'CNF' side of the operation counts of Fig. 5), used for the ablation against
+    Algorithm 1."""
+    return Circuit(n_vars, list(range(1, n_vars + 1)), [], _clean(clauses), 0)
+
+
 def factorize(n_vars: int, clauses, max_support: int = 8, max_window: int = 16) -> Circuit:
     """Algorithm 1 with the readings listed in the module docstring."""
     clauses = _clean(clauses)

@@ -187,6 +187,7 @@ sat_status sat_circuit_build(const sat_cnf* cnf, const sat_build_opts* opts, sat
     if (opts) {
         to.max_support = opts->max_support;
         to.max_window = opts->max_window;
+        to.direct = opts->direct != 0;
     }
     try {
         auto* c = new sat_circuit();

@@ -59,6 +59,7 @@ struct Circuit {
 struct TransformOpts {
     uint32_t max_support = 8;
     uint32_t max_window = 16;
+    bool direct = false;  // no factorization: clauses as OR outputs, all variables inputs
 };
 
 // Algorithm 1 with the fallback for under-specified clauses.

@@ -251,6 +251,12 @@ bool transform(const Cnf& cnf, const TransformOpts& o, Circuit& out, std::string
         if (cl.empty()) { err = "empty clause: the CNF is unsatisfiable"; return false; }
         cls.push_back(std::move(cl));
     }
+    if (o.direct) {
+        out.outputs = std::move(cls);
+        for (uint32_t v = 1; v <= cnf.n_vars; v++) out.pis.push_back(v);
+        out.wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        return true;
+    }
     std::vector<int64_t> last(cnf.n_vars + 1, -1);
     for (size_t i = 0; i < cls.size(); i++)
         for (int32_t l : cls[i]) last[std::abs(l)] = (int64_t)i;

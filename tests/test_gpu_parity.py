@@ -73,6 +73,33 @@ def test_forward_backward_parity(gpu, name, B):
     assert ok.all(), (np.argwhere(~ok)[:5], g[~ok][:5], gref[~ok][:5])
 
 
+@pytest.mark.parametrize("name", ["planted3sat_50_200", "tseitin_small"])
+def test_direct_relaxation_parity(gpu, name):
+    """The direct relaxation (no factorization, one OR output per clause) on the same
+    kernels: forward values, loss and gradients against the oracle's direct circuit."""
+    import paper_2502_08673_b300 as P
+    text = INSTANCES[name]()
+    cnf = P.Cnf.from_dimacs(text)
+    plan = P.Plan.create(P.Circuit.build(cnf, direct=True), cnf)
+    orc = oracle.Oracle(text, direct=True)
+    assert list(plan.pi_vars()) == orc.circuit.pis
+    B = 45
+    V0 = normal_logits(B, orc.n_pi, seed=3)
+    V = torch.tensor(V0.T.copy(), device=gpu)
+    act, adj = P.new_act(plan, B), P.new_adj(plan, B)
+    loss = torch.empty(B, device=gpu)
+    gV = torch.zeros_like(V)
+    P.sat_forward(plan, V, act, loss)
+    P.sat_backward(plan, V, act, adj, gV)
+    torch.cuda.synchronize()
+    vals, loss_ref = oracle.forward(orc.flat, V0.astype(np.float64))
+    gref, _ = oracle.backward(orc.flat, vals)
+    np.testing.assert_allclose(loss.cpu().numpy(), loss_ref, rtol=0, atol=1e-5 * max(1, plan.n_outputs))
+    g = gV.cpu().numpy().T
+    ok = _grad_close(g.astype(np.float64), gref)
+    assert ok.all(), (np.argwhere(~ok)[:5], g[~ok][:5], gref[~ok][:5])
+
+
 def test_fused_steps_equal_unfused(gpu):
     """sat_steps = forward, backward, opt_update, bit for bit (Adam and GD)."""
     P, cnf, circ, plan, orc = _setup(INSTANCES["tseitin_small"]())

@@ -33,6 +33,18 @@ def _oracle_dump(text):
     return oracle_dump(fz.factorize(n, cl))
 
 
+def test_direct_build_matches_oracle():
+    """direct=True: the cleaned clauses as outputs, all variables as inputs."""
+    n0, cl0 = parse_dimacs(planted_3sat(30, 120, 5).dimacs())
+    with_extras = dimacs_text(n0, cl0 + [[2, -2, 7], [3, 3, -4]])  # a tautology and a repeated literal
+    for text in (with_extras, tseitin_random_circuit(20, 60, 6, 3, seed=1).dimacs()):
+        circ = P.Circuit.build(P.Cnf.from_dimacs(text), direct=True)
+        n, cl = parse_dimacs(text)
+        assert circ.dump() == oracle_dump(fz.direct_circuit(n, cl))
+        st = circ.stats
+        assert st["n_pi"] == n and st["n_iv"] == 0 and st["n_outputs"] == len(fz.direct_circuit(n, cl).outputs)
+
+
 CASES = {
     "fig1": fig1_example_dimacs,
     "tseitin_small": lambda: tseitin_random_circuit(20, 60, 6, 3, seed=1).dimacs(),

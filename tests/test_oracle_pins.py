@@ -155,6 +155,25 @@ def test_small_planted3sat_bruteforce(seed):
     assert tuple(int(x) for x in inst.hidden) in sols
 
 
+@pytest.mark.parametrize("seed", range(3))
+def test_direct_circuit_bruteforce(seed):
+    """Direct relaxation (no factorization): every variable an input, every clause an
+    OR output; its solutions are the CNF's, and its flattened gates, evaluated on
+    every assignment, are all 1 exactly where the CNF holds."""
+    n, cl = parse_dimacs(planted_3sat(12, 45, seed).dimacs())
+    cl = cl + [[1, -1, 3]]  # plus a tautology, which is dropped
+    c = fz.direct_circuit(n, cl)
+    assert c.pis == list(range(1, n + 1)) and c.defs == [] and len(c.outputs) == 45
+    assert _count_circuit(c) == _count_cnf(n, cl)
+    fc = oracle.flatten(c)
+    allb = np.array(list(itertools.product([0, 1], repeat=n)), dtype=np.uint8)
+    bits = oracle.hard_eval(fc, allb)
+    outs_ok = (bits[:, fc.out_node] == fc.target[None, :]).all(axis=1)
+    assign = np.zeros((len(allb), n + 1), np.uint8)
+    assign[:, 1:] = allb
+    assert (outs_ok == oracle.cnf_check(n, cl, assign).astype(bool)).all()
+
+
 def test_tseitin_ground_truth_gates():
     """Every generated gate is recovered with the generator's Boolean function."""
     inst = tseitin_random_circuit(n_pi=40, n_gates=120, depth=6, n_out=4, seed=3)
