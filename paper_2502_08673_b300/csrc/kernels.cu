@@ -62,11 +62,35 @@ template <> struct ActIO<float> {
         }
         return r;
     }
+    // L2-only load (bypasses L1): for rows another SM may have written
+    static __device__ __forceinline__ VF ldcg(const float* p) {
+        VF r;
+        if constexpr (VEC == 4) {
+            const float4 q = __ldcg(reinterpret_cast<const float4*>(p));
+            r.v[0] = q.x; r.v[1] = q.y; r.v[2] = q.z; r.v[3] = q.w;
+        } else {
+            const float2 q = __ldcg(reinterpret_cast<const float2*>(p));
+            r.v[0] = q.x; r.v[1] = q.y;
+        }
+        return r;
+    }
     static __device__ __forceinline__ void st(float* p, const VF& x) {
         if constexpr (VEC == 4) *reinterpret_cast<float4*>(p) = make_float4(x.v[0], x.v[1], x.v[2], x.v[3]);
         else *reinterpret_cast<float2*>(p) = make_float2(x.v[0], x.v[1]);
     }
 };
+// Two 16-bit values per 32-bit word; ldcg reads the lane's VEC values through L2 only.
+template <typename H, typename H2>
+__device__ __forceinline__ VF ld16_cg(const H* p, float2 (*cvt)(H2)) {
+    VF r;
+#pragma unroll
+    for (int q = 0; q < VEC; q += 2) {
+        const unsigned u = __ldcg(reinterpret_cast<const unsigned*>(p) + q / 2);
+        const float2 f = cvt(*reinterpret_cast<const H2*>(&u));
+        r.v[q] = f.x; r.v[q + 1] = f.y;
+    }
+    return r;
+}
 template <> struct ActIO<__nv_bfloat16> {
     static __device__ __forceinline__ VF ld(const __nv_bfloat16* p) {
         VF r;
@@ -76,6 +100,9 @@ template <> struct ActIO<__nv_bfloat16> {
             r.v[q] = f.x; r.v[q + 1] = f.y;
         }
         return r;
+    }
+    static __device__ __forceinline__ VF ldcg(const __nv_bfloat16* p) {
+        return ld16_cg<__nv_bfloat16, __nv_bfloat162>(p, __bfloat1622float2);
     }
     static __device__ __forceinline__ void st(__nv_bfloat16* p, const VF& x) {
 #pragma unroll
@@ -93,6 +120,7 @@ template <> struct ActIO<__half> {
         }
         return r;
     }
+    static __device__ __forceinline__ VF ldcg(const __half* p) { return ld16_cg<__half, __half2>(p, __half22float2); }
     static __device__ __forceinline__ void st(__half* p, const VF& x) {
 #pragma unroll
         for (int q = 0; q < VEC; q += 2)
@@ -122,18 +150,30 @@ __device__ __forceinline__ float gate_apply(const float4& k, float a, float b) {
     return fmaf(fmaf(k.w, a, k.z), b, fmaf(k.y, a, k.x));
 }
 
+// A tile is processed by one CTA, or (split mode) by the two CTAs of a
+// thread-block cluster, which divide every level's rows between their warps
+// and meet at cluster barriers.  vw / nvw number the warps across the cluster.
 struct TileCtx {
     int lane, warp, nw;
+    int vw, nvw;    // work distribution: this warp among all warps serving the tile
+    int rank;       // CTA within the cluster (0 outside split mode)
+    int tile;       // tile index (samples tile*TILE .. tile*TILE+TILE-1)
+    bool split;
     int64_t b;      // first of this lane's VEC samples
     int nvalid;     // how many of them are < B
 };
 
-__device__ __forceinline__ TileCtx tile_ctx(int64_t B) {
+__device__ __forceinline__ TileCtx tile_ctx(int64_t B, int tile0 = 0, bool split = false) {
     TileCtx c;
     c.lane = threadIdx.x & 31;
     c.warp = threadIdx.x >> 5;
     c.nw = blockDim.x >> 5;
-    c.b = (int64_t)blockIdx.x * TILE + c.lane * VEC;
+    c.split = split;
+    c.rank = split ? (int)(blockIdx.x & 1u) : 0;
+    c.tile = tile0 + (int)(split ? blockIdx.x >> 1 : blockIdx.x);
+    c.vw = c.rank * c.nw + c.warp;
+    c.nvw = (split ? 2 : 1) * c.nw;
+    c.b = (int64_t)c.tile * TILE + c.lane * VEC;
     const int64_t rem = B - c.b;
     c.nvalid = rem <= 0 ? 0 : (rem >= VEC ? VEC : (int)rem);
     return c;
@@ -142,6 +182,15 @@ __device__ __forceinline__ TileCtx tile_ctx(int64_t B) {
 // Element offset of this lane's samples in row `row` of a tile's [n_cone][TILE] block.
 __device__ __forceinline__ uint32_t at(int row, const TileCtx& c) {
     return (uint32_t)row * TILE + (uint32_t)(c.lane * VEC);
+}
+
+// Barrier between levels: the CTA, or both CTAs of a split tile (release /
+// acquire at cluster scope, so rows written by either CTA are visible after it).
+__device__ __forceinline__ void level_sync(const TileCtx& c) {
+    if (c.split)
+        asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    else
+        __syncthreads();
 }
 
 // Adam bias corrections at step t >= 1 (PyTorch: step_size = lr / (1 - b1^t),
@@ -311,7 +360,7 @@ __device__ void tile_forward(const DevPlan& p, const float* __restrict__ V, int6
                              const float4* gcoef, const RowMaps& rm, const TileCtx& c) {
     constexpr int ROWB = TILE * (int)sizeof(T);
     constexpr int SLOT = slot_bytes<T>();
-    for (int i0 = c.warp * UBATCH; i0 < p.n_cone_pi; i0 += c.nw * UBATCH) {
+    for (int i0 = c.vw * UBATCH; i0 < p.n_cone_pi; i0 += c.nvw * UBATCH) {
         VF x[UBATCH];
 #pragma unroll
         for (int u = 0; u < UBATCH; u++) {
@@ -336,14 +385,14 @@ __device__ void tile_forward(const DevPlan& p, const float* __restrict__ V, int6
         }
     }
     fence_async_global();
-    __syncthreads();
+    level_sync(c);
     // This warp's gate run of level l and its first 32 gate records; those of the
     // next level are loaded before the level barrier, so that their latency
     // overlaps the wait for the other warps.
     auto level_run = [&](int l, int& g0, int& g1, int2& first) {
         const int lo = __ldg(&p.c_level_off[l]), hi = __ldg(&p.c_level_off[l + 1]);
-        const int per = (hi - lo + c.nw - 1) / c.nw;
-        g0 = lo + c.warp * per;
+        const int per = (hi - lo + c.nvw - 1) / c.nvw;
+        g0 = lo + c.vw * per;
         g1 = min(g0 + per, hi);
         first = make_int2(0, 0);
         if (c.lane < g1 - g0) first = __ldg(&p.c_gate[g0 + c.lane - p.n_cone_pi]);
@@ -403,7 +452,7 @@ __device__ void tile_forward(const DevPlan& p, const float* __restrict__ V, int6
         }
         if (l < p.n_clev) level_run(l + 1, g0, g1, first);
         fence_async_global();
-        __syncthreads();
+        level_sync(c);
     }
 }
 
@@ -413,7 +462,7 @@ __device__ void tile_loss(const DevPlan& p, const T* act, float* loss, const Til
     __shared__ VF part[STEP_THREADS / 32][32];
     VF acc = vf_fill(0.0f);
     for (int j = c.warp; j < p.n_out; j += c.nw) {
-        const VF y = ActIO<T>::ld(act + at(p.c_out_node[j], c));
+        const VF y = ActIO<T>::ldcg(act + at(p.c_out_node[j], c));
         const float t = p.out_target[j];
 #pragma unroll
         for (int q = 0; q < VEC; q++) acc.v[q] = fmaf(y.v[q] - t, y.v[q] - t, acc.v[q]);
@@ -448,9 +497,9 @@ struct AdjRun {
 __device__ __forceinline__ AdjRun adj_run(const DevPlan& p, int l, const TileCtx& c) {
     const int lo = l == 0 ? 0 : __ldg(&p.c_level_off[l]);
     const int hi = l == 0 ? p.n_cone_pi : __ldg(&p.c_level_off[l + 1]);
-    const int per = (hi - lo + c.nw - 1) / c.nw;
+    const int per = (hi - lo + c.nvw - 1) / c.nvw;
     AdjRun r;
-    r.u0 = lo + c.warp * per;
+    r.u0 = lo + c.vw * per;
     r.u1 = min(r.u0 + per, hi);
     r.off = 0;
     r.first = make_int4(-1, 0, 0, 0);
@@ -567,13 +616,15 @@ __device__ __forceinline__ void input_update(const OptParams& o, float* V, float
 
 // Discard, from L2, this tile's adjoint rows of cone level l (level 0 = the
 // inputs); the whole CTA shares the 128-byte lines.
-__device__ __forceinline__ void discard_adj_rows(const DevPlan& p, int l, const float* adj) {
+__device__ __forceinline__ void discard_adj_rows(const DevPlan& p, int l, const float* adj, const TileCtx& c) {
     const int lo = l == 0 ? 0 : __ldg(&p.c_level_off[l]);
     const int hi = l == 0 ? p.n_cone_pi : __ldg(&p.c_level_off[l + 1]);
     const char* b = reinterpret_cast<const char*>(adj);
     constexpr int LINES_PER_ROW = TILE * 4 / 128;
     const int n = (hi - lo) * LINES_PER_ROW;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) discard_l2_line(b + (size_t)lo * TILE * 4 + (size_t)i * 128);
+    const int stride = (c.split ? 2 : 1) * (int)blockDim.x;
+    for (int i = c.rank * (int)blockDim.x + (int)threadIdx.x; i < n; i += stride)
+        discard_l2_line(b + (size_t)lo * TILE * 4 + (size_t)i * 128);
 }
 
 // Backward pass of one tile over levels n_clev..0.  The input level's adjoints
@@ -592,12 +643,12 @@ __device__ void tile_backward(const DevPlan& p, const OptParams& o, float* V, fl
         level_adjoint<T>(p, run, act, adj, seed_scale, st, rm, c);
         if (l > 0) run = adj_run(p, l - 1, c);
         fence_async_global();
-        __syncthreads();
+        level_sync(c);
         // Adjoint rows of level l + span have no reader below level l.
-        if (l + p.max_span <= p.n_clev) discard_adj_rows(p, l + p.max_span, adj);
+        if (l + p.max_span <= p.n_clev) discard_adj_rows(p, l + p.max_span, adj, c);
     }
     const bool adam = UPDATE && o.opt == 0;
-    for (int i0 = c.warp * UBATCH; i0 < p.n_cone_pi; i0 += c.nw * UBATCH) {
+    for (int i0 = c.vw * UBATCH; i0 < p.n_cone_pi; i0 += c.nvw * UBATCH) {
         VF vv[UBATCH], pb[UBATCH], mm[UBATCH], ss[UBATCH];
         int64_t r[UBATCH];
 #pragma unroll
@@ -607,7 +658,7 @@ __device__ void tile_backward(const DevPlan& p, const OptParams& o, float* V, fl
             vv[u] = mm[u] = ss[u] = pb[u] = vf_fill(0.0f);
             if (i < p.n_cone_pi) {
                 r[u] = (int64_t)__ldg(&p.cone_pi_row[i]) * ldv + c.b;
-                pb[u] = ActIO<float>::ld(adj + at(i, c));
+                pb[u] = ActIO<float>::ldcg(adj + at(i, c));  // possibly written by the other CTA
 #pragma unroll
                 for (int q = 0; q < VEC; q++) {
                     if (q < c.nvalid) {
@@ -630,8 +681,8 @@ __device__ void tile_backward(const DevPlan& p, const OptParams& o, float* V, fl
                                          ac.step[q], ac.bc2s[q]);
         }
     }
-    __syncthreads();
-    for (int l = 0; l < p.max_span && l <= p.n_clev; l++) discard_adj_rows(p, l, adj);
+    level_sync(c);
+    for (int l = 0; l < p.max_span && l <= p.n_clev; l++) discard_adj_rows(p, l, adj, c);
 }
 
 // Scratch of tile t: act / adj rows [n_cone][TILE] starting at element t * n_cone * TILE.
@@ -655,8 +706,8 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) forward_kernel(DevPlan p, con
     __shared__ float4 gcoef[16];
     const TileCtx c = tile_ctx(B);
     Stage st = init_stage<T>(smem, p, gcoef, c);
-    T* a = act + (size_t)blockIdx.x * (size_t)p.n_cone * TILE;
-    const RowMaps rm{&amap, &amap, (int)(blockIdx.x * (int64_t)p.n_cone)};
+    T* a = act + (size_t)c.tile * (size_t)p.n_cone * TILE;
+    const RowMaps rm{&amap, &amap, (int)(c.tile * (int64_t)p.n_cone)};
     tile_forward<T>(p, V, ldv, a, st, gcoef, rm, c);
     if (loss) tile_loss<T>(p, a, loss, c);
 }
@@ -671,38 +722,39 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) backward_kernel(DevPlan p, co
     __shared__ float4 gcoef[16];
     const TileCtx c = tile_ctx(B);
     Stage st = init_stage<T>(smem, p, gcoef, c);
-    const size_t off = (size_t)blockIdx.x * (size_t)p.n_cone * TILE;
+    const size_t off = (size_t)c.tile * (size_t)p.n_cone * TILE;
     OptParams o;
     AdamCorr ac;
 #pragma unroll
     for (int q = 0; q < VEC; q++) ac.step[q] = ac.bc2s[q] = 1.0f;
-    const RowMaps rm{&amap, &gmap, (int)(blockIdx.x * (int64_t)p.n_cone)};
+    const RowMaps rm{&amap, &gmap, (int)(c.tile * (int64_t)p.n_cone)};
     tile_backward<T, false>(p, o, const_cast<float*>(V), nullptr, nullptr, gV, ldv, act + off, adj + off, grad_loss,
                             ac, st, rm, c);
 }
 
 // The fused hot loop: n_steps x (forward, loss, adjoint, update) for one tile,
 // at Adam steps t0 + s (+ age[b] per sample when age is given).
-template <typename T>
+// SPLIT: launched in clusters of two CTAs per tile (tiles tile0, tile0 + 1, ...).
+template <typename T, bool SPLIT>
 __global__ void __launch_bounds__(STEP_THREADS, 1) steps_kernel(DevPlan p, OptParams o, float* V, float* m, float* v,
                                                                 int64_t ldv, T* act, float* adj, float* loss,
                                                                 int t0, const int32_t* age, int n_steps, int64_t B,
-                                                                const __grid_constant__ CUtensorMap amap,
+                                                                int tile0, const __grid_constant__ CUtensorMap amap,
                                                                 const __grid_constant__ CUtensorMap gmap) {
     extern __shared__ __align__(128) char smem[];
     __shared__ float4 gcoef[16];
-    const TileCtx c = tile_ctx(B);
+    const TileCtx c = tile_ctx(B, tile0, SPLIT);
     Stage st = init_stage<T>(smem, p, gcoef, c);
-    const size_t off = (size_t)blockIdx.x * (size_t)p.n_cone * TILE;
+    const size_t off = (size_t)c.tile * (size_t)p.n_cone * TILE;
     T* a = act + off;
     float* g = adj + off;
-    const RowMaps rm{&amap, &gmap, (int)(blockIdx.x * (int64_t)p.n_cone)};
+    const RowMaps rm{&amap, &gmap, (int)(c.tile * (int64_t)p.n_cone)};
 #pragma unroll 1
     for (int s = 0; s < n_steps; s++) {
         AdamCorr ac;
         if (o.opt == 0) ac = adam_corr(o, age, t0 + s, c);
         tile_forward<T>(p, V, ldv, a, st, gcoef, rm, c);
-        if (loss && s == n_steps - 1) tile_loss<T>(p, a, loss, c);
+        if (loss && s == n_steps - 1 && c.rank == 0) tile_loss<T>(p, a, loss, c);
         tile_backward<T, true>(p, o, V, m, v, nullptr, ldv, a, g, nullptr, ac, st, rm, c);
     }
 }
@@ -721,7 +773,9 @@ cudaError_t prepare_tile_kernels() {
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(backward_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(steps_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+            e = cudaFuncSetAttribute(steps_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(steps_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         return e;
     }();
     return done;
@@ -1043,11 +1097,40 @@ cudaError_t steps_launch(const DevPlan& p, const OptParams& o, float* V, float* 
                          cudaStream_t s) {
     cudaError_t e = prepare_tile_kernels<T>();
     if (e != cudaSuccess) return e;
-    const unsigned grid = (unsigned)((B + TILE - 1) / TILE);
+    const int tiles = (int)((B + TILE - 1) / TILE);
     CUtensorMap amap, gmap;
-    if ((e = row_maps<T>(p, act, adj, grid, &amap, &gmap)) != cudaSuccess) return e;
-    steps_kernel<T><<<grid, STEP_THREADS, stage_smem<T>(), s>>>(p, o, V, m, v, ldv, (T*)act, adj, loss, t0, age,
-                                                                n_steps, B, amap, gmap);
+    if ((e = row_maps<T>(p, act, adj, (unsigned)tiles, &amap, &gmap)) != cudaSuccess) return e;
+    // Whole waves of tiles run one CTA per tile; a last, partial wave of at most half
+    // the SMs runs in split mode (two CTAs of a cluster per tile) so that it fills them.
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                   cudaSuccess)
+        return cudaErrorInvalidDevice;
+    int main_tiles = tiles - tiles % sms;
+    if (2 * (tiles - main_tiles) > sms) main_tiles = tiles;
+    const int tail = tiles - main_tiles;
+    if (main_tiles > 0) {
+        steps_kernel<T, false><<<(unsigned)main_tiles, STEP_THREADS, stage_smem<T>(), s>>>(
+            p, o, V, m, v, ldv, (T*)act, adj, loss, t0, age, n_steps, B, 0, amap, gmap);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (tail > 0) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(2 * tail), 1, 1);
+        cfg.blockDim = dim3(STEP_THREADS, 1, 1);
+        cfg.dynamicSmemBytes = stage_smem<T>();
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, steps_kernel<T, true>, p, o, V, m, v, ldv, (T*)act, adj, loss, t0, age, n_steps,
+                               B, main_tiles, amap, gmap);
+        if (e != cudaSuccess) return e;
+    }
     return cudaGetLastError();
 }
 
