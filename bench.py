@@ -175,6 +175,17 @@ def profile_traffic(workload, act_dtype):
     return float(m.group(1)), f.name
 
 
+def step_kernel_launches(B, torch):
+    """Launches of the fused step kernel per call: whole waves of one-CTA tiles, plus a
+    partial last wave of at most half the SMs as 2-CTA clusters (the library's policy)."""
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    tiles = -(-B // 128)
+    main = tiles - tiles % sms
+    if 2 * (tiles - main) > sms:
+        main = tiles
+    return int(main > 0) + int(tiles > main)
+
+
 def kernel_source_hash():
     return hashlib.sha256((ROOT / "paper_2502_08673_b300" / "csrc" / "kernels.cu").read_bytes()).hexdigest()[:16]
 
@@ -514,7 +525,8 @@ def main():
                          "algorithmic_bytes_per_launch": alg,
                          "traffic": (dram_per_sample_step * B * steps) if dram_per_sample_step else None,
                          "traffic_source": prof},
-            "gpu_launches": (8 * args.steps if args.check_every <= 0 else 9 * len(ee_events)),
+            "gpu_launches": ((7 + step_kernel_launches(B, torch)) * args.steps if args.check_every <= 0
+                             else (8 + step_kernel_launches(B, torch)) * len(ee_events)),
             "transform_s": transform_s,
             "plan": {k: info[k] for k in ("n_pi", "n_cone_pi", "n_cone_gates", "n_gates", "n_clauses",
                                           "n_cone_levels", "max_span")},
