@@ -208,8 +208,9 @@ def oracle_sample(text, w, n_samples, n_steps):
 
 def cpu_baseline_entry(text, w, budget_s=15.0):
     # scale the sample so the oracle runs for roughly budget_s seconds
-    probe = oracle_sample(text, w, 16, 40)
-    per_sample_step = probe["seconds"] / (16 * 40)
+    # calibrate on as many samples as host threads work on in parallel, so the estimate holds for the run
+    probe = oracle_sample(text, w, 64, 20)
+    per_sample_step = probe["seconds"] / (64 * 20)
     steps = w["steps"]
     n = int(max(4, min(1024, budget_s / max(per_sample_step * steps, 1e-9))))
     r = oracle_sample(text, w, n, steps)
@@ -379,7 +380,7 @@ def main():
     if args.curve:
         return run_curve(P, torch, plan, ws, opt, args, w, info)
     n_rounds = args.warmup + args.steps
-    harvest_rounds = n_rounds + 1 + (args.steps if args.proposal != "none" else 0)
+    harvest_rounds = n_rounds + 1 + (2 * args.steps if args.proposal != "none" else 0)
     if args.check_every > 0:  # up to one harvest per sample and epoch
         harvest_rounds *= -(-steps // args.check_every)
     dedup = P.Dedup.create(plan, max_keys=B * harvest_rounds, max_batch=B)
@@ -394,7 +395,7 @@ def main():
     ee_events = []
     max_age = args.max_age or steps
 
-    def one_round(k, ev=None, use_mlp=True):
+    def one_round(k, ev=None, use_mlp=True, n_steps=None):
         if args.check_every > 0:
             # early exit: one bench step = `steps` descent steps of the batch in epochs; the batch
             # carries over between bench steps (a continuous sampler); kernel events per launch
@@ -410,8 +411,8 @@ def main():
         ws.v.zero_()
         if ev is not None:
             ev[0].record(stream)
-        P.sat_steps(plan, opt, ws.V, ws.m, ws.v, ws.act, ws.adj, 1, prop_steps if (mlp is not None and use_mlp) else steps,
-                    act_dtype=ad)
+        P.sat_steps(plan, opt, ws.V, ws.m, ws.v, ws.act, ws.adj, 1,
+                    n_steps or (prop_steps if (mlp is not None and use_mlp) else steps), act_dtype=ad)
         if ev is not None:
             ev[1].record(stream)
         P.sat_threshold(plan, ws.V, ws.bits, ws.keys)
@@ -466,20 +467,25 @@ def main():
 
     plain_cmp = None
     if mlp is not None:
-        # the plain form on the same instance, same batch and steps, fresh streams
-        before_p = dedup.count()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        vp = 0
-        e0.record(stream)
-        for k in range(args.steps):
-            one_round(n_rounds + 64 + k, use_mlp=False)
-            if args.check_every <= 0:
-                vp += int(P.valid_mask(ws.valid, B).sum())
-        e1.record(stream)
-        torch.cuda.synchronize()
-        tp = e0.elapsed_time(e1)
-        plain_cmp = {"value": (dedup.count() - before_p) / (tp / 1e3), "valid_fraction": vp / (B * args.steps),
-                     "ms_per_step": tp / args.steps}
+        # the plain form on the same instance and batch, fresh streams: at the proposal's step
+        # count (same budget) and, if different, at the workload's own step count
+        plain_cmp = {}
+        for label, ns in (("same_steps", prop_steps), ("workload_steps", steps)):
+            if label == "workload_steps" and ns == prop_steps:
+                continue
+            before_p = dedup.count()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            vp = 0
+            e0.record(stream)
+            for k in range(args.steps):
+                one_round(n_rounds + 64 + (0 if label == "same_steps" else 32) + k, use_mlp=False, n_steps=ns)
+                if args.check_every <= 0:
+                    vp += int(P.valid_mask(ws.valid, B).sum())
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tp = e0.elapsed_time(e1)
+            plain_cmp[label] = {"steps": ns, "value": (dedup.count() - before_p) / (tp / 1e3),
+                                "valid_fraction": vp / (B * args.steps), "ms_per_step": tp / args.steps}
     del ws, dedup
     torch.cuda.empty_cache()
     e2e = None
