@@ -186,6 +186,30 @@ def step_kernel_launches(B, torch):
     return int(main > 0) + int(tiles > main)
 
 
+ROUNDS_PER_RANK = 1 << 20
+
+
+def round_base_of(rank):
+    """First Philox round counter of a rank: ranks draw from disjoint ranges of 2^20
+    rounds (a run uses 4,096 per bench step under early exit, so < 256 steps)."""
+    return rank * ROUNDS_PER_RANK
+
+
+def merge_ranks(elapsed_ms, uniq, valid, device="cuda"):
+    """Whole-job figures over the ranks: the slowest rank's time and the summed unique and
+    valid counts (the ranks' streams are disjoint, so are their solutions, up to chance
+    repeats of 2,000-bit keys).  Without a process group: the rank's own figures."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return elapsed_ms, uniq, valid
+    tt = torch.tensor([elapsed_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    cnt = torch.tensor([uniq, valid], dtype=torch.float64, device=device)
+    dist.all_reduce(cnt)
+    return float(tt.item()), int(cnt[0].item()), int(cnt[1].item())
+
+
 def kernel_source_hash():
     return hashlib.sha256((ROOT / "paper_2502_08673_b300" / "csrc" / "kernels.cu").read_bytes()).hexdigest()[:16]
 
@@ -385,7 +409,7 @@ def main():
         harvest_rounds *= -(-steps // args.check_every)
     dedup = P.Dedup.create(plan, max_keys=B * harvest_rounds, max_batch=B)
     stream = torch.cuda.current_stream()
-    round_base = rank << 20
+    round_base = round_base_of(rank)
 
     prop_log = {}
     mlp = (train_proposal(P, torch, plan, w, args.proposal, B, opt, ad, prop_log, args.proposal_train_steps,
@@ -449,13 +473,7 @@ def main():
     else:
         kernel_ms = [a.elapsed_time(b) for a, b in kev]
         launch_steps = None
-    t_max, uniq_all, valid_all = elapsed_ms, uniq, valid_total
-    if world > 1:
-        tt = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        cnt = torch.tensor([uniq, valid_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(cnt)
-        t_max, uniq_all, valid_all = float(tt.item()), int(cnt[0].item()), int(cnt[1].item())
+    t_max, uniq_all, valid_all = merge_ranks(elapsed_ms, uniq, valid_total, device="cuda")
     value = uniq_all / (t_max / 1e3)
     run_steps = prop_steps if (mlp is not None and args.check_every <= 0) else steps
     gate_evals = info["n_cone_gates"] * B * run_steps * args.steps * world
