@@ -52,9 +52,18 @@ ACT_BYTES = {"f32": 4, "bf16": 2, "f16": 2}
 def instance_text(w, planted_seed=None):
     from workloads import tseitin_random_circuit, planted_3sat
     if w["kind"] == "tseitin":
-        return tseitin_random_circuit(w["n_pi"], w["n_gates"], w["depth"], w["n_out"], seed=w["seed"],
+        text = tseitin_random_circuit(w["n_pi"], w["n_gates"], w["depth"], w["n_out"], seed=w["seed"],
                                       planted_seed=planted_seed).dimacs()
-    return planted_3sat(w["n_vars"], w["n_clauses"], w["seed"]).dimacs()
+    else:
+        text = planted_3sat(w["n_vars"], w["n_clauses"], w["seed"]).dimacs()
+    if w.get("shuffle_clauses"):
+        # the same CNF with its clauses in a seeded random order (out-of-order files)
+        import random
+        from oracle.dimacs import parse_dimacs
+        from workloads import dimacs_text
+        n, cl = parse_dimacs(text)
+        text = dimacs_text(n, random.Random(w["seed"]).sample(cl, len(cl)))
+    return text
 
 
 def train_proposal(P, torch, plan, w, mode, B, opt, ad, log, train_steps=0, rounds=0):
@@ -218,7 +227,7 @@ def kernel_source_hash():
 def oracle_sample(text, w, n_samples, n_steps):
     """Time the CPU oracle on a bounded sample: n_samples x n_steps + verification."""
     import oracle
-    orc = oracle.Oracle(text, direct=w.get("direct", False))
+    orc = oracle.Oracle(text, direct=w.get("direct", False), reorder=w.get("reorder", False))
     V0 = oracle.init_normal(n_samples, orc.n_pi, seed=0, rnd=0, scale=w["init_scale"])
     t0 = time.perf_counter()
     res = oracle.sample_round(orc.flat, orc.n_vars, orc.clauses, V0, steps=n_steps, lr=w["lr"],
@@ -359,6 +368,9 @@ def main():
     ap.add_argument("--max-age", type=int, default=0, help="early exit: restart samples unsolved after this many steps")
     ap.add_argument("--direct", action="store_true",
                     help="relax the CNF directly (one OR output per clause, no factorization): the ablation")
+    ap.add_argument("--shuffle-clauses", action="store_true", help="the workload's CNF with its clauses shuffled")
+    ap.add_argument("--reorder", action="store_true",
+                    help="sort clauses by (largest variable, length, position) before Algorithm 1")
     ap.add_argument("--optimizer", default="adam", choices=["adam", "gd"])
     ap.add_argument("--lr", type=float, default=0.0, help="override the workload's learning rate")
     ap.add_argument("--curve", default="",
@@ -375,6 +387,7 @@ def main():
     if args.lr:
         w["lr"] = args.lr
     w["optimizer"], w["direct"] = args.optimizer, args.direct
+    w["shuffle_clauses"], w["reorder"] = args.shuffle_clauses, args.reorder
     if args.impl == "reference":
         return run_reference(args, w)
     if args.mlp:
@@ -394,7 +407,7 @@ def main():
     text = instance_text(w, planted_seed=17 if args.proposal == "heldout" else None)
     cnf = P.Cnf.from_dimacs(text)
     t0 = time.perf_counter()
-    circ = P.Circuit.build(cnf, direct=args.direct)
+    circ = P.Circuit.build(cnf, direct=args.direct, reorder=args.reorder)
     transform_s = time.perf_counter() - t0
     plan = P.Plan.create(circ, cnf)
     info = plan.info

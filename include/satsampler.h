@@ -98,6 +98,10 @@ typedef struct sat_build_opts {
     uint32_t direct;   /* nonzero: no factorization, every (cleaned) clause is an OR output
                           constrained to 1 and every variable a primary input (the CNF side of
                           the paper's Fig. 5 comparison, for the direct-relaxation ablation) */
+    uint32_t reorder;  /* nonzero: before Algorithm 1, sort the clauses by (largest variable,
+                          longer first, position) so that the clauses defining a variable are
+                          adjacent, ahead of unit clauses on it, even when the file interleaves
+                          them; 0 = the file's order, as in the paper */
 } sat_build_opts;
 
 typedef struct sat_build_stats {

@@ -231,11 +231,12 @@ def verify(fc: FlatCircuit, n_vars, clauses, V):
 class Oracle:
     """Convenience bundle: DIMACS text -> oracle circuit -> rounds."""
 
-    def __init__(self, dimacs_text: str, direct: bool = False):
+    def __init__(self, dimacs_text: str, direct: bool = False, reorder: bool = False):
         from .dimacs import parse_dimacs
         from .transform import factorize, direct_circuit
         self.n_vars, self.clauses = parse_dimacs(dimacs_text)
-        self.circuit = (direct_circuit if direct else factorize)(self.n_vars, self.clauses)
+        self.circuit = (direct_circuit(self.n_vars, self.clauses) if direct
+                        else factorize(self.n_vars, self.clauses, reorder=reorder))
         self.flat = flatten(self.circuit)
 
     @property

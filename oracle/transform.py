@@ -224,9 +224,15 @@ def direct_circuit(n_vars: int, clauses) -> Circuit:
     return Circuit(n_vars, list(range(1, n_vars + 1)), [], _clean(clauses), 0)
 
 
-def factorize(n_vars: int, clauses, max_support: int = 8, max_window: int = 16) -> Circuit:
-    """Algorithm 1 with the readings listed in the module docstring."""
+def factorize(n_vars: int, clauses, max_support: int = 8, max_window: int = 16, reorder: bool = False) -> Circuit:
+    """Algorithm 1 with the readings listed in the module docstring.  reorder: first
+    sort the (cleaned) clauses by their largest variable, then longer clauses first,
+    then position, so that a variable's defining clauses are adjacent (and ahead of
+    unit clauses on it) in files that interleave them."""
     clauses = _clean(clauses)
+    if reorder:
+        keyed = sorted((max(abs(l) for l in c), -len(c), i) for i, c in enumerate(clauses))
+        clauses = [clauses[i] for _, _, i in keyed]
     last = {}
     for i, c in enumerate(clauses):
         for l in c:

@@ -25,7 +25,8 @@ class SatError(RuntimeError):
 
 
 class BuildOpts(C.Structure):
-    _fields_ = [("max_support", C.c_uint32), ("max_window", C.c_uint32), ("direct", C.c_uint32)]
+    _fields_ = [("max_support", C.c_uint32), ("max_window", C.c_uint32), ("direct", C.c_uint32),
+                ("reorder", C.c_uint32)]
 
 
 class BuildStats(C.Structure):

@@ -84,12 +84,15 @@ class Circuit(_Handle):
     _free = "sat_circuit_free"
 
     @classmethod
-    def build(cls, cnf: Cnf, max_support: int = 8, max_window: int = 16, direct: bool = False):
+    def build(cls, cnf: Cnf, max_support: int = 8, max_window: int = 16, direct: bool = False,
+              reorder: bool = False):
         """Algorithm 1 (default), or with direct=True one OR output per clause and no
-        factorization (the direct relaxation the paper compares against)."""
+        factorization (the direct relaxation the paper compares against).  reorder=True
+        sorts the clauses by (largest variable, position) first, for files whose gate
+        clauses are not adjacent."""
         h = C.c_void_p()
         st = N.BuildStats()
-        opts = N.BuildOpts(max_support, max_window, 1 if direct else 0)
+        opts = N.BuildOpts(max_support, max_window, 1 if direct else 0, 1 if reorder else 0)
         check(lib().sat_circuit_build(cnf.handle, C.byref(opts), C.byref(h), C.byref(st)))
         c = cls(h)
         c.stats = _struct_dict(st)

@@ -188,6 +188,7 @@ sat_status sat_circuit_build(const sat_cnf* cnf, const sat_build_opts* opts, sat
         to.max_support = opts->max_support;
         to.max_window = opts->max_window;
         to.direct = opts->direct != 0;
+        to.reorder = opts->reorder != 0;
     }
     try {
         auto* c = new sat_circuit();

@@ -59,7 +59,8 @@ struct Circuit {
 struct TransformOpts {
     uint32_t max_support = 8;
     uint32_t max_window = 16;
-    bool direct = false;  // no factorization: clauses as OR outputs, all variables inputs
+    bool direct = false;   // no factorization: clauses as OR outputs, all variables inputs
+    bool reorder = false;  // sort clauses by (largest variable, position) first
 };
 
 // Algorithm 1 with the fallback for under-specified clauses.

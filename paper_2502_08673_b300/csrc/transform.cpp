@@ -12,6 +12,9 @@
 //  * with no definition, the window is emitted as OR outputs constrained to 1
 //    when none of its variables occurs later, and is kept within max_window
 //    clauses / max_support variables by emitting its oldest clause;
+//  * optionally (reorder), clauses are first sorted by (largest variable,
+//    longer first, position), which makes each defined variable's clauses
+//    adjacent, ahead of unit clauses on it, when a file interleaves them;
 //  * accepted functions are simplified to aliases, AND/OR/XOR of literals, or
 //    a sum of products over a minimum prime cover (fewest terms, then fewest
 //    literals, then first in (literal count, care mask, value) order; with more
@@ -19,6 +22,7 @@
 #include <algorithm>
 #include <chrono>
 #include <set>
+#include <tuple>
 #include <sstream>
 #include <unordered_set>
 
@@ -250,6 +254,21 @@ bool transform(const Cnf& cnf, const TransformOpts& o, Circuit& out, std::string
         if (taut) continue;
         if (cl.empty()) { err = "empty clause: the CNF is unsatisfiable"; return false; }
         cls.push_back(std::move(cl));
+    }
+    if (o.reorder) {
+        // key: largest variable, then longer clauses first (a variable's defining clauses
+        // before unit clauses on it), then position
+        std::vector<std::tuple<uint32_t, int64_t, size_t>> key(cls.size());
+        for (size_t i = 0; i < cls.size(); i++) {
+            uint32_t mx = 0;
+            for (int32_t l : cls[i]) mx = std::max(mx, (uint32_t)std::abs(l));
+            key[i] = {mx, -(int64_t)cls[i].size(), i};
+        }
+        std::sort(key.begin(), key.end());
+        std::vector<Clause> sorted;
+        sorted.reserve(cls.size());
+        for (const auto& k : key) sorted.push_back(std::move(cls[std::get<2>(k)]));
+        cls = std::move(sorted);
     }
     if (o.direct) {
         out.outputs = std::move(cls);

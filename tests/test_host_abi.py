@@ -33,6 +33,24 @@ def _oracle_dump(text):
     return oracle_dump(fz.factorize(n, cl))
 
 
+def test_reorder_build_matches_oracle_and_recovers_shuffled_gates():
+    """reorder=True: the native build equals the oracle's on shuffled clauses, and a
+    shuffled Tseitin file yields the same circuit as the file in gate order."""
+    import random
+    n, cl = parse_dimacs(tseitin_random_circuit(40, 160, 8, 4, seed=2).dimacs())
+    base = oracle_dump(fz.factorize(n, cl))
+    for seed in range(3):
+        sh = random.Random(seed).sample(cl, len(cl))
+        text = dimacs_text(n, sh)
+        native = P.Circuit.build(P.Cnf.from_dimacs(text), reorder=True).dump()
+        assert native == oracle_dump(fz.factorize(n, sh, reorder=True))
+        assert native == base
+    n3, cl3 = parse_dimacs(planted_3sat(30, 120, 2).dimacs())
+    text3 = dimacs_text(n3, cl3[::-1])
+    assert P.Circuit.build(P.Cnf.from_dimacs(text3), reorder=True).dump() == \
+        oracle_dump(fz.factorize(n3, cl3[::-1], reorder=True))
+
+
 def test_direct_build_matches_oracle():
     """direct=True: the cleaned clauses as outputs, all variables as inputs."""
     n0, cl0 = parse_dimacs(planted_3sat(30, 120, 5).dimacs())

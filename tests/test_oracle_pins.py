@@ -156,6 +156,19 @@ def test_small_planted3sat_bruteforce(seed):
 
 
 @pytest.mark.parametrize("seed", range(3))
+def test_reorder_shuffled_tseitin_bruteforce(seed):
+    """Clauses shuffled, then reordered: the solution set is still the CNF's (enumeration in
+    both spaces) and every generated gate is recovered as an intermediate variable."""
+    import random
+    inst = tseitin_random_circuit(n_pi=6, n_gates=12, depth=4, n_out=2, seed=seed)
+    n, cl = parse_dimacs(inst.dimacs())
+    sh = random.Random(seed + 10).sample(cl, len(cl))
+    c = fz.factorize(n, sh, reorder=True)
+    assert c.pis == list(range(1, 7)) and sorted(d.var for d in c.defs) == list(range(7, 19))
+    assert _count_circuit(c) == _count_cnf(n, sh)
+
+
+@pytest.mark.parametrize("seed", range(3))
 def test_direct_circuit_bruteforce(seed):
     """Direct relaxation (no factorization): every variable an input, every clause an
     OR output; its solutions are the CNF's, and its flattened gates, evaluated on
