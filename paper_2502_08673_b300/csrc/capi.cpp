@@ -285,6 +285,9 @@ sat_status sat_plan_create(const sat_circuit* c, const sat_cnf* cnf, sat_plan** 
         std::memcpy(&i1, &c1, 4);
         fe[e] = make_int4(P.fo_g[e], P.fo_sib[e], i0, i1);
     }
+    // bit 31 of the sibling field marks the last edge of each node's range
+    for (size_t n = 0; n + 1 < P.fo_off.size(); n++)
+        if (P.fo_off[n + 1] > P.fo_off[n]) fe[(size_t)P.fo_off[n + 1] - 1].y |= (int32_t)0x80000000u;
     std::vector<int32_t> cl_lit(P.cl_node.size());
     for (size_t i = 0; i < cl_lit.size(); i++) cl_lit[i] = (P.cl_node[i] << 1) | P.cl_neg[i];
     if ((st = upload(p, P.c_level_off, &d.c_level_off)) != SAT_OK) return bail(st);

@@ -18,7 +18,7 @@ struct DevPlan {
     const int2* c_gate = nullptr;       // per cone gate: (in0 | gop << 28, in1)
     const int32_t* cone_pi_row = nullptr;
     const int32_t* fo_off = nullptr;    // [n_cone + 1]
-    const int4* fo_edge = nullptr;      // (consumer or -1, sibling, float bits of c0, float bits of c1)
+    const int4* fo_edge = nullptr;      // (consumer or -1, sibling | last-edge-of-node << 31, c0 bits, c1 bits)
     int32_t n_out = 0;
     const int32_t* c_out_node = nullptr;
     const float* out_target = nullptr;

@@ -409,16 +409,20 @@ __device__ void tile_forward(const DevPlan& p, const float* __restrict__ V, int6
                 if (c.lane < cnt) mine = __ldg(&p.c_gate[base + c.lane - p.n_cone_pi]);
             }
             const int nch = (cnt + CHUNK - 1) / CHUNK;
+            // per lane (= gate of the batch): tensor-map rows of both inputs and the gate code
+            const int x_row = rm.row0 + (mine.x & 0x0FFFFFFF), y_row = rm.row0 + mine.y;
+            const int gop_mine = (int)((uint32_t)mine.x >> 28);
+            T* out = act + at(base, c);
             auto issue = [&](int ch) {
                 const int s = ch % NSLOT;
                 // first inputs of the chunk's 4 gates -> rows 0..3, second inputs -> rows 4..7
-                // (a partial chunk repeats its last gate)
+                // (a partial chunk repeats its last gate; gate indices stay below 32)
                 int xr[CHUNK], yr[CHUNK];
 #pragma unroll
                 for (int j = 0; j < CHUNK; j++) {
                     const int gl = min(ch * CHUNK + j, cnt - 1);
-                    xr[j] = rm.row0 + (__shfl_sync(FULL, mine.x, gl & 31) & 0x0FFFFFFF);
-                    yr[j] = rm.row0 + __shfl_sync(FULL, mine.y, gl & 31);
+                    xr[j] = __shfl_sync(FULL, x_row, gl);
+                    yr[j] = __shfl_sync(FULL, y_row, gl);
                 }
                 if (c.lane == 0) {
                     mbar_expect_tx(st.bar + s, (uint32_t)(2 * CHUNK * ROWB));
@@ -432,10 +436,11 @@ __device__ void tile_forward(const DevPlan& p, const float* __restrict__ V, int6
                 const int s = ch % NSLOT;
                 stage_wait(st, s);
                 const char* sb = st.buf + s * SLOT;
+                T* out_ch = out + ch * CHUNK * TILE;
 #pragma unroll
                 for (int j = 0; j < CHUNK; j++) {
-                    const int gl = ch * CHUNK + j;
-                    const uint32_t gop = (uint32_t)__shfl_sync(FULL, mine.x, gl & 31) >> 28;
+                    const int gl = ch * CHUNK + j;  // < 32: at most 8 chunks of a batch
+                    const int gop = __shfl_sync(FULL, gop_mine, gl);
                     if (gl < cnt) {
                         const float4 k = gcoef[gop];
                         const VF x = ActIO<T>::ld(reinterpret_cast<const T*>(sb + j * ROWB) + c.lane * VEC);
@@ -443,7 +448,7 @@ __device__ void tile_forward(const DevPlan& p, const float* __restrict__ V, int6
                         VF z;
 #pragma unroll
                         for (int q = 0; q < VEC; q++) z.v[q] = gate_apply(k, x.v[q], y.v[q]);
-                        ActIO<T>::st(act + at(base + gl, c), z);
+                        ActIO<T>::st(out_ch + j * TILE, z);
                     }
                 }
                 fence_async_shared();
@@ -524,8 +529,8 @@ __device__ void level_adjoint(const DevPlan& p, const AdjRun& run, const T* act,
         const int nn = min(31, u1 - ua);
         const int off = ua == u0 ? run.off : ((c.lane <= nn) ? __ldg(&p.fo_off[ua + c.lane]) : 0);
         const int e_begin = __shfl_sync(FULL, off, 0), e_end = __shfl_sync(FULL, off, nn);
-        int k = 0;
-        int k_end = __shfl_sync(FULL, off, 1);
+        int k = 0;                         // nodes of this run stored so far
+        float* node_row = adj + at(ua, c);  // where the next node's adjoint goes
         VF acc = vf_fill(0.0f);
         for (int base = e_begin; base < e_end; base += 32) {
             const int cnt = min(32, e_end - base);
@@ -535,17 +540,21 @@ __device__ void level_adjoint(const DevPlan& p, const AdjRun& run, const T* act,
                 if (c.lane < cnt) mine = __ldg(&p.fo_edge[base + c.lane]);
             }
             const int nch = (cnt + CHUNK - 1) / CHUNK;
+            // per lane (= edge of the batch): tensor-map rows of the consumer adjoint (an
+            // output seed, which has none, loads a stand-in row) and of the sibling
+            const int g_row = rm.row0 + max(mine.x, 0), s_row = rm.row0 + (mine.y & 0x7FFFFFFF);
+            // edges that close their node's sum (the node's adjoint row is stored there)
+            const unsigned last_mask = __ballot_sync(FULL, c.lane < cnt && mine.y < 0);
             auto issue = [&](int ch) {
                 const int s = ch % NSLOT;
-                // consumer adjoints -> the 4 fp32 rows, siblings -> the 4 act rows; an output
-                // seed (no consumer) and the tail of a partial chunk load a stand-in row
+                // consumer adjoints -> the 4 fp32 rows, siblings -> the 4 act rows (the tail of
+                // a partial chunk repeats its last edge; edge indices stay below 32)
                 int gr[CHUNK], sr[CHUNK];
 #pragma unroll
                 for (int j = 0; j < CHUNK; j++) {
                     const int el = min(ch * CHUNK + j, cnt - 1);
-                    const int g = __shfl_sync(FULL, mine.x, el & 31);
-                    gr[j] = rm.row0 + max(g, 0);
-                    sr[j] = rm.row0 + __shfl_sync(FULL, mine.y, el & 31);
+                    gr[j] = __shfl_sync(FULL, g_row, el);
+                    sr[j] = __shfl_sync(FULL, s_row, el);
                 }
                 if (c.lane == 0) {
                     char* sb = st.buf + s * SLOT;
@@ -562,32 +571,32 @@ __device__ void level_adjoint(const DevPlan& p, const AdjRun& run, const T* act,
                 const char* sb = st.buf + s * SLOT;
 #pragma unroll
                 for (int j = 0; j < CHUNK; j++) {
-                    const int el = ch * CHUNK + j;
-                    const int gx = __shfl_sync(FULL, mine.x, el & 31);
-                    const float c0 = __int_as_float(__shfl_sync(FULL, mine.z, el & 31));
-                    const float c1 = __int_as_float(__shfl_sync(FULL, mine.w, el & 31));
+                    const int el = ch * CHUNK + j;  // < 32: at most 8 chunks of a batch
+                    const int gx = __shfl_sync(FULL, mine.x, el);
+                    const float c0 = __int_as_float(__shfl_sync(FULL, mine.z, el));
+                    const float c1 = __int_as_float(__shfl_sync(FULL, mine.w, el));
                     if (el < cnt) {
-                        const int e = base + el;
-                        while (e >= k_end) {
-                            ActIO<float>::st(adj + at(ua + k, c), acc);
-                            acc = vf_fill(0.0f);
-                            k++;
-                            k_end = __shfl_sync(FULL, off, k + 1);
-                        }
                         const VF ga = gx < 0 ? seed_scale
                                              : ActIO<float>::ld(reinterpret_cast<const float*>(sb + j * ROWF) + c.lane * VEC);
                         const VF sv =
                             ActIO<T>::ld(reinterpret_cast<const T*>(sb + CHUNK * ROWF + j * ROWB) + c.lane * VEC);
 #pragma unroll
                         for (int q = 0; q < VEC; q++) acc.v[q] = fmaf(ga.v[q], fmaf(c1, sv.v[q], c0), acc.v[q]);
+                        if ((last_mask >> el) & 1u) {
+                            ActIO<float>::st(node_row, acc);
+                            node_row += TILE;
+                            acc = vf_fill(0.0f);
+                            k++;
+                        }
                     }
                 }
                 fence_async_shared();
                 __syncwarp();
             }
         }
-        while (k < nn) {
-            ActIO<float>::st(adj + at(ua + k, c), acc);
+        while (k < nn) {  // (none left: every node's range ends with a marked edge)
+            ActIO<float>::st(node_row, acc);
+            node_row += TILE;
             acc = vf_fill(0.0f);
             k++;
         }

@@ -212,12 +212,20 @@ bool build_plan(const Circuit& c, const Cnf& cnf, Plan& P, std::string& err) {
     for (int32_t n : P.out_node) P.c_out_node.push_back(cidx[n]);
 
     // Fan-out CSR (deterministic order: output seeds, then consumers by index, slot 0 first).
+    // Every cone node has at least one edge (it is an output or feeds a cone gate); a node
+    // without one would get a zero edge, so that each node's adjoint is stored at its last edge.
     std::vector<int64_t> deg(nc + 1, 0);
     for (int32_t n : P.c_out_node) deg[n]++;
     for (size_t g = 0; g < P.c_in0.size(); g++) {
         deg[P.c_in0[g]]++;
         deg[P.c_in1[g]]++;
     }
+    std::vector<int64_t> zero_edge;
+    for (int64_t i = 0; i < nc; i++)
+        if (deg[i] == 0) {
+            deg[i] = 1;
+            zero_edge.push_back(i);
+        }
     P.fo_off.assign(nc + 1, 0);
     for (int64_t i = 0; i < nc; i++) P.fo_off[i + 1] = P.fo_off[i] + deg[i];
     int64_t E = P.fo_off[nc];
@@ -247,6 +255,13 @@ bool build_plan(const Circuit& c, const Cnf& cnf, Plan& P, std::string& err) {
         span = std::max<uint32_t>(span, (uint32_t)(clev[gn] - clev[P.c_in1[g]]));
     }
     P.max_span = span;
+    for (int64_t i : zero_edge) {  // contribution 0 * (0 + 0 * A_i)
+        int64_t e = fill[i]++;
+        P.fo_g[e] = -1;
+        P.fo_sib[e] = (int32_t)i;
+        P.fo_c0[e] = 0;
+        P.fo_c1[e] = 0;
+    }
 
     // Original clauses in node space.
     P.cl_off.assign(cnf.n_clauses() + 1, 0);
