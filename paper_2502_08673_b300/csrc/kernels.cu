@@ -285,6 +285,19 @@ struct RowMaps {
     int row0;  // this tile's first row
 };
 
+// Adjoint rows are re-read by the next few levels (as consumer adjoints): stored with
+// an evict-last L2 policy (and discarded after their last reader).
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ void st_row_hint(float* p, const VF& x, uint64_t pol) {
+    static_assert(VEC == 4, "one 16-byte store per lane");
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(x.v[0]), "f"(x.v[1]),
+                 "f"(x.v[2]), "f"(x.v[3]), "l"(pol)
+                 : "memory");
+}
 __device__ __forceinline__ uint64_t policy_evict_first() {
     uint64_t pol;
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
@@ -524,6 +537,7 @@ __device__ void level_adjoint(const DevPlan& p, const AdjRun& run, const T* act,
     constexpr int ROWF = TILE * 4;
     constexpr int SLOT = slot_bytes<T>();
     const uint64_t stream_policy = policy_evict_first();
+    const uint64_t keep_policy = policy_evict_last();
     const int u0 = run.u0, u1 = run.u1;
     for (int ua = u0; ua < u1; ua += 31) {
         const int nn = min(31, u1 - ua);
@@ -583,7 +597,7 @@ __device__ void level_adjoint(const DevPlan& p, const AdjRun& run, const T* act,
 #pragma unroll
                         for (int q = 0; q < VEC; q++) acc.v[q] = fmaf(ga.v[q], fmaf(c1, sv.v[q], c0), acc.v[q]);
                         if ((last_mask >> el) & 1u) {
-                            ActIO<float>::st(node_row, acc);
+                            st_row_hint(node_row, acc, keep_policy);
                             node_row += TILE;
                             acc = vf_fill(0.0f);
                             k++;
