@@ -109,15 +109,13 @@ def train_proposal(P, torch, plan, w, mode, B, opt, ad, log, train_steps=0, roun
 
 
 def algorithmic_bytes_per_step(info, B, act_dtype):
-    """Minimum HBM bytes of one fused step with stored activations.
-
-    Per sample: every cone gate stores its activation once (forward) and
-    loads it once (adjoint); every cone input loads V (forward), stores and
-    reloads P, and loads + stores V, m, v (update).  Adjoints are counted as
-    staying on chip.
-    """
+    """HBM bytes of one fused step in the stored-activation schedule, per sample:
+    G (2 s_a + 8) + n 28 for the G gates and n inputs the step evaluates (the cone
+    of the outputs): every gate's activation is written once and read once (2 s_a),
+    its FP32 adjoint written once and read once (8); every input reads V, m, v and
+    writes them back (24) and hands its adjoint over (4)."""
     sa = ACT_BYTES[act_dtype]
-    return B * (info["n_cone_gates"] * 2 * sa + info["n_cone_pi"] * (4 + 2 * sa + 24))
+    return B * (info["n_cone_gates"] * (2 * sa + 8) + info["n_cone_pi"] * 28)
 
 
 class ClockSampler:
