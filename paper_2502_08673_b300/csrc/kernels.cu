@@ -33,7 +33,10 @@ namespace {
 constexpr int VEC = SAT_VEC;           // consecutive samples per lane
 constexpr int TILE = 32 * VEC;         // samples per CTA
 static_assert(TILE == SAT_TILE_SAMPLES, "tile width must match the ABI");
-constexpr int STEP_THREADS = 640;
+// Threads of a step-kernel CTA: 20 warps with FP32 activations, 24 with 16-bit ones
+// (their smaller staging slots leave room; measured best for each).
+template <typename T>
+__host__ __device__ constexpr int step_threads() { return sizeof(T) == 4 ? 640 : 768; }
 constexpr int UBATCH = 2;              // input rows per warp in the input-level passes
 constexpr unsigned FULL = 0xffffffffu;
 
@@ -477,7 +480,7 @@ __device__ void tile_forward(const DevPlan& p, const float* __restrict__ V, int6
 // Per-sample loss sum_j (Y_j - T_j)^2, FP32, fixed order (warp-strided partials, then warp order).
 template <typename T>
 __device__ void tile_loss(const DevPlan& p, const T* act, float* loss, const TileCtx& c) {
-    __shared__ VF part[STEP_THREADS / 32][32];
+    __shared__ VF part[step_threads<T>() / 32][32];
     VF acc = vf_fill(0.0f);
     for (int j = c.warp; j < p.n_out; j += c.nw) {
         const VF y = ActIO<T>::ldcg(act + at(p.c_out_node[j], c));
@@ -722,7 +725,7 @@ __device__ __forceinline__ Stage init_stage(char* smem, const DevPlan& p, float4
 }
 
 template <typename T>
-__global__ void __launch_bounds__(STEP_THREADS, 1) forward_kernel(DevPlan p, const float* V, int64_t ldv, T* act,
+__global__ void __launch_bounds__(step_threads<T>(), 1) forward_kernel(DevPlan p, const float* V, int64_t ldv, T* act,
                                                                   float* loss, int64_t B,
                                                                   const __grid_constant__ CUtensorMap amap) {
     extern __shared__ __align__(128) char smem[];
@@ -736,7 +739,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) forward_kernel(DevPlan p, con
 }
 
 template <typename T>
-__global__ void __launch_bounds__(STEP_THREADS, 1) backward_kernel(DevPlan p, const float* V, int64_t ldv,
+__global__ void __launch_bounds__(step_threads<T>(), 1) backward_kernel(DevPlan p, const float* V, int64_t ldv,
                                                                    const T* act, float* adj, const float* grad_loss,
                                                                    float* gV, int64_t B,
                                                                    const __grid_constant__ CUtensorMap amap,
@@ -759,7 +762,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) backward_kernel(DevPlan p, co
 // at Adam steps t0 + s (+ age[b] per sample when age is given).
 // SPLIT: launched in clusters of two CTAs per tile (tiles tile0, tile0 + 1, ...).
 template <typename T, bool SPLIT>
-__global__ void __launch_bounds__(STEP_THREADS, 1) steps_kernel(DevPlan p, OptParams o, float* V, float* m, float* v,
+__global__ void __launch_bounds__(step_threads<T>(), 1) steps_kernel(DevPlan p, OptParams o, float* V, float* m, float* v,
                                                                 int64_t ldv, T* act, float* adj, float* loss,
                                                                 int t0, const int32_t* age, int n_steps, int64_t B,
                                                                 int tile0, const __grid_constant__ CUtensorMap amap,
@@ -784,7 +787,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) steps_kernel(DevPlan p, OptPa
 
 template <typename T>
 constexpr size_t stage_smem() {
-    return (size_t)(STEP_THREADS / 32) * warp_stage_bytes<T>();
+    return (size_t)(step_threads<T>() / 32) * warp_stage_bytes<T>();
 }
 
 // Opt the step kernels into the dynamic shared memory they use (once per type).
@@ -1097,7 +1100,7 @@ cudaError_t forward_launch(const DevPlan& p, const float* V, int64_t ldv, void* 
     const unsigned grid = (unsigned)((B + TILE - 1) / TILE);
     CUtensorMap amap, gmap;
     if ((e = row_maps<T>(p, act, nullptr, grid, &amap, &gmap)) != cudaSuccess) return e;
-    forward_kernel<T><<<grid, STEP_THREADS, stage_smem<T>(), s>>>(p, V, ldv, (T*)act, loss, B, amap);
+    forward_kernel<T><<<grid, step_threads<T>(), stage_smem<T>(), s>>>(p, V, ldv, (T*)act, loss, B, amap);
     return cudaGetLastError();
 }
 
@@ -1109,7 +1112,7 @@ cudaError_t backward_launch(const DevPlan& p, const float* V, int64_t ldv, const
     const unsigned grid = (unsigned)((B + TILE - 1) / TILE);
     CUtensorMap amap, gmap;
     if ((e = row_maps<T>(p, act, adj, grid, &amap, &gmap)) != cudaSuccess) return e;
-    backward_kernel<T><<<grid, STEP_THREADS, stage_smem<T>(), s>>>(p, V, ldv, (const T*)act, adj, grad_loss, gV, B,
+    backward_kernel<T><<<grid, step_threads<T>(), stage_smem<T>(), s>>>(p, V, ldv, (const T*)act, adj, grad_loss, gV, B,
                                                                    amap, gmap);
     return cudaGetLastError();
 }
@@ -1133,14 +1136,14 @@ cudaError_t steps_launch(const DevPlan& p, const OptParams& o, float* V, float* 
     if (2 * (tiles - main_tiles) > sms) main_tiles = tiles;
     const int tail = tiles - main_tiles;
     if (main_tiles > 0) {
-        steps_kernel<T, false><<<(unsigned)main_tiles, STEP_THREADS, stage_smem<T>(), s>>>(
+        steps_kernel<T, false><<<(unsigned)main_tiles, step_threads<T>(), stage_smem<T>(), s>>>(
             p, o, V, m, v, ldv, (T*)act, adj, loss, t0, age, n_steps, B, 0, amap, gmap);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (tail > 0) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(2 * tail), 1, 1);
-        cfg.blockDim = dim3(STEP_THREADS, 1, 1);
+        cfg.blockDim = dim3(step_threads<T>(), 1, 1);
         cfg.dynamicSmemBytes = stage_smem<T>();
         cfg.stream = s;
         cudaLaunchAttribute attr[1];
