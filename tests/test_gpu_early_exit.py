@@ -158,3 +158,33 @@ def test_run_epochs_matches_c_loop(gpu):
                 key[i // 32] |= np.uint32(1) << np.uint32(i % 32)
         theirs.add(key.view(np.int32).tobytes())
     assert mine == theirs and len(mine) > 0
+
+
+def test_early_exit_with_proposal_restarts(gpu):
+    """sat_sample with early exit and a proposal network: restarted slots start from the
+    proposal's logits (its noise of the restart round); every returned assignment is valid."""
+    import paper_2502_08673_b300 as P
+    text = planted_3sat(50, 200, 3).dimacs()
+    cnf = P.Cnf.from_dimacs(text)
+    circ = P.Circuit.build(cnf)
+    plan = P.Plan.create(circ, cnf)
+    B = 512
+    mlp = P.Mlp.create(64, 256, plan.n_pi, max_rows=B, seed=1)
+    sols = P.sample(circ, cnf, n_wanted=10 ** 9, batch=B, steps=60, max_rounds=1, lr=0.1, seed=3,
+                    proposal=mlp, tau=1.0, check_every=10, max_age=30)
+    A = sols.assignments()
+    n, cl = oracle.parse_dimacs(text)
+    assign = np.zeros((len(A), n + 1), np.uint8)
+    assign[:, 1:] = A
+    assert oracle.cnf_check(n, cl, assign).all()
+    assert sols.stats["rounds"] == 6 and sols.stats["samples"] >= B
+    # the Python orchestration on the same streams restarts from the proposal: after one epoch
+    # with every sample forced to restart (max_age 1), V equals the proposal of round 1
+    ws = P.new_workspace(plan, B)
+    dd = P.Dedup.create(plan, max_keys=4 * B, max_batch=B)
+    P.run_epochs(plan, ws, P.opt_params("adam", lr=0.1), 1, 1, 1, seed=3, round_=0, dedup=dd, proposal=mlp)
+    expect = torch.empty_like(ws.V)
+    mlp.propose(expect, 3, 1, 1.0)
+    torch.cuda.synchronize()
+    assert torch.equal(ws.V, expect)
+    assert (ws.m == 0).all() and (ws.v == 0).all() and (ws.age == 0).all()
