@@ -325,6 +325,15 @@ sat_status sat_mlp_loss_grad(sat_mlp* m, const void* z, const uint32_t* keys, in
 /* One IMLE step with K candidates per target and Adam (lr, PyTorch defaults otherwise). */
 sat_status sat_mlp_train_step(sat_mlp* m, const uint32_t* keys, int32_t key_words, int64_t S, int32_t K, float lr,
                               uint64_t seed, uint32_t round, float* loss_host, void* stream);
+/* Train the proposal on distinct solutions: sols holds n full assignments in the
+ * sat_solutions_copy format (host uint64 words, ceil(n_vars/64) per solution) of the
+ * circuit the plan p was made from; their primary-input bits (in p's input order, the
+ * network's outputs) are the targets.  `steps` IMLE steps (sat_mlp_train_step) of S targets
+ * drawn uniformly with replacement (SplitMix64 of seed) and K candidates each, learning rate
+ * lr; loss_host (nullable) receives the last step's mean loss.  S*K must be <= max_rows.
+ * Each step's S targets are gathered on the host and copied in; synchronises the stream at the end. */
+sat_status sat_mlp_train(sat_mlp* m, const sat_plan* p, const uint64_t* sols, uint64_t n, int32_t steps, int64_t S,
+                         int32_t K, float lr, uint64_t seed, float* loss_host, void* stream);
 /* Status word of the network's kernels (bit 3: a bounded GEMM wait expired). */
 sat_status sat_mlp_status(const sat_mlp* m, uint32_t* status);
 void sat_mlp_free(sat_mlp* m);

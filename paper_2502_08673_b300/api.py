@@ -264,6 +264,17 @@ class Mlp(_Handle):
                                       g.ctypes.data_as(C.c_void_p), _stream(stream)))
         return loss.value, g
 
+    def train(self, plan: "Plan", solutions, steps: int, S: int = 4096, K: int = 16, lr: float = 1e-3,
+              seed: int = 0, stream=None) -> float:
+        """IMLE training on distinct solutions (sat_mlp_train): `solutions` is a uint64 array
+        [n, ceil(n_vars/64)] of full assignments (Solutions.words() format) of plan's circuit.
+        Returns the last step's mean loss."""
+        w = np.ascontiguousarray(solutions, dtype=np.uint64)
+        loss = C.c_float()
+        check(lib().sat_mlp_train(self._h, plan.handle, w.ctypes.data, w.shape[0], steps, S, K, lr, seed,
+                                  C.byref(loss), _stream(stream)))
+        return float(loss.value)
+
     def train_step(self, keys, S: int, K: int, lr: float, seed: int, round_: int, stream=None) -> float:
         loss = C.c_float()
         check(lib().sat_mlp_train_step(self._h, _ptr(keys), keys.shape[1], S, K, lr, seed, round_, C.byref(loss),

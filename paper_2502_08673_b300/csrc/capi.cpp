@@ -389,6 +389,51 @@ sat_status sat_plan_pi_vars(const sat_plan* p, uint32_t* vars) {
     return SAT_OK;
 }
 
+sat_status sat_mlp_train(sat_mlp* m, const sat_plan* p, const uint64_t* sols, uint64_t n, int32_t steps, int64_t nb,
+                         int32_t K, float lr, uint64_t seed, float* loss_host, void* stream) {
+    if (!m || !p || (!sols && n > 0) || steps < 0 || nb < 1 || K < 1 || !(lr > 0.0f))
+        return fail(SAT_ERR_ARG, "bad argument (S, K >= 1, lr > 0, steps >= 0)");
+    if (n == 0 || steps == 0) return SAT_OK;
+    const size_t n_pi = p->pi_var.size(), kw = (n_pi + 31) / 32, aw = (p->info.n_vars + 63) / 64;
+    if (n_pi == 0) return fail(SAT_ERR_ARG, "the plan has no primary inputs");
+    // targets: the primary-input bits of every solution, packed like the sampler's keys
+    std::vector<uint32_t> keys(n * kw, 0u);
+    for (uint64_t s = 0; s < n; s++)
+        for (size_t i = 0; i < n_pi; i++) {
+            const uint32_t v = p->pi_var[i] - 1;  // DIMACS var v -> bit v-1 of the assignment
+            if ((sols[s * aw + v / 64] >> (v % 64)) & 1ull) keys[s * kw + i / 32] |= 1u << (i % 32);
+        }
+    cudaStream_t str = S(stream);
+    uint32_t* d_batch = nullptr;
+    struct Free {
+        void* a;
+        ~Free() { cudaFree(a); }
+    } fr{nullptr};
+    if (cudaMalloc(&d_batch, (size_t)nb * kw * 4) != cudaSuccess) return fail(SAT_ERR_OOM, "cudaMalloc failed (batch)");
+    fr.a = d_batch;
+    std::vector<uint32_t> batch((size_t)nb * kw);
+    uint64_t state = seed;
+    auto next = [&state]() {  // SplitMix64
+        uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    for (int32_t it = 0; it < steps; it++) {
+        for (int64_t j = 0; j < nb; j++) {
+            const uint64_t r = next() % n;
+            std::copy(keys.begin() + r * kw, keys.begin() + (r + 1) * kw, batch.begin() + j * kw);
+        }
+        // pageable source: staged before the call returns, so the buffer is reused safely
+        CK(cudaMemcpyAsync(d_batch, batch.data(), batch.size() * 4, cudaMemcpyHostToDevice, str));
+        sat_status s = sat_mlp_train_step(m, d_batch, (int32_t)kw, nb, K, lr, seed, (uint32_t)it,
+                                          it + 1 == steps ? loss_host : nullptr, stream);
+        if (s != SAT_OK) return s;
+    }
+    CK(cudaStreamSynchronize(str));
+    return SAT_OK;
+}
+
 sat_status sat_plan_var_nodes(const sat_plan* p, int64_t* cone_node, int64_t* full_node, uint8_t* neg) {
     if (!p) return fail(SAT_ERR_ARG, "NULL plan");
     if (cone_node) std::copy(p->var_cone.begin(), p->var_cone.end(), cone_node);

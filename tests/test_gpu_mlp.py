@@ -119,3 +119,45 @@ def test_imle_training_reduces_loss(gpu):
     assert mlp.status() == 0
     assert np.isfinite(losses).all()
     assert np.mean(losses[-5:]) < 0.5 * np.mean(losses[:5])
+
+
+def test_train_on_solutions_equals_manual_steps(gpu):
+    """sat_mlp_train: the targets are the solutions' primary-input bits, S of them drawn per
+    step by SplitMix64 (Steele, Lea, Flood 2014) of the seed; equal, bit for bit, to
+    train_step on the same batches."""
+    import paper_2502_08673_b300 as P
+    from workloads import tseitin_random_circuit
+    text = tseitin_random_circuit(64, 640, 16, 8, seed=3).dimacs()
+    cnf = P.Cnf.from_dimacs(text)
+    circ = P.Circuit.build(cnf)
+    plan = P.Plan.create(circ, cnf)
+    sols = P.sample(circ, cnf, n_wanted=10 ** 9, batch=1024, steps=100, max_rounds=2, seed=0)
+    W = sols.words()
+    n = len(W)
+    assert n > 10
+    S, K, steps, seed = 64, 4, 5, 11
+    a = P.Mlp.create(64, 256, plan.n_pi, max_rows=S * K, seed=2)
+    b = P.Mlp.create(64, 256, plan.n_pi, max_rows=S * K, seed=2)
+    la = a.train(plan, W, steps, S=S, K=K, lr=1e-3, seed=seed)
+    pis = [int(v) - 1 for v in plan.pi_vars()]
+    bits = np.array([[(int(W[s][v // 64]) >> (v % 64)) & 1 for v in pis] for s in range(n)], np.uint8)
+    keys_all = _keys(bits)
+    M64 = (1 << 64) - 1
+    state = seed
+
+    def nxt():
+        nonlocal state
+        state = (state + 0x9E3779B97F4A7C15) & M64
+        z = state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M64
+        return z ^ (z >> 31)
+
+    lb = None
+    for it in range(steps):
+        idx = [nxt() % n for _ in range(S)]
+        lb = b.train_step(keys_all[idx].contiguous().to(gpu), S, K, lr=1e-3, seed=seed, round_=it)
+    torch.cuda.synchronize()
+    assert a.status() == 0 and b.status() == 0
+    assert np.array_equal(a.params(), b.params())
+    assert la == lb
