@@ -108,14 +108,17 @@ def train_proposal(P, torch, plan, w, mode, B, opt, ad, log, train_steps=0, roun
     return mlp
 
 
-def algorithmic_bytes_per_step(info, B, act_dtype):
+def algorithmic_bytes_per_step(info, B, act_dtype, segment=0):
     """HBM bytes of one fused step in the stored-activation schedule, per sample:
     G (2 s_a + 8) + n 28 for the G gates and n inputs the step evaluates (the cone
     of the outputs): every gate's activation is written once and read once (2 s_a),
     its FP32 adjoint written once and read once (8); every input reads V, m, v and
-    writes them back (24) and hands its adjoint over (4)."""
+    writes them back (24) and hands its adjoint over (4).  With recomputation every
+    k levels: G s_a (1 + 1/k) more (the re-evaluated activations written again, the
+    kept levels read again)."""
     sa = ACT_BYTES[act_dtype]
-    return B * (info["n_cone_gates"] * (2 * sa + 8) + info["n_cone_pi"] * 28)
+    extra = info["n_cone_gates"] * sa * (1 + 1 / segment) if segment > 0 else 0
+    return B * (info["n_cone_gates"] * (2 * sa + 8) + info["n_cone_pi"] * 28 + extra)
 
 
 class ClockSampler:
@@ -374,6 +377,8 @@ def main():
     ap.add_argument("--reorder", action="store_true",
                     help="sort clauses by (largest variable, length, position) before Algorithm 1")
     ap.add_argument("--optimizer", default="adam", choices=["adam", "gd"])
+    ap.add_argument("--recompute", type=int, default=0,
+                    help="level-segment recomputation every K levels (0: store every activation)")
     ap.add_argument("--lr", type=float, default=0.0, help="override the workload's learning rate")
     ap.add_argument("--curve", default="",
                     help="comma-separated step counts: unique solutions vs iterations (one JSON line)")
@@ -415,7 +420,7 @@ def main():
     info = plan.info
     B, steps, ad = w["batch"], w["steps"], w["act_dtype"]
     opt = P.opt_params(args.optimizer, lr=w["lr"])
-    ws = P.new_workspace(plan, B, ad)
+    ws = P.new_workspace(plan, B, ad, segment=args.recompute)
     if args.curve:
         return run_curve(P, torch, plan, ws, opt, args, w, info)
     n_rounds = args.warmup + args.steps
@@ -451,7 +456,8 @@ def main():
         if ev is not None:
             ev[0].record(stream)
         P.sat_steps(plan, opt, ws.V, ws.m, ws.v, ws.act, ws.adj, 1,
-                    n_steps or (prop_steps if (mlp is not None and use_mlp) else steps), act_dtype=ad)
+                    n_steps or (prop_steps if (mlp is not None and use_mlp) else steps), act_dtype=ad,
+                    segment=args.recompute)
         if ev is not None:
             ev[1].record(stream)
         P.sat_threshold(plan, ws.V, ws.bits, ws.keys)
@@ -493,7 +499,7 @@ def main():
     run_steps = prop_steps if (mlp is not None and args.check_every <= 0) else steps
     gate_evals = info["n_cone_gates"] * B * run_steps * args.steps * world
     peak, peak_kind = measured_peaks()
-    alg = algorithmic_bytes_per_step(info, B, ad) * (launch_steps or run_steps)
+    alg = algorithmic_bytes_per_step(info, B, ad, args.recompute) * (launch_steps or run_steps)
     kavg = statistics.mean(kernel_ms)
     achieved = alg / (kavg / 1e3) / 1e9
     dram_per_sample_step, prof = profile_traffic(args.workload, ad)
@@ -519,6 +525,7 @@ def main():
             tp = e0.elapsed_time(e1)
             plain_cmp[label] = {"steps": ns, "value": (dedup.count() - before_p) / (tp / 1e3),
                                 "valid_fraction": vp / (B * args.steps), "ms_per_step": tp / args.steps}
+    scratch = {"act": ws.act.numel() * ws.act.element_size(), "adj": ws.adj.numel() * ws.adj.element_size()}
     del ws, dedup
     torch.cuda.empty_cache()
     e2e = None
@@ -552,8 +559,9 @@ def main():
             "data": "synthetic (seeded Tseitin random circuit)" if w["kind"] == "tseitin" else "synthetic (planted 3-SAT)",
             "config": {"workload": args.workload, **{k: v for k, v in w.items() if k != "kind"},
                        "optimizer": args.optimizer, "relaxation": "direct CNF" if args.direct else "Algorithm 1",
+                       "recompute_segment": args.recompute,
                        "l2_flush": "working set > L2 (activations %.1f GB)" %
-                       (info["n_cone"] * B * ACT_BYTES[ad] / 1e9),
+                       (scratch["act"] / 1e9),
                        "parallelism": f"replicas x{world} (disjoint Philox streams)"},
             "gate_evals_per_s": gate_evals / (t_max / 1e3),
             "valid_fraction": (valid_all / (B * args.steps * world)) if args.check_every <= 0 else None,
@@ -569,6 +577,7 @@ def main():
             "transform_s": transform_s,
             "plan": {k: info[k] for k in ("n_pi", "n_cone_pi", "n_cone_gates", "n_gates", "n_clauses",
                                           "n_cone_levels", "max_span")},
+            "scratch_bytes": scratch,
             "clocks": clocks.summary(),
             "cpu_baseline": cpu,
             "e2e": e2e,

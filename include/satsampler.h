@@ -147,8 +147,17 @@ sat_status sat_plan_var_nodes(const sat_plan* p, int64_t* cone_node, int64_t* fu
  * healthy; bit 2 = a bounded wait for an asynchronous copy expired, and the
  * results of that launch are invalid.  clear != 0 resets it. */
 sat_status sat_plan_status(const sat_plan* p, uint32_t* status, int32_t clear, void* stream);
-/* Elements of one act / adj scratch array for a batch of B samples. */
+/* Elements of one act / adj scratch array for a batch of B samples (enough for
+ * either array under every call that takes them without a segment). */
 sat_status sat_plan_scratch_elems(const sat_plan* p, int64_t B, uint64_t* elems);
+/* Exact sizes: act_elems (nullable) = elements of the act array of the fused steps
+ * with recomputation segment `segment` (0 = every level stored: the layout of
+ * sat_forward / sat_steps), adj_elems (nullable) = elements of the adj array (a ring
+ * of max_span + 1 gate levels plus the input level, the same for every call).  A
+ * segment > 0 builds and uploads that layout on first use (synchronous device
+ * allocations and copies: make the first call before any stream capture). */
+sat_status sat_plan_layout_elems(const sat_plan* p, int32_t segment, int64_t B, uint64_t* act_elems,
+                                 uint64_t* adj_elems);
 void sat_plan_free(sat_plan* p);
 
 /* ------------------------------------------- hot-path kernels (device) ---
@@ -169,8 +178,9 @@ sat_status sat_forward(const sat_plan* p, sat_act_dtype act_dtype, const float* 
 
 /* Eq. 8 (chain rule with the Table 1 derivatives): gV[r][b] = d(sum_b w_b
  * loss_b)/dV[r][b] with w = grad_loss (NULL = all ones), from the act written
- * by sat_forward.  adj: float32 scratch of the act layout.  Rows of gV outside
- * the cone are not written (their gradient is zero). */
+ * by sat_forward.  adj: float32 scratch (sat_plan_layout_elems; its contents are
+ * undefined afterwards).  Rows of gV outside the cone are not written (their
+ * gradient is zero). */
 sat_status sat_backward(const sat_plan* p, sat_act_dtype act_dtype, const float* V, int64_t ldv, const void* act,
                         float* adj, const float* grad_loss, float* gV, int64_t B, void* stream);
 
@@ -198,6 +208,22 @@ sat_status sat_steps(const sat_plan* p, sat_act_dtype act_dtype, const sat_opt_p
 sat_status sat_steps_aged(const sat_plan* p, sat_act_dtype act_dtype, const sat_opt_params* o, float* V, float* m,
                           float* v, int64_t ldv, void* act, float* adj, float* loss, const int32_t* age, int32_t t0,
                           int32_t n_steps, int64_t B, void* stream);
+
+/* sat_steps_aged with level-segment recomputation (segment > 0): the forward pass
+ * keeps, of the gate levels, only the top max_span levels of every segment of
+ * `segment` levels (the inputs of the next segment) and the levels holding outputs;
+ * the backward pass evaluates each segment's other levels again (Eqs. 5-6, the same
+ * arithmetic in the same order) before its adjoints.  Results are bit-identical to
+ * sat_steps_aged; act needs sat_plan_layout_elems(p, segment, B) elements instead of
+ * the full layout, for about (1 - max_span/segment) of a forward pass more work per step.
+ * segment = 0 is sat_steps_aged, and so is a segment whose layout would not be smaller
+ * than the full one (segment <= max_span, or segments so long that the two scratch
+ * buffers outweigh the levels saved).  The paper stores every activation (autograd);
+ * this is a memory schedule for circuits x batches beyond device memory. */
+sat_status sat_steps_recompute(const sat_plan* p, sat_act_dtype act_dtype, const sat_opt_params* o, float* V,
+                               float* m, float* v, int64_t ldv, void* act, float* adj, float* loss,
+                               const int32_t* age, int32_t t0, int32_t n_steps, int64_t B, int32_t segment,
+                               void* stream);
 
 /* Early exit: verify every k steps, harvest the valid samples and give their
  * slots (and those of samples that have not converged after max_age steps) a
@@ -362,6 +388,7 @@ typedef struct sat_sample_opts {
     int32_t check_every;        /* > 0: early exit, verify every check_every steps (see sat_retire);
                                    the budget stays max_rounds x steps descent steps of the batch */
     int32_t max_age;            /* early exit: restart samples unsolved after max_age steps (0 = steps) */
+    int32_t recompute_segment;  /* > 0: level-segment recomputation (sat_steps_recompute); 0 = store all */
 } sat_sample_opts;
 
 typedef struct sat_sample_stats {

@@ -55,7 +55,8 @@ class SampleOpts(C.Structure):
                 ("seed", C.c_uint64), ("first_round", C.c_uint32), ("init_scale", C.c_float),
                 ("act_dtype", C.c_int32), ("steps_per_launch", C.c_int32), ("init_logits", C.c_void_p),
                 ("init_ld", C.c_int64), ("stream", C.c_void_p), ("proposal", C.c_void_p),
-                ("proposal_tau", C.c_float), ("check_every", C.c_int32), ("max_age", C.c_int32)]
+                ("proposal_tau", C.c_float), ("check_every", C.c_int32), ("max_age", C.c_int32),
+                ("recompute_segment", C.c_int32)]
 
 
 class SampleStats(C.Structure):
@@ -84,6 +85,7 @@ PROTOTYPES = {
     "sat_plan_pi_vars": (I32, [P, P]),
     "sat_plan_var_nodes": (I32, [P, P, P, P]),
     "sat_plan_scratch_elems": (I32, [P, I64, C.POINTER(U64)]),
+    "sat_plan_layout_elems": (I32, [P, I32, I64, C.POINTER(U64), C.POINTER(U64)]),
     "sat_plan_status": (I32, [P, C.POINTER(U32), I32, P]),
     "sat_plan_free": (None, [P]),
     "sat_init_normal": (I32, [P, U64, U32, F32, P, I64, I64, P]),
@@ -93,6 +95,7 @@ PROTOTYPES = {
     "sat_steps": (I32, [P, I32, C.POINTER(OptParams), P, P, P, I64, P, P, P, I32, I32, I64, P]),
     "sat_steps_noalloc": (I32, [P, I32, C.POINTER(OptParams), P, P, P, I64, P, I32, I32, I64, P]),
     "sat_steps_aged": (I32, [P, I32, C.POINTER(OptParams), P, P, P, I64, P, P, P, P, I32, I32, I64, P]),
+    "sat_steps_recompute": (I32, [P, I32, C.POINTER(OptParams), P, P, P, I64, P, P, P, P, I32, I32, I64, I32, P]),
     "sat_retire": (I32, [P, P, P, I32, I32, I64, P]),
     "sat_restart": (I32, [P, P, U64, U32, F32, P, I64, P, P, P, I64, I64, P]),
     "sat_threshold": (I32, [P, P, I64, P, I64, P, I64, P]),

@@ -136,6 +136,13 @@ class Plan(_Handle):
         check(lib().sat_plan_scratch_elems(self._h, B, C.byref(n)))
         return n.value
 
+    def layout_rows(self, segment: int = 0):
+        """Rows per 128-sample tile of the act scratch (recomputation segment `segment`,
+        0 = every level stored) and of the adj scratch (the adjoint ring)."""
+        a, g = C.c_uint64(), C.c_uint64()
+        check(lib().sat_plan_layout_elems(self._h, segment, N.TILE, C.byref(a), C.byref(g)))
+        return a.value // N.TILE, g.value // N.TILE
+
     def pi_vars(self) -> np.ndarray:
         out = np.zeros(self.info["n_pi"], np.uint32)
         check(lib().sat_plan_pi_vars(self._h, out.ctypes.data_as(C.c_void_p)))
@@ -301,18 +308,22 @@ def _tiles(B: int) -> int:
     return (B + N.TILE - 1) // N.TILE
 
 
-def new_act(plan: Plan, B: int, act_dtype: str = "f32", device="cuda"):
+def new_act(plan: Plan, B: int, act_dtype: str = "f32", device="cuda", segment: int = 0):
+    """act scratch [tiles][rows][128]: rows = n_cone (segment 0, every level stored; the
+    layout sat_forward writes) or the rows of recomputation segment `segment`."""
     import torch
-    return torch.empty((_tiles(B), plan.info["n_cone"], N.TILE), dtype=_act_torch_dtype(act_dtype), device=device)
+    rows = plan.info["n_cone"] if segment == 0 else plan.layout_rows(segment)[0]
+    return torch.empty((_tiles(B), rows, N.TILE), dtype=_act_torch_dtype(act_dtype), device=device)
 
 
 def new_adj(plan: Plan, B: int, device="cuda"):
+    """adj scratch [tiles][rows][128] (the input level plus a ring of max_span + 1 gate levels)."""
     import torch
-    return torch.empty((_tiles(B), plan.info["n_cone"], N.TILE), dtype=torch.float32, device=device)
+    return torch.empty((_tiles(B), plan.layout_rows(0)[1], N.TILE), dtype=torch.float32, device=device)
 
 
 def untile(x, B: int):
-    """[n_cone, B] view of a tile-major act/adj array."""
+    """[n_cone, B] view of a tile-major act array of the full layout."""
     return x.permute(1, 0, 2).reshape(x.shape[1], -1)[:, :B]
 
 
@@ -336,9 +347,14 @@ def sat_opt_update(plan: Plan, opt: N.OptParams, V, m, v, gV, t: int, stream=Non
 
 
 def sat_steps(plan: Plan, opt: N.OptParams, V, m, v, act, adj, t0: int, n_steps: int, loss=None,
-              act_dtype="f32", stream=None, age=None):
-    """Fused steps; with `age` (int32 [B]) the Adam step of sample b is age[b] + t0 + s (sat_steps_aged)."""
-    if age is None:
+              act_dtype="f32", stream=None, age=None, segment: int = 0):
+    """Fused steps; with `age` (int32 [B]) the Adam step of sample b is age[b] + t0 + s (sat_steps_aged);
+    with segment > 0, level-segment recomputation (sat_steps_recompute; act from new_act(..., segment=))."""
+    if segment:
+        check(lib().sat_steps_recompute(plan.handle, N.ACT_DTYPES[act_dtype], C.byref(opt), _ptr(V), _ptr(m),
+                                        _ptr(v), V.stride(0), _ptr(act), _ptr(adj), _ptr(loss), _ptr(age), t0,
+                                        n_steps, V.shape[1], segment, _stream(stream)))
+    elif age is None:
         check(lib().sat_steps(plan.handle, N.ACT_DTYPES[act_dtype], C.byref(opt), _ptr(V), _ptr(m), _ptr(v),
                               V.stride(0), _ptr(act), _ptr(adj), _ptr(loss), t0, n_steps, V.shape[1],
                               _stream(stream)))
@@ -408,18 +424,19 @@ class Workspace:
     age: object = None      # early exit (run_epochs): int32 [B] steps since each sample's start
     restart: object = None  # early exit: restart bits [ceil(B/32)]
     src: object = None      # early exit with a proposal: new starts [n_pi][B]
+    segment: int = 0        # level-segment recomputation of the fused steps (act laid out for it)
 
 
-def new_workspace(plan: Plan, B: int, act_dtype: str = "f32", device="cuda") -> Workspace:
+def new_workspace(plan: Plan, B: int, act_dtype: str = "f32", device="cuda", segment: int = 0) -> Workspace:
     import torch
     npi = plan.info["n_pi"]
     W = (B + 31) // 32
     z = lambda *s: torch.zeros(s, dtype=torch.float32, device=device)
     return Workspace(
-        B, z(npi, B), z(npi, B), z(npi, B), new_act(plan, B, act_dtype, device), new_adj(plan, B, device),
+        B, z(npi, B), z(npi, B), z(npi, B), new_act(plan, B, act_dtype, device, segment), new_adj(plan, B, device),
         torch.zeros((plan.info["n_nodes"], W), dtype=torch.int32, device=device),
         torch.zeros((B, max(1, plan.info["key_words"])), dtype=torch.int32, device=device),
-        torch.zeros(W, dtype=torch.int32, device=device), z(B), act_dtype)
+        torch.zeros(W, dtype=torch.int32, device=device), z(B), act_dtype, segment=segment)
 
 
 def run_round(plan: Plan, ws: Workspace, opt: N.OptParams, steps: int, seed: int, round_: int,
@@ -437,7 +454,7 @@ def run_round(plan: Plan, ws: Workspace, opt: N.OptParams, steps: int, seed: int
     ws.v.zero_()
     if steps > 0:
         sat_steps(plan, opt, ws.V, ws.m, ws.v, ws.act, ws.adj, 1, steps, loss=ws.loss, act_dtype=ws.act_dtype,
-                  stream=stream)
+                  stream=stream, segment=ws.segment)
     sat_threshold(plan, ws.V, ws.bits, ws.keys, stream)
     sat_hard_eval(plan, ws.bits, ws.B, stream)
     sat_cnf_check(plan, ws.bits, ws.valid, ws.B, stream)
@@ -474,7 +491,7 @@ def run_epochs(plan: Plan, ws: Workspace, opt: N.OptParams, steps: int, check_ev
             ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
             ev[0].record(stream)
         sat_steps(plan, opt, ws.V, ws.m, ws.v, ws.act, ws.adj, 1, kk, act_dtype=ws.act_dtype, stream=stream,
-                  age=ws.age)
+                  age=ws.age, segment=ws.segment)
         if events is not None:
             ev[1].record(stream)
             events.append((kk, ev))
@@ -501,8 +518,9 @@ def valid_mask(valid_words, B: int) -> np.ndarray:
 def sample(circuit: Circuit, cnf: Cnf, n_wanted: int, batch=1024, steps=200, max_rounds=1, optimizer="adam",
            lr=0.1, beta1=0.9, beta2=0.999, eps=1e-8, seed=0, first_round=0, init_scale=1.0, act_dtype="f32",
            steps_per_launch=0, proposal: "Mlp | None" = None, tau: float = 1.0, check_every=0, max_age=0,
-           stream=None):
-    """End to end from host objects (the C call sat_sample); check_every > 0 = early exit."""
+           recompute_segment=0, stream=None):
+    """End to end from host objects (the C call sat_sample); check_every > 0 = early exit;
+    recompute_segment > 0 = level-segment recomputation in the fused steps."""
     o = N.SampleOpts()
     lib().sat_sample_opts_default(C.byref(o))
     o.batch, o.steps, o.max_rounds = batch, steps, max_rounds
@@ -513,6 +531,7 @@ def sample(circuit: Circuit, cnf: Cnf, n_wanted: int, batch=1024, steps=200, max
     o.proposal = None if proposal is None else proposal.handle
     o.proposal_tau = tau
     o.check_every, o.max_age = check_every, max_age
+    o.recompute_segment = recompute_segment
     h = C.c_void_p()
     st = N.SampleStats()
     status = check(lib().sat_sample(circuit.handle, cnf.handle, C.byref(o), n_wanted, C.byref(h), C.byref(st)),

@@ -9,6 +9,8 @@
 #include <cstdio>
 #include <cstring>
 #include <fstream>
+#include <map>
+#include <mutex>
 #include <new>
 #include <sstream>
 #include <string>
@@ -36,6 +38,14 @@ struct sat_plan {
     sat::DevPlan dp;
     std::vector<void*> allocs;
     std::vector<int32_t> h_c_level_off, h_f_level_off;
+    // host copies of the cone records (full layout), for building recomputation layouts
+    std::vector<int2> h_gate;
+    std::vector<int4> h_edge;
+    std::vector<int32_t> h_out;
+    // recomputation layouts, built on first use (segment length -> layout)
+    mutable std::mutex lay_mu;
+    mutable std::map<int32_t, sat::DevAct> layouts;
+    mutable std::vector<void*> lay_allocs;
     std::vector<uint32_t> pi_var;
     std::vector<int64_t> var_cone, var_full;
     std::vector<uint8_t> var_neg;
@@ -78,19 +88,23 @@ sat_status fail(sat_status s, const std::string& m) {
     } while (0)
 
 template <typename T>
-sat_status upload(sat_plan* p, const std::vector<T>& h, const T** dst) {
+sat_status upload_to(std::vector<void*>& allocs, const std::vector<T>& h, const T** dst) {
     *dst = nullptr;
     if (h.empty()) return SAT_OK;
-    p->info.upload_bytes += h.size() * sizeof(T);
     void* d = nullptr;
     if (cudaMalloc(&d, h.size() * sizeof(T)) != cudaSuccess) {
         cudaGetLastError();
         return fail(SAT_ERR_OOM, "cudaMalloc failed for plan array");
     }
-    p->allocs.push_back(d);
+    allocs.push_back(d);
     CK(cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
     *dst = (const T*)d;
     return SAT_OK;
+}
+template <typename T>
+sat_status upload(sat_plan* p, const std::vector<T>& h, const T** dst) {
+    p->info.upload_bytes += h.size() * sizeof(T);
+    return upload_to(p->allocs, h, dst);
 }
 
 sat_status check_device(int device) {
@@ -247,6 +261,7 @@ void sat_circuit_free(sat_circuit* c) { delete c; }
 void sat_plan_free(sat_plan* p) {
     if (!p) return;
     for (void* a : p->allocs) cudaFree(a);
+    for (void* a : p->lay_allocs) cudaFree(a);
     delete p;
 }
 
@@ -276,14 +291,35 @@ sat_status sat_plan_create(const sat_circuit* c, const sat_cnf* cnf, sat_plan** 
     std::vector<int2> cg(P.c_in0.size()), fg(P.in0.size());
     for (size_t g = 0; g < cg.size(); g++) cg[g] = make_int2(P.c_in0[g] | ((int32_t)P.c_gop[g] << 28), P.c_in1[g]);
     for (size_t g = 0; g < fg.size(); g++) fg[g] = make_int2(P.in0[g] | ((int32_t)P.gop[g] << 28), P.in1[g]);
+    // Adjoint ring: a gate level's adjoints are read by the inputs of its gates, at most
+    // max_span levels down, so max_span + 1 slots of the largest level hold every live one.
+    {
+        int32_t M = 0;
+        for (int32_t l = 1; l <= d.n_clev; l++) M = std::max(M, P.c_level_off[l + 1] - P.c_level_off[l]);
+        const int64_t ring = (int64_t)P.n_cone_pi + (int64_t)(d.max_span + 1) * M;
+        if (d.max_span + 1 < d.n_clev && ring < (int64_t)P.n_cone) {
+            d.adj_slots = d.max_span + 1;
+            d.adj_slot_rows = M;
+            d.n_adj_rows = ring;
+        } else {
+            d.n_adj_rows = (int64_t)P.n_cone;
+        }
+    }
     std::vector<int4> fe(P.fo_g.size());
-    // edge record: consumer, sibling, and the partial's coefficients c0, c1 as float bits
-    for (size_t e = 0; e < fe.size(); e++) {
-        float c0 = (float)P.fo_c0[e], c1 = (float)P.fo_c1[e];
-        int32_t i0, i1;
-        std::memcpy(&i0, &c0, 4);
-        std::memcpy(&i1, &c1, 4);
-        fe[e] = make_int4(P.fo_g[e], P.fo_sib[e], i0, i1);
+    {
+        // edge record: consumer's adj row, sibling, and the partial's coefficients c0, c1 as float bits
+        std::vector<int32_t> adj_row(P.n_cone);
+        for (uint32_t i = 0; i < P.n_cone_pi; i++) adj_row[i] = (int32_t)i;
+        for (int32_t l = 1; l <= d.n_clev; l++)
+            for (int32_t x = P.c_level_off[l]; x < P.c_level_off[l + 1]; x++)
+                adj_row[x] = (int32_t)(sat::adj_level_row(d, l, P.c_level_off[l]) + (x - P.c_level_off[l]));
+        for (size_t e = 0; e < fe.size(); e++) {
+            float c0 = (float)P.fo_c0[e], c1 = (float)P.fo_c1[e];
+            int32_t i0, i1;
+            std::memcpy(&i0, &c0, 4);
+            std::memcpy(&i1, &c1, 4);
+            fe[e] = make_int4(P.fo_g[e] < 0 ? -1 : adj_row[P.fo_g[e]], P.fo_sib[e], i0, i1);
+        }
     }
     // bit 31 of the sibling field marks the last edge of each node's range
     for (size_t n = 0; n + 1 < P.fo_off.size(); n++)
@@ -303,6 +339,15 @@ sat_status sat_plan_create(const sat_circuit* c, const sat_cnf* cnf, sat_plan** 
     if ((st = upload(p, fg, &d.f_gate)) != SAT_OK) return bail(st);
     if ((st = upload(p, P.cl_off, &d.cl_off)) != SAT_OK) return bail(st);
     if ((st = upload(p, cl_lit, &d.cl_lit)) != SAT_OK) return bail(st);
+    d.full.k = 0;
+    d.full.n_act_rows = (int64_t)P.n_cone;
+    d.full.act_off = d.c_level_off;
+    d.full.gate = d.c_gate;
+    d.full.edge = d.fo_edge;
+    d.full.out_row = d.c_out_node;
+    p->h_gate = std::move(cg);
+    p->h_edge = std::move(fe);
+    p->h_out = P.c_out_node;
     {
         void* w = nullptr;
         if (cudaMalloc(&w, sizeof(unsigned int)) != cudaSuccess) {
@@ -380,6 +425,100 @@ sat_status sat_plan_get_info(const sat_plan* p, sat_plan_info* info) {
 sat_status sat_plan_scratch_elems(const sat_plan* p, int64_t B, uint64_t* elems) {
     if (!p || !elems || B < 0) return fail(SAT_ERR_ARG, "bad argument");
     *elems = (uint64_t)((B + SAT_TILE_SAMPLES - 1) / SAT_TILE_SAMPLES) * p->info.n_cone * SAT_TILE_SAMPLES;
+    return SAT_OK;
+}
+
+// The act layout of segment length k (0: the full layout), built and uploaded on first use.
+// Levels 1.. form segments of k levels (segment j = levels jk+1 .. jk+k).  Kept levels:
+// 0, the top max_span levels of each segment (every input of the next segment's gates is
+// among them, since no edge spans more than max_span levels) and levels with an output
+// (the loss reads them).  Kept levels get their own rows; the other levels of segment j
+// go to scratch buffer j % 2, which holds the largest segment's unkept levels.
+static sat_status plan_layout(const sat_plan* p, int32_t k, const sat::DevAct** out) {
+    *out = nullptr;
+    if (k < 0) return fail(SAT_ERR_ARG, "segment must be >= 0");
+    if (k == 0) {
+        *out = &p->dp.full;
+        return SAT_OK;
+    }
+    std::lock_guard<std::mutex> lock(p->lay_mu);
+    auto it = p->layouts.find(k);
+    if (it != p->layouts.end()) {
+        *out = &it->second;
+        return SAT_OK;
+    }
+    const sat::DevPlan& d = p->dp;
+    const std::vector<int32_t>& off = p->h_c_level_off;
+    const int32_t L = d.n_clev, W = d.max_span;
+    std::vector<int32_t> level(d.n_cone, 0);
+    for (int32_t l = 1; l <= L; l++)
+        for (int32_t x = off[l]; x < off[l + 1]; x++) level[x] = l;
+    std::vector<uint8_t> stored(L + 1, 0);
+    stored[0] = 1;
+    for (int32_t l = 1; l <= L; l++) stored[l] = (uint8_t)((l - 1) % k >= k - W);
+    for (int32_t x : p->h_out) stored[level[x]] = 1;
+    std::vector<int32_t> act_off(L + 1, 0);
+    int64_t next = d.n_cone_pi;
+    for (int32_t l = 1; l <= L; l++)
+        if (stored[l]) {
+            act_off[l] = (int32_t)next;
+            next += off[l + 1] - off[l];
+        }
+    int64_t S = 0;
+    for (int32_t l0 = 1; l0 <= L; l0 += k) {
+        int64_t seg = 0;
+        for (int32_t l = l0; l < l0 + k && l <= L; l++)
+            if (!stored[l]) seg += off[l + 1] - off[l];
+        S = std::max(S, seg);
+    }
+    for (int32_t l0 = 1, j = 0; l0 <= L; l0 += k, j++) {
+        int64_t pos = next + (j % 2) * S;
+        for (int32_t l = l0; l < l0 + k && l <= L; l++)
+            if (!stored[l]) {
+                act_off[l] = (int32_t)pos;
+                pos += off[l + 1] - off[l];
+            }
+    }
+    auto row = [&](int32_t x) { return x < d.n_cone_pi ? x : act_off[level[x]] + (x - off[level[x]]); };
+    std::vector<int2> gate(p->h_gate.size());
+    for (size_t g = 0; g < gate.size(); g++) {
+        const int2 r = p->h_gate[g];
+        gate[g] = make_int2(row(r.x & 0x0FFFFFFF) | (int32_t)((uint32_t)r.x & 0xF0000000u), row(r.y));
+    }
+    std::vector<int4> edge(p->h_edge);
+    for (int4& e : edge) e.y = row(e.y & 0x7FFFFFFF) | (int32_t)((uint32_t)e.y & 0x80000000u);
+    std::vector<int32_t> out_row(p->h_out.size());
+    for (size_t j = 0; j < out_row.size(); j++) out_row[j] = row(p->h_out[j]);
+    if (next + 2 * S >= d.n_cone) {  // no saving (segments too long or too short): keep every level
+        *out = &(p->layouts[k] = d.full);
+        return SAT_OK;
+    }
+    sat::DevAct a;
+    a.k = k;
+    a.n_act_rows = next + 2 * S;
+    sat_status st;
+    if ((st = upload_to(p->lay_allocs, act_off, &a.act_off)) != SAT_OK) return st;
+    if ((st = upload_to(p->lay_allocs, stored, &a.stored)) != SAT_OK) return st;
+    if ((st = upload_to(p->lay_allocs, gate, &a.gate)) != SAT_OK) return st;
+    if ((st = upload_to(p->lay_allocs, edge, &a.edge)) != SAT_OK) return st;
+    if ((st = upload_to(p->lay_allocs, out_row, &a.out_row)) != SAT_OK) return st;
+    *out = &(p->layouts[k] = a);
+    return SAT_OK;
+}
+
+sat_status sat_plan_layout_elems(const sat_plan* p, int32_t segment, int64_t B, uint64_t* act_elems,
+                                 uint64_t* adj_elems) {
+    if (!p || B < 0) return fail(SAT_ERR_ARG, "bad argument");
+    if (segment < 0) return fail(SAT_ERR_ARG, "segment must be >= 0");
+    const uint64_t tiles = (uint64_t)((B + SAT_TILE_SAMPLES - 1) / SAT_TILE_SAMPLES);
+    if (act_elems) {
+        sat_status st = segment > 0 ? check_device(p->device) : SAT_OK;
+        if (st != SAT_OK) return st;
+        const sat::DevAct* lay = nullptr;
+        if ((st = plan_layout(p, segment, &lay)) != SAT_OK) return st;
+        *act_elems = tiles * (uint64_t)lay->n_act_rows * SAT_TILE_SAMPLES;
+    }
+    if (adj_elems) *adj_elems = tiles * (uint64_t)p->dp.n_adj_rows * SAT_TILE_SAMPLES;
     return SAT_OK;
 }
 
@@ -497,7 +636,8 @@ sat_status sat_steps(const sat_plan* p, sat_act_dtype t, const sat_opt_params* o
                   (p->dp.n_cone > 0 && (!act || !adj))))
         return fail(SAT_ERR_ARG, "NULL buffer");
     if ((((uintptr_t)act | (uintptr_t)adj) & 15) != 0) return fail(SAT_ERR_ARG, "act/adj must be 16-byte aligned");
-    CK(sat::launch_steps(p->dp, (int)t, opt_of(o), V, m, v, ldv, act, adj, loss, t0, n_steps, B, S(stream)));
+    CK(sat::launch_steps(p->dp, p->dp.full, (int)t, opt_of(o), V, m, v, ldv, act, adj, loss, t0, n_steps, B,
+                         S(stream)));
     return SAT_OK;
 }
 
@@ -512,7 +652,27 @@ sat_status sat_steps_aged(const sat_plan* p, sat_act_dtype t, const sat_opt_para
                   (p->dp.n_cone > 0 && (!act || !adj))))
         return fail(SAT_ERR_ARG, "NULL buffer");
     if ((((uintptr_t)act | (uintptr_t)adj) & 15) != 0) return fail(SAT_ERR_ARG, "act/adj must be 16-byte aligned");
-    CK(sat::launch_steps(p->dp, (int)t, opt_of(o), V, m, v, ldv, act, adj, loss, t0, n_steps, B, S(stream), age));
+    CK(sat::launch_steps(p->dp, p->dp.full, (int)t, opt_of(o), V, m, v, ldv, act, adj, loss, t0, n_steps, B,
+                         S(stream), age));
+    return SAT_OK;
+}
+
+sat_status sat_steps_recompute(const sat_plan* p, sat_act_dtype t, const sat_opt_params* o, float* V, float* m,
+                               float* v, int64_t ldv, void* act, float* adj, float* loss, const int32_t* age,
+                               int32_t t0, int32_t n_steps, int64_t B, int32_t segment, void* stream) {
+    sat_status s = check_layout(p, B, ldv);
+    if (s != SAT_OK) return s;
+    if (t < SAT_ACT_F32 || t > SAT_ACT_F16) return fail(SAT_ERR_ARG, "bad act_dtype");
+    if (!opt_ok(o) || t0 < 1 || n_steps < 0) return fail(SAT_ERR_ARG, "bad optimiser parameters or steps");
+    if (segment < 0) return fail(SAT_ERR_ARG, "segment must be >= 0");
+    if (B > 0 && ((p->dp.n_pi > 0 && (!V || (o->optimizer == SAT_OPT_ADAM && (!m || !v)))) ||
+                  (p->dp.n_cone > 0 && (!act || !adj))))
+        return fail(SAT_ERR_ARG, "NULL buffer");
+    if ((((uintptr_t)act | (uintptr_t)adj) & 15) != 0) return fail(SAT_ERR_ARG, "act/adj must be 16-byte aligned");
+    const sat::DevAct* lay = nullptr;
+    if ((s = plan_layout(p, segment, &lay)) != SAT_OK) return s;
+    CK(sat::launch_steps(p->dp, *lay, (int)t, opt_of(o), V, m, v, ldv, act, adj, loss, t0, n_steps, B, S(stream),
+                         age));
     return SAT_OK;
 }
 
@@ -682,6 +842,7 @@ void sat_sample_opts_default(sat_sample_opts* o) {
     o->proposal_tau = 1.0f;
     o->check_every = 0;
     o->max_age = 0;
+    o->recompute_segment = 0;
 }
 
 namespace {
@@ -692,6 +853,7 @@ struct Workspace {
     void* act = nullptr;
     uint32_t *bits = nullptr, *keys = nullptr, *valid = nullptr;
     int64_t ldw = 0;
+    const sat::DevAct* lay = nullptr;  // act layout of the fused steps
     ~Workspace() {
         for (void* b : bufs) cudaFree(b);
     }
@@ -708,8 +870,8 @@ struct Workspace {
 
 size_t act_bytes(int t) { return t == SAT_ACT_F32 ? 4 : 2; }
 
-size_t scratch_elems(const sat::DevPlan& dp, int64_t B) {
-    return (size_t)((B + SAT_TILE_SAMPLES - 1) / SAT_TILE_SAMPLES) * (size_t)dp.n_cone * SAT_TILE_SAMPLES;
+size_t scratch_elems(int64_t rows, int64_t B) {
+    return (size_t)((B + SAT_TILE_SAMPLES - 1) / SAT_TILE_SAMPLES) * (size_t)rows * SAT_TILE_SAMPLES;
 }
 
 }  // namespace
@@ -770,7 +932,7 @@ static sat_status sample_early_exit(const sat_plan* p, sat_dedup* d, const sat_s
         const int kk = (int)std::min<int64_t>(k, budget - done);
         CK(cudaEventRecord(ev[0], str));
         for (int t0 = 1; t0 <= kk; t0 += spl)
-            CK(sat::launch_steps(dp, o->act_dtype, op, w.V, w.m, w.v, B, w.act, w.adj, nullptr, t0,
+            CK(sat::launch_steps(dp, *w.lay, o->act_dtype, op, w.V, w.m, w.v, B, w.act, w.adj, nullptr, t0,
                                  std::min(spl, kk - t0 + 1), B, str, age));
         CK(cudaEventRecord(ev[1], str));
         CK(sat::launch_threshold(dp, w.V, B, w.bits, w.ldw, w.keys, B, str));
@@ -830,16 +992,19 @@ sat_status sat_sample_plan(const sat_plan* p, sat_dedup* d, const sat_sample_opt
     if (o->check_every < 0 || o->max_age < 0) return fail(SAT_ERR_ARG, "bad check_every / max_age");
     if (o->act_dtype < SAT_ACT_F32 || o->act_dtype > SAT_ACT_F16) return fail(SAT_ERR_ARG, "bad act_dtype");
     if (o->init_logits && o->init_ld < B) return fail(SAT_ERR_ARG, "init_ld < batch");
+    if (o->recompute_segment < 0) return fail(SAT_ERR_ARG, "recompute_segment must be >= 0");
     sat_status s = check_device(p->device);
     if (s != SAT_OK) return s;
     cudaStream_t str = S(o->stream);
     const sat::DevPlan& dp = p->dp;
     Workspace w;
+    if ((s = plan_layout(p, o->recompute_segment, &w.lay)) != SAT_OK) return s;
     w.ldw = (B + 31) / 32;
     const size_t npi = (size_t)dp.n_pi;
     if (!w.alloc((void**)&w.V, npi * B * 4) || !w.alloc((void**)&w.m, npi * B * 4) ||
-        !w.alloc((void**)&w.v, npi * B * 4) || !w.alloc(&w.act, scratch_elems(dp, B) * act_bytes(o->act_dtype)) ||
-        !w.alloc((void**)&w.adj, scratch_elems(dp, B) * 4) ||
+        !w.alloc((void**)&w.v, npi * B * 4) ||
+        !w.alloc(&w.act, scratch_elems(w.lay->n_act_rows, B) * act_bytes(o->act_dtype)) ||
+        !w.alloc((void**)&w.adj, scratch_elems(dp.n_adj_rows, B) * 4) ||
         !w.alloc((void**)&w.bits, (size_t)dp.n_nodes * w.ldw * 4) ||
         !w.alloc((void**)&w.keys, (size_t)B * std::max(1, dp.key_words) * 4) ||
         !w.alloc((void**)&w.valid, (size_t)w.ldw * 4))
@@ -872,7 +1037,7 @@ sat_status sat_sample_plan(const sat_plan* p, sat_dedup* d, const sat_sample_opt
         CK(cudaMemsetAsync(w.v, 0, npi * B * 4, str));
         CK(cudaEventRecord(ev[1], str));
         for (int t0 = 1; t0 <= o->steps; t0 += spl)
-            CK(sat::launch_steps(dp, o->act_dtype, op, w.V, w.m, w.v, B, w.act, w.adj, nullptr, t0,
+            CK(sat::launch_steps(dp, *w.lay, o->act_dtype, op, w.V, w.m, w.v, B, w.act, w.adj, nullptr, t0,
                                  std::min(spl, o->steps - t0 + 1), B, str));
         CK(cudaEventRecord(ev[2], str));
         CK(sat::launch_threshold(dp, w.V, B, w.bits, w.ldw, w.keys, B, str));

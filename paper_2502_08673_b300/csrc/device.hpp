@@ -7,6 +7,22 @@
 
 namespace sat {
 
+// Activation layout of a tile's act scratch.  k = 0: every cone node has its own row
+// (row = node).  k > 0 (level-segment recomputation): levels 1.. are cut into segments
+// of k levels; a level is kept ("stored") when it is among the top max_span levels of
+// its segment (the inputs the next segment's gates read) or holds an output; the other
+// levels of segment j share scratch buffer j % 2 and are evaluated again in the
+// backward pass.  Level 0 is always kept.
+struct DevAct {
+    int32_t k = 0;
+    int64_t n_act_rows = 0;            // rows of one tile's act scratch
+    const int32_t* act_off = nullptr;  // [n_clev + 1]: act row of the first node of level l
+    const uint8_t* stored = nullptr;   // [n_clev + 1]: 1 = kept level (k > 0 only)
+    const int2* gate = nullptr;        // per cone gate: (act row of in0 | gop << 28, act row of in1)
+    const int4* edge = nullptr;        // fan-out edges with the sibling's act row
+    const int32_t* out_row = nullptr;  // act rows of the outputs
+};
+
 // Device copy of a Plan.  All pointers are device pointers owned by the plan.
 struct DevPlan {
     // cone schedule (gradient loop)
@@ -18,7 +34,13 @@ struct DevPlan {
     const int2* c_gate = nullptr;       // per cone gate: (in0 | gop << 28, in1)
     const int32_t* cone_pi_row = nullptr;
     const int32_t* fo_off = nullptr;    // [n_cone + 1]
-    const int4* fo_edge = nullptr;      // (consumer or -1, sibling | last-edge-of-node << 31, c0 bits, c1 bits)
+    const int4* fo_edge = nullptr;      // (consumer's adj row or -1, sibling | last-edge-of-node << 31, c0 bits, c1 bits)
+    // Adjoint scratch rows of a tile: level 0 (the cone inputs) in rows [0, n_cone_pi); a
+    // gate level l is live only until the backward pass has finished level l - max_span, so
+    // with adj_slots > 0 level l >= 1 occupies slot (l - 1) % adj_slots of a ring of
+    // adj_slots = max_span + 1 slots of adj_slot_rows rows each (adj_slots = 0: row = node).
+    int64_t n_adj_rows = 0;
+    int32_t adj_slots = 0, adj_slot_rows = 0;
     int32_t n_out = 0;
     const int32_t* c_out_node = nullptr;
     const float* out_target = nullptr;
@@ -34,10 +56,17 @@ struct DevPlan {
     const int32_t* cl_lit = nullptr;    // node << 1 | negation
     int32_t key_words = 0;              // ceil(n_pi / 32)
     unsigned int* status = nullptr;     // device status word (bit 2: an async-copy wait expired)
+    DevAct full;                        // the full act layout (row = node)
     // host mirrors of the level offsets (launch loops need them)
     const int32_t* h_c_level_off = nullptr;
     const int32_t* h_f_level_off = nullptr;
 };
+
+// Adjoint row of the first node of level l >= 1.
+inline __host__ __device__ int64_t adj_level_row(const DevPlan& p, int l, int32_t level_off) {
+    return p.adj_slots ? (int64_t)p.n_cone_pi + (int64_t)((l - 1) % p.adj_slots) * p.adj_slot_rows
+                       : (int64_t)level_off;
+}
 
 enum ActType { ACT_F32 = 0, ACT_BF16 = 1, ACT_F16 = 2 };
 
@@ -50,14 +79,16 @@ struct OptParams {
 cudaError_t launch_init_normal(const DevPlan& p, uint64_t seed, uint32_t round, float scale,
                                float* V, int64_t ldv, int64_t B, cudaStream_t s);
 // act / adj scratch is tile-major: tile t (samples 128t .. 128t+127) owns rows
-// [n_cone][128] starting at element t * n_cone * 128 (SAT_TILE = 128).
+// [n_act_rows][128] of act starting at element t * n_act_rows * 128 (SAT_TILE = 128),
+// and [n_adj_rows][128] of adj likewise.  forward / backward use the full act layout.
 cudaError_t launch_forward(const DevPlan& p, int act_type, const float* V, int64_t ldv, void* act, float* loss,
                            int64_t B, cudaStream_t s);
 cudaError_t launch_backward(const DevPlan& p, int act_type, const float* V, int64_t ldv, const void* act, float* adj,
                             const float* grad_loss, float* gV, int64_t B, cudaStream_t s);
 // Adam step of sample b at in-launch step s: t0 + s, plus age[b] when age is given.
-cudaError_t launch_steps(const DevPlan& p, int act_type, const OptParams& o, float* V, float* m, float* v,
-                         int64_t ldv, void* act, float* adj, float* loss, int t0, int n_steps, int64_t B,
+// lay: the act layout (the full one, or a recomputation layout of the plan).
+cudaError_t launch_steps(const DevPlan& p, const DevAct& lay, int act_type, const OptParams& o, float* V, float* m,
+                         float* v, int64_t ldv, void* act, float* adj, float* loss, int t0, int n_steps, int64_t B,
                          cudaStream_t s, const int32_t* age = nullptr);
 // Early exit: restart[b] = valid(b) or age[b] + k >= max_age (bit-packed like valid);
 // age[b] = 0 where restarting, else age[b] + k.

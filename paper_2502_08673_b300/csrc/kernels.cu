@@ -281,11 +281,12 @@ __device__ __forceinline__ void gather4_hint(void* dst, const CUtensorMap* map, 
         : "memory");
 }
 
-// Tensor maps over the scratch rows of all tiles (row = tile * n_cone + node).
+// Tensor maps over the scratch rows of all tiles (act row = tile * n_act_rows + row in
+// the tile, adj likewise with n_adj_rows).
 struct RowMaps {
     const CUtensorMap* act;
     const CUtensorMap* adj;
-    int row0;  // this tile's first row
+    int arow0, grow0;  // this tile's first act / adj row
 };
 
 // Adjoint rows are re-read by the next few levels (as consumer adjoints): stored with
@@ -365,17 +366,10 @@ __device__ __forceinline__ void stage_wait(Stage& st, int s) {
     __syncwarp();
 }
 
-// Forward pass of one tile: P = sigmoid(V) for the cone inputs, then every cone
-// level.  Within a level each warp takes a contiguous run of gates; 32 gate
-// records come in one coalesced load and are broadcast by shuffles; the two
-// input rows of each gate are gathered into shared memory (two gather4 loads
-// per CHUNK = 4 gates), NSLOT-1 chunks ahead of the computation.  gcoef: the 16 bilinear
-// coefficient sets in shared memory.
+// Forward pass of one tile, input level: P = sigmoid(V) for the cone inputs (rows
+// 0 .. n_cone_pi - 1 in every layout).
 template <typename T>
-__device__ void tile_forward(const DevPlan& p, const float* __restrict__ V, int64_t ldv, T* act, Stage& st,
-                             const float4* gcoef, const RowMaps& rm, const TileCtx& c) {
-    constexpr int ROWB = TILE * (int)sizeof(T);
-    constexpr int SLOT = slot_bytes<T>();
+__device__ void tile_inputs(const DevPlan& p, const float* __restrict__ V, int64_t ldv, T* act, const TileCtx& c) {
     for (int i0 = c.vw * UBATCH; i0 < p.n_cone_pi; i0 += c.nvw * UBATCH) {
         VF x[UBATCH];
 #pragma unroll
@@ -402,33 +396,55 @@ __device__ void tile_forward(const DevPlan& p, const float* __restrict__ V, int6
     }
     fence_async_global();
     level_sync(c);
-    // This warp's gate run of level l and its first 32 gate records; those of the
-    // next level are loaded before the level barrier, so that their latency
-    // overlaps the wait for the other warps.
-    auto level_run = [&](int l, int& g0, int& g1, int2& first) {
+}
+
+// Forward pass over cone levels l_lo .. l_hi (all of them, or with scratch_only the
+// levels the layout does not keep: the re-evaluation of a segment).  Within a level each
+// warp takes a contiguous run of gates; 32 gate records come in one coalesced load and
+// are broadcast by shuffles; the two input rows of each gate are gathered into shared
+// memory (two gather4 loads per CHUNK = 4 gates), NSLOT-1 chunks ahead of the
+// computation.  gcoef: the 16 bilinear coefficient sets in shared memory.
+template <typename T>
+__device__ void forward_levels(const DevPlan& p, const DevAct& L, T* act, Stage& st, const float4* gcoef,
+                               const RowMaps& rm, const TileCtx& c, int l_lo, int l_hi, bool scratch_only) {
+    constexpr int ROWB = TILE * (int)sizeof(T);
+    constexpr int SLOT = slot_bytes<T>();
+    auto wanted = [&](int l) { return !scratch_only || __ldg(&L.stored[l]) == 0; };
+    auto next_level = [&](int l) {
+        do l++;
+        while (l <= l_hi && !wanted(l));
+        return l;
+    };
+    // This warp's gate run of level l, its first 32 gate records and the act row of the
+    // level's first gate; those of the next level are loaded before the level barrier, so
+    // that their latency overlaps the wait for the other warps.
+    auto level_run = [&](int l, int& g0, int& g1, int& orow, int2& first) {
         const int lo = __ldg(&p.c_level_off[l]), hi = __ldg(&p.c_level_off[l + 1]);
         const int per = (hi - lo + c.nvw - 1) / c.nvw;
         g0 = lo + c.vw * per;
         g1 = min(g0 + per, hi);
+        orow = __ldg(&L.act_off[l]) - lo;
         first = make_int2(0, 0);
-        if (c.lane < g1 - g0) first = __ldg(&p.c_gate[g0 + c.lane - p.n_cone_pi]);
+        if (c.lane < g1 - g0) first = __ldg(&L.gate[g0 + c.lane - p.n_cone_pi]);
     };
-    int g0 = 0, g1 = 0;
+    int g0 = 0, g1 = 0, orow = 0;
     int2 first = make_int2(0, 0);
-    if (p.n_clev >= 1) level_run(1, g0, g1, first);
-    for (int l = 1; l <= p.n_clev; l++) {
+    int l = l_lo;
+    if (l <= l_hi && !wanted(l)) l = next_level(l);
+    if (l <= l_hi) level_run(l, g0, g1, orow, first);
+    while (l <= l_hi) {
         for (int base = g0; base < g1; base += 32) {
             const int cnt = min(32, g1 - base);
             int2 mine = first;
             if (base != g0) {
                 mine = make_int2(0, 0);
-                if (c.lane < cnt) mine = __ldg(&p.c_gate[base + c.lane - p.n_cone_pi]);
+                if (c.lane < cnt) mine = __ldg(&L.gate[base + c.lane - p.n_cone_pi]);
             }
             const int nch = (cnt + CHUNK - 1) / CHUNK;
             // per lane (= gate of the batch): tensor-map rows of both inputs and the gate code
-            const int x_row = rm.row0 + (mine.x & 0x0FFFFFFF), y_row = rm.row0 + mine.y;
+            const int x_row = rm.arow0 + (mine.x & 0x0FFFFFFF), y_row = rm.arow0 + mine.y;
             const int gop_mine = (int)((uint32_t)mine.x >> 28);
-            T* out = act + at(base, c);
+            T* out = act + at(base + orow, c);
             auto issue = [&](int ch) {
                 const int s = ch % NSLOT;
                 // first inputs of the chunk's 4 gates -> rows 0..3, second inputs -> rows 4..7
@@ -471,19 +487,27 @@ __device__ void tile_forward(const DevPlan& p, const float* __restrict__ V, int6
                 __syncwarp();
             }
         }
-        if (l < p.n_clev) level_run(l + 1, g0, g1, first);
+        l = next_level(l);
+        if (l <= l_hi) level_run(l, g0, g1, orow, first);
         fence_async_global();
         level_sync(c);
     }
 }
 
+template <typename T>
+__device__ void tile_forward(const DevPlan& p, const DevAct& L, const float* __restrict__ V, int64_t ldv, T* act,
+                             Stage& st, const float4* gcoef, const RowMaps& rm, const TileCtx& c) {
+    tile_inputs<T>(p, V, ldv, act, c);
+    forward_levels<T>(p, L, act, st, gcoef, rm, c, 1, p.n_clev, false);
+}
+
 // Per-sample loss sum_j (Y_j - T_j)^2, FP32, fixed order (warp-strided partials, then warp order).
 template <typename T>
-__device__ void tile_loss(const DevPlan& p, const T* act, float* loss, const TileCtx& c) {
+__device__ void tile_loss(const DevPlan& p, const DevAct& L, const T* act, float* loss, const TileCtx& c) {
     __shared__ VF part[step_threads<T>() / 32][32];
     VF acc = vf_fill(0.0f);
     for (int j = c.warp; j < p.n_out; j += c.nw) {
-        const VF y = ActIO<T>::ldcg(act + at(p.c_out_node[j], c));
+        const VF y = ActIO<T>::ldcg(act + at(__ldg(&L.out_row[j]), c));
         const float t = p.out_target[j];
 #pragma unroll
         for (int q = 0; q < VEC; q++) acc.v[q] = fmaf(y.v[q] - t, y.v[q] - t, acc.v[q]);
@@ -513,29 +537,31 @@ __device__ void tile_loss(const DevPlan& p, const T* act, float* loss, const Til
 // the level above) so that the three dependent loads do not stall the level.
 struct AdjRun {
     int u0, u1, off;
+    int arow;  // adj row of node u0
     int4 first;
 };
-__device__ __forceinline__ AdjRun adj_run(const DevPlan& p, int l, const TileCtx& c) {
+__device__ __forceinline__ AdjRun adj_run(const DevPlan& p, const DevAct& L, int l, const TileCtx& c) {
     const int lo = l == 0 ? 0 : __ldg(&p.c_level_off[l]);
     const int hi = l == 0 ? p.n_cone_pi : __ldg(&p.c_level_off[l + 1]);
     const int per = (hi - lo + c.nvw - 1) / c.nvw;
     AdjRun r;
     r.u0 = lo + c.vw * per;
     r.u1 = min(r.u0 + per, hi);
+    r.arow = (int)((l == 0 ? (int64_t)lo : adj_level_row(p, l, lo)) + (r.u0 - lo));
     r.off = 0;
     r.first = make_int4(-1, 0, 0, 0);
     if (r.u0 < r.u1) {
         const int nn = min(31, r.u1 - r.u0);
         r.off = (c.lane <= nn) ? __ldg(&p.fo_off[r.u0 + c.lane]) : 0;
         const int e_begin = __shfl_sync(FULL, r.off, 0), e_end = __shfl_sync(FULL, r.off, nn);
-        if (c.lane < min(32, e_end - e_begin)) r.first = __ldg(&p.fo_edge[e_begin + c.lane]);
+        if (c.lane < min(32, e_end - e_begin)) r.first = __ldg(&L.edge[e_begin + c.lane]);
     }
     return r;
 }
 
 template <typename T>
-__device__ void level_adjoint(const DevPlan& p, const AdjRun& run, const T* act, float* adj, const VF& seed_scale,
-                              Stage& st, const RowMaps& rm, const TileCtx& c) {
+__device__ void level_adjoint(const DevPlan& p, const DevAct& L, const AdjRun& run, const T* act, float* adj,
+                              const VF& seed_scale, Stage& st, const RowMaps& rm, const TileCtx& c) {
     constexpr int ROWB = TILE * (int)sizeof(T);
     constexpr int ROWF = TILE * 4;
     constexpr int SLOT = slot_bytes<T>();
@@ -547,19 +573,19 @@ __device__ void level_adjoint(const DevPlan& p, const AdjRun& run, const T* act,
         const int off = ua == u0 ? run.off : ((c.lane <= nn) ? __ldg(&p.fo_off[ua + c.lane]) : 0);
         const int e_begin = __shfl_sync(FULL, off, 0), e_end = __shfl_sync(FULL, off, nn);
         int k = 0;                         // nodes of this run stored so far
-        float* node_row = adj + at(ua, c);  // where the next node's adjoint goes
+        float* node_row = adj + at(run.arow + (ua - u0), c);  // where the next node's adjoint goes
         VF acc = vf_fill(0.0f);
         for (int base = e_begin; base < e_end; base += 32) {
             const int cnt = min(32, e_end - base);
             int4 mine = run.first;
             if (ua != u0 || base != e_begin) {
                 mine = make_int4(-1, 0, 0, 0);
-                if (c.lane < cnt) mine = __ldg(&p.fo_edge[base + c.lane]);
+                if (c.lane < cnt) mine = __ldg(&L.edge[base + c.lane]);
             }
             const int nch = (cnt + CHUNK - 1) / CHUNK;
             // per lane (= edge of the batch): tensor-map rows of the consumer adjoint (an
             // output seed, which has none, loads a stand-in row) and of the sibling
-            const int g_row = rm.row0 + max(mine.x, 0), s_row = rm.row0 + (mine.y & 0x7FFFFFFF);
+            const int g_row = rm.grow0 + max(mine.x, 0), s_row = rm.arow0 + (mine.y & 0x7FFFFFFF);
             // edges that close their node's sum (the node's adjoint row is stored there)
             const unsigned last_mask = __ballot_sync(FULL, c.lane < cnt && mine.y < 0);
             auto issue = [&](int ch) {
@@ -645,33 +671,55 @@ __device__ __forceinline__ void input_update(const OptParams& o, float* V, float
 __device__ __forceinline__ void discard_adj_rows(const DevPlan& p, int l, const float* adj, const TileCtx& c) {
     const int lo = l == 0 ? 0 : __ldg(&p.c_level_off[l]);
     const int hi = l == 0 ? p.n_cone_pi : __ldg(&p.c_level_off[l + 1]);
+    const int64_t row = l == 0 ? 0 : adj_level_row(p, l, lo);
     const char* b = reinterpret_cast<const char*>(adj);
     constexpr int LINES_PER_ROW = TILE * 4 / 128;
     const int n = (hi - lo) * LINES_PER_ROW;
     const int stride = (c.split ? 2 : 1) * (int)blockDim.x;
     for (int i = c.rank * (int)blockDim.x + (int)threadIdx.x; i < n; i += stride)
-        discard_l2_line(b + (size_t)lo * TILE * 4 + (size_t)i * 128);
+        discard_l2_line(b + (size_t)row * TILE * 4 + (size_t)i * 128);
 }
 
-// Backward pass of one tile over levels n_clev..0.  The input level's adjoints
-// (of P) are turned into dL/dV and either stored (gV) or applied by the
-// optimiser, UBATCH rows at a time.
+// Discard the whole adjoint scratch of this tile (after the input level has been read).
+__device__ __forceinline__ void discard_adj_all(const DevPlan& p, const float* adj, const TileCtx& c) {
+    const char* b = reinterpret_cast<const char*>(adj);
+    constexpr int LINES_PER_ROW = TILE * 4 / 128;
+    const int64_t n = p.n_adj_rows * LINES_PER_ROW;
+    const int stride = (c.split ? 2 : 1) * (int)blockDim.x;
+    for (int64_t i = c.rank * (int)blockDim.x + (int)threadIdx.x; i < n; i += stride)
+        discard_l2_line(b + (size_t)i * 128);
+}
+
+// Backward pass of one tile over levels n_clev..0.  Under a recomputation layout
+// (L.k > 0) each segment's unkept levels are evaluated again, from the kept levels
+// below it, before its adjoints; the forward pass leaves the top two segments'
+// scratch valid (buffers J % 2 and (J - 1) % 2), so those are not re-evaluated.  The
+// input level's adjoints (of P) are turned into dL/dV and either stored (gV) or
+// applied by the optimiser, UBATCH rows at a time.
 template <typename T, bool UPDATE>
-__device__ void tile_backward(const DevPlan& p, const OptParams& o, float* V, float* m, float* v, float* gV,
-                              int64_t ldv, const T* act, float* adj, const float* grad_loss, const AdamCorr& ac,
-                              Stage& st, const RowMaps& rm, const TileCtx& c) {
+__device__ void tile_backward(const DevPlan& p, const DevAct& L, const OptParams& o, float* V, float* m, float* v,
+                              float* gV, int64_t ldv, T* act, float* adj, const float* grad_loss,
+                              const AdamCorr& ac, Stage& st, const float4* gcoef, const RowMaps& rm,
+                              const TileCtx& c) {
     VF seed_scale = vf_fill(1.0f);
     if (grad_loss != nullptr)
 #pragma unroll
         for (int q = 0; q < VEC; q++) seed_scale.v[q] = q < c.nvalid ? grad_loss[c.b + q] : 0.0f;
-    AdjRun run = adj_run(p, p.n_clev, c);
+    const int top_seg = L.k > 0 && p.n_clev > 0 ? (p.n_clev - 1) / L.k : 0;
+    AdjRun run = adj_run(p, L, p.n_clev, c);
     for (int l = p.n_clev; l >= 0; l--) {
-        level_adjoint<T>(p, run, act, adj, seed_scale, st, rm, c);
-        if (l > 0) run = adj_run(p, l - 1, c);
+        if (L.k > 0 && l >= 1 && (l % L.k == 0 || l == p.n_clev)) {  // l: the top level of its segment
+            const int j = (l - 1) / L.k;
+            if (j + 2 <= top_seg) forward_levels<T>(p, L, act, st, gcoef, rm, c, j * L.k + 1, l, true);
+        }
+        level_adjoint<T>(p, L, run, act, adj, seed_scale, st, rm, c);
+        if (l > 0) run = adj_run(p, L, l - 1, c);
         fence_async_global();
         level_sync(c);
-        // Adjoint rows of level l + span have no reader below level l.
-        if (l + p.max_span <= p.n_clev) discard_adj_rows(p, l + p.max_span, adj, c);
+        // Adjoint rows of level l + span have no reader below level l.  (In the ring, their
+        // slot is level l - 1's, written right after this barrier: a discard there would
+        // race with those stores, so ring slots are only discarded at the end.)
+        if (p.adj_slots == 0 && l + p.max_span <= p.n_clev) discard_adj_rows(p, l + p.max_span, adj, c);
     }
     const bool adam = UPDATE && o.opt == 0;
     for (int i0 = c.vw * UBATCH; i0 < p.n_cone_pi; i0 += c.nvw * UBATCH) {
@@ -708,10 +756,14 @@ __device__ void tile_backward(const DevPlan& p, const OptParams& o, float* V, fl
         }
     }
     level_sync(c);
-    for (int l = 0; l < p.max_span && l <= p.n_clev; l++) discard_adj_rows(p, l, adj, c);
+    if (p.adj_slots == 0)
+        for (int l = 0; l < p.max_span && l <= p.n_clev; l++) discard_adj_rows(p, l, adj, c);
+    else
+        discard_adj_all(p, adj, c);
 }
 
-// Scratch of tile t: act / adj rows [n_cone][TILE] starting at element t * n_cone * TILE.
+// Scratch of tile t: act rows [n_act_rows][TILE] from element t * n_act_rows * TILE, adj
+// rows [n_adj_rows][TILE] from element t * n_adj_rows * TILE.
 // Dynamic shared memory: warp_stage_bytes<T>() per warp (slots + mbarriers).
 template <typename T>
 __device__ __forceinline__ Stage init_stage(char* smem, const DevPlan& p, float4* gcoef, const TileCtx& c) {
@@ -732,10 +784,10 @@ __global__ void __launch_bounds__(step_threads<T>(), 1) forward_kernel(DevPlan p
     __shared__ float4 gcoef[16];
     const TileCtx c = tile_ctx(B);
     Stage st = init_stage<T>(smem, p, gcoef, c);
-    T* a = act + (size_t)c.tile * (size_t)p.n_cone * TILE;
-    const RowMaps rm{&amap, &amap, (int)(c.tile * (int64_t)p.n_cone)};
-    tile_forward<T>(p, V, ldv, a, st, gcoef, rm, c);
-    if (loss) tile_loss<T>(p, a, loss, c);
+    T* a = act + (size_t)c.tile * (size_t)p.full.n_act_rows * TILE;
+    const RowMaps rm{&amap, &amap, (int)(c.tile * p.full.n_act_rows), 0};
+    tile_forward<T>(p, p.full, V, ldv, a, st, gcoef, rm, c);
+    if (loss) tile_loss<T>(p, p.full, a, loss, c);
 }
 
 template <typename T>
@@ -748,22 +800,22 @@ __global__ void __launch_bounds__(step_threads<T>(), 1) backward_kernel(DevPlan 
     __shared__ float4 gcoef[16];
     const TileCtx c = tile_ctx(B);
     Stage st = init_stage<T>(smem, p, gcoef, c);
-    const size_t off = (size_t)c.tile * (size_t)p.n_cone * TILE;
     OptParams o;
     AdamCorr ac;
 #pragma unroll
     for (int q = 0; q < VEC; q++) ac.step[q] = ac.bc2s[q] = 1.0f;
-    const RowMaps rm{&amap, &gmap, (int)(c.tile * (int64_t)p.n_cone)};
-    tile_backward<T, false>(p, o, const_cast<float*>(V), nullptr, nullptr, gV, ldv, act + off, adj + off, grad_loss,
-                            ac, st, rm, c);
+    const RowMaps rm{&amap, &gmap, (int)(c.tile * p.full.n_act_rows), (int)(c.tile * p.n_adj_rows)};
+    tile_backward<T, false>(p, p.full, o, const_cast<float*>(V), nullptr, nullptr, gV, ldv,
+                            const_cast<T*>(act) + (size_t)c.tile * (size_t)p.full.n_act_rows * TILE,
+                            adj + (size_t)c.tile * (size_t)p.n_adj_rows * TILE, grad_loss, ac, st, gcoef, rm, c);
 }
 
 // The fused hot loop: n_steps x (forward, loss, adjoint, update) for one tile,
 // at Adam steps t0 + s (+ age[b] per sample when age is given).
 // SPLIT: launched in clusters of two CTAs per tile (tiles tile0, tile0 + 1, ...).
 template <typename T, bool SPLIT>
-__global__ void __launch_bounds__(step_threads<T>(), 1) steps_kernel(DevPlan p, OptParams o, float* V, float* m, float* v,
-                                                                int64_t ldv, T* act, float* adj, float* loss,
+__global__ void __launch_bounds__(step_threads<T>(), 1) steps_kernel(DevPlan p, DevAct L, OptParams o, float* V, float* m,
+                                                                float* v, int64_t ldv, T* act, float* adj, float* loss,
                                                                 int t0, const int32_t* age, int n_steps, int64_t B,
                                                                 int tile0, const __grid_constant__ CUtensorMap amap,
                                                                 const __grid_constant__ CUtensorMap gmap) {
@@ -771,17 +823,16 @@ __global__ void __launch_bounds__(step_threads<T>(), 1) steps_kernel(DevPlan p, 
     __shared__ float4 gcoef[16];
     const TileCtx c = tile_ctx(B, tile0, SPLIT);
     Stage st = init_stage<T>(smem, p, gcoef, c);
-    const size_t off = (size_t)c.tile * (size_t)p.n_cone * TILE;
-    T* a = act + off;
-    float* g = adj + off;
-    const RowMaps rm{&amap, &gmap, (int)(c.tile * (int64_t)p.n_cone)};
+    T* a = act + (size_t)c.tile * (size_t)L.n_act_rows * TILE;
+    float* g = adj + (size_t)c.tile * (size_t)p.n_adj_rows * TILE;
+    const RowMaps rm{&amap, &gmap, (int)(c.tile * L.n_act_rows), (int)(c.tile * p.n_adj_rows)};
 #pragma unroll 1
     for (int s = 0; s < n_steps; s++) {
         AdamCorr ac;
         if (o.opt == 0) ac = adam_corr(o, age, t0 + s, c);
-        tile_forward<T>(p, V, ldv, a, st, gcoef, rm, c);
-        if (loss && s == n_steps - 1 && c.rank == 0) tile_loss<T>(p, a, loss, c);
-        tile_backward<T, true>(p, o, V, m, v, nullptr, ldv, a, g, nullptr, ac, st, rm, c);
+        tile_forward<T>(p, L, V, ldv, a, st, gcoef, rm, c);
+        if (loss && s == n_steps - 1 && c.rank == 0) tile_loss<T>(p, L, a, loss, c);
+        tile_backward<T, true>(p, L, o, V, m, v, nullptr, ldv, a, g, nullptr, ac, st, gcoef, rm, c);
     }
 }
 
@@ -1072,21 +1123,21 @@ constexpr CUtensorMapDataType tmap_type() {
                                                             : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
 }
 
-// Maps over the act (type T) and adj (fp32) scratch of `tiles` tiles: one row per
-// (tile, cone node), TILE elements wide, box = one row (for tile::gather4).
+// Maps over the act (type T, layout L) and adj (fp32) scratch of `tiles` tiles: one row
+// per (tile, scratch row), TILE elements wide, box = one row (for tile::gather4).
 // With an empty cone the maps stay zero and unused.
 template <typename T>
-cudaError_t row_maps(const DevPlan& p, const void* act, const float* adj, unsigned tiles, CUtensorMap* amap,
-                     CUtensorMap* gmap) {
+cudaError_t row_maps(const DevPlan& p, const DevAct& L, const void* act, const float* adj, unsigned tiles,
+                     CUtensorMap* amap, CUtensorMap* gmap) {
     memset(amap, 0, sizeof(*amap));
     memset(gmap, 0, sizeof(*gmap));
     if (p.n_cone == 0 || tiles == 0) return cudaSuccess;
-    const int64_t rows = (int64_t)tiles * p.n_cone;
-    if (rows > 0x7fffffff) return cudaErrorInvalidValue;  // row coordinates are int32
-    if (act && !encode_2d(amap, act, tmap_type<T>(), (int)sizeof(T), rows, TILE, TILE, TILE, 1,
+    const int64_t arows = (int64_t)tiles * L.n_act_rows, grows = (int64_t)tiles * p.n_adj_rows;
+    if (arows > 0x7fffffff || grows > 0x7fffffff) return cudaErrorInvalidValue;  // row coordinates are int32
+    if (act && !encode_2d(amap, act, tmap_type<T>(), (int)sizeof(T), arows, TILE, TILE, TILE, 1,
                           CU_TENSOR_MAP_SWIZZLE_NONE))
         return cudaErrorInvalidValue;
-    if (adj && !encode_2d(gmap, adj, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, rows, TILE, TILE, TILE, 1,
+    if (adj && !encode_2d(gmap, adj, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, grows, TILE, TILE, TILE, 1,
                           CU_TENSOR_MAP_SWIZZLE_NONE))
         return cudaErrorInvalidValue;
     return cudaSuccess;
@@ -1099,7 +1150,7 @@ cudaError_t forward_launch(const DevPlan& p, const float* V, int64_t ldv, void* 
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)((B + TILE - 1) / TILE);
     CUtensorMap amap, gmap;
-    if ((e = row_maps<T>(p, act, nullptr, grid, &amap, &gmap)) != cudaSuccess) return e;
+    if ((e = row_maps<T>(p, p.full, act, nullptr, grid, &amap, &gmap)) != cudaSuccess) return e;
     forward_kernel<T><<<grid, step_threads<T>(), stage_smem<T>(), s>>>(p, V, ldv, (T*)act, loss, B, amap);
     return cudaGetLastError();
 }
@@ -1111,21 +1162,21 @@ cudaError_t backward_launch(const DevPlan& p, const float* V, int64_t ldv, const
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)((B + TILE - 1) / TILE);
     CUtensorMap amap, gmap;
-    if ((e = row_maps<T>(p, act, adj, grid, &amap, &gmap)) != cudaSuccess) return e;
+    if ((e = row_maps<T>(p, p.full, act, adj, grid, &amap, &gmap)) != cudaSuccess) return e;
     backward_kernel<T><<<grid, step_threads<T>(), stage_smem<T>(), s>>>(p, V, ldv, (const T*)act, adj, grad_loss, gV, B,
                                                                    amap, gmap);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t steps_launch(const DevPlan& p, const OptParams& o, float* V, float* m, float* v, int64_t ldv, void* act,
-                         float* adj, float* loss, int t0, const int32_t* age, int n_steps, int64_t B,
-                         cudaStream_t s) {
+cudaError_t steps_launch(const DevPlan& p, const DevAct& L, const OptParams& o, float* V, float* m, float* v,
+                         int64_t ldv, void* act, float* adj, float* loss, int t0, const int32_t* age, int n_steps,
+                         int64_t B, cudaStream_t s) {
     cudaError_t e = prepare_tile_kernels<T>();
     if (e != cudaSuccess) return e;
     const int tiles = (int)((B + TILE - 1) / TILE);
     CUtensorMap amap, gmap;
-    if ((e = row_maps<T>(p, act, adj, (unsigned)tiles, &amap, &gmap)) != cudaSuccess) return e;
+    if ((e = row_maps<T>(p, L, act, adj, (unsigned)tiles, &amap, &gmap)) != cudaSuccess) return e;
     // Whole waves of tiles run one CTA per tile; a last, partial wave of at most half
     // the SMs runs in split mode (two CTAs of a cluster per tile) so that it fills them.
     int dev = 0, sms = 148;
@@ -1137,7 +1188,7 @@ cudaError_t steps_launch(const DevPlan& p, const OptParams& o, float* V, float* 
     const int tail = tiles - main_tiles;
     if (main_tiles > 0) {
         steps_kernel<T, false><<<(unsigned)main_tiles, step_threads<T>(), stage_smem<T>(), s>>>(
-            p, o, V, m, v, ldv, (T*)act, adj, loss, t0, age, n_steps, B, 0, amap, gmap);
+            p, L, o, V, m, v, ldv, (T*)act, adj, loss, t0, age, n_steps, B, 0, amap, gmap);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (tail > 0) {
@@ -1153,8 +1204,8 @@ cudaError_t steps_launch(const DevPlan& p, const OptParams& o, float* V, float* 
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, steps_kernel<T, true>, p, o, V, m, v, ldv, (T*)act, adj, loss, t0, age, n_steps,
-                               B, main_tiles, amap, gmap);
+        e = cudaLaunchKernelEx(&cfg, steps_kernel<T, true>, p, L, o, V, m, v, ldv, (T*)act, adj, loss, t0, age,
+                               n_steps, B, main_tiles, amap, gmap);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
@@ -1192,14 +1243,14 @@ cudaError_t launch_backward(const DevPlan& p, int act_type, const float* V, int6
     }
 }
 
-cudaError_t launch_steps(const DevPlan& p, int act_type, const OptParams& o, float* V, float* m, float* v, int64_t ldv,
-                         void* act, float* adj, float* loss, int t0, int n_steps, int64_t B, cudaStream_t s,
-                         const int32_t* age) {
+cudaError_t launch_steps(const DevPlan& p, const DevAct& L, int act_type, const OptParams& o, float* V, float* m,
+                         float* v, int64_t ldv, void* act, float* adj, float* loss, int t0, int n_steps, int64_t B,
+                         cudaStream_t s, const int32_t* age) {
     if (B == 0 || n_steps <= 0) return cudaSuccess;
     switch (act_type) {
-    case ACT_F32: return steps_launch<float>(p, o, V, m, v, ldv, act, adj, loss, t0, age, n_steps, B, s);
-    case ACT_BF16: return steps_launch<__nv_bfloat16>(p, o, V, m, v, ldv, act, adj, loss, t0, age, n_steps, B, s);
-    default: return steps_launch<__half>(p, o, V, m, v, ldv, act, adj, loss, t0, age, n_steps, B, s);
+    case ACT_F32: return steps_launch<float>(p, L, o, V, m, v, ldv, act, adj, loss, t0, age, n_steps, B, s);
+    case ACT_BF16: return steps_launch<__nv_bfloat16>(p, L, o, V, m, v, ldv, act, adj, loss, t0, age, n_steps, B, s);
+    default: return steps_launch<__half>(p, L, o, V, m, v, ldv, act, adj, loss, t0, age, n_steps, B, s);
     }
 }
 

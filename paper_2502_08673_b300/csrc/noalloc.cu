@@ -63,10 +63,11 @@ extern "C" sat_status sat_steps_noalloc(const sat_plan* p, sat_act_dtype act_dty
     if (B > 0 && dp->n_pi > 0 && (!V || (o->optimizer == SAT_OPT_ADAM && (!m || !v))))
         return sat::report_error(SAT_ERR_ARG, "NULL buffer");
     // act and adj blocks, each rounded up to 256 bytes
-    const uint64_t elems = (uint64_t)((B + SAT_TILE_SAMPLES - 1) / SAT_TILE_SAMPLES) * (uint64_t)dp->n_cone *
-                           SAT_TILE_SAMPLES;
-    const uint64_t act_bytes = (elems * (act_dtype == SAT_ACT_F32 ? 4u : 2u) + 255) / 256 * 256;
-    const uint64_t adj_bytes = (elems * 4u + 255) / 256 * 256;
+    const uint64_t tiles = (uint64_t)((B + SAT_TILE_SAMPLES - 1) / SAT_TILE_SAMPLES);
+    const uint64_t act_elems = tiles * (uint64_t)dp->full.n_act_rows * SAT_TILE_SAMPLES;
+    const uint64_t adj_elems = tiles * (uint64_t)dp->n_adj_rows * SAT_TILE_SAMPLES;
+    const uint64_t act_bytes = (act_elems * (act_dtype == SAT_ACT_F32 ? 4u : 2u) + 255) / 256 * 256;
+    const uint64_t adj_bytes = (adj_elems * 4u + 255) / 256 * 256;
     if (act_bytes + adj_bytes > SAT_NOALLOC_SCRATCH_BYTES)
         return sat::report_error(
             SAT_ERR_ARG, "sat_steps_noalloc needs " + std::to_string(act_bytes + adj_bytes) +
@@ -85,8 +86,8 @@ extern "C" sat_status sat_steps_noalloc(const sat_plan* p, sat_act_dtype act_dty
     op.b1 = o->beta1;
     op.b2 = o->beta2;
     op.eps = o->eps;
-    e = sat::launch_steps(*dp, (int)act_dtype, op, V, m, v, ldv, s, reinterpret_cast<float*>(s + act_bytes), loss, t0,
-                          n_steps, B, (cudaStream_t)stream);
+    e = sat::launch_steps(*dp, dp->full, (int)act_dtype, op, V, m, v, ldv, s, reinterpret_cast<float*>(s + act_bytes),
+                          loss, t0, n_steps, B, (cudaStream_t)stream);
     if (e != cudaSuccess) return sat::report_error(SAT_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
     return SAT_OK;
 }
