@@ -95,6 +95,10 @@ def train_proposal(P, torch, plan, w, mode, B, opt, ad, log, train_steps=0, roun
     n = keys.shape[0]
     S, K = 4096, 16
     mlp = P.Mlp.create(64, 256, plan.info["n_pi"], max_rows=max(B, S * K), seed=0)
+    if n == 0:  # the plain sampler found nothing to learn from: the proposal keeps its initial weights
+        log.update({"proposal_mode": mode, "proposal_training_solutions": 0, "proposal_train_steps": 0,
+                    "proposal_setup_s": time.perf_counter() - t0})
+        return mlp
     steps = train_steps or max(64, min(512, 2 * n // S))
     g = torch.Generator(device="cuda").manual_seed(0)
     losses = []
