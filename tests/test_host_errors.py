@@ -31,6 +31,10 @@ def test_null_objects_are_rejected():
     opt = N.OptParams(0, 0.1, 0.9, 0.999, 1e-8)
     _err(L.sat_steps(None, 0, C.byref(opt), None, None, None, 0, None, None, None, 1, 1, 0, None))
     _err(L.sat_steps_aged(None, 0, C.byref(opt), None, None, None, 0, None, None, None, None, 1, 1, 0, None))
+    _err(L.sat_steps_recompute(None, 0, C.byref(opt), None, None, None, 0, None, None, None, None, 1, 1, 0, 8,
+                               None))
+    a, g = C.c_uint64(), C.c_uint64()
+    _err(L.sat_plan_layout_elems(None, 8, 128, C.byref(a), C.byref(g)))
     _err(L.sat_threshold(None, None, 0, None, 0, None, 0, None))
     assert L.sat_solutions_count(None) == 0
 
