@@ -299,3 +299,38 @@ def test_sample_end_to_end_planted3sat(gpu):
     w = sols.words()
     order = [tuple(int(x) for x in r) for r in w]
     assert sols.stats["valid"] >= len(A)
+
+
+@pytest.mark.parametrize("act_dtype,act_bound,rel_bound", [("f32", 1e-5, 1e-4), ("bf16", 0.06, 2.0),
+                                                           ("f16", 0.01, 0.5)])
+def test_per_step_error_vs_fp64(gpu, act_dtype, act_bound, rel_bound):
+    """Per-step error on the 20k-gate workload against the FP64 oracle, by activation
+    storage type: activations (max abs), loss (max rel) and dL/dV (max of |g - g*| /
+    max(|g*|, 1e-2 max_i |g*_i|) per sample).  FP32 meets the parity tolerances; the
+    16-bit types are reported (printed) and loosely bounded."""
+    P, cnf, circ, plan, orc = _setup(INSTANCES["tseitin_2k_20k_d40"]())
+    B = 256
+    V0 = normal_logits(B, orc.n_pi, seed=31)
+    V = torch.tensor(V0.T.copy(), device=gpu)
+    act = P.new_act(plan, B, act_dtype)
+    loss = torch.empty(B, device=gpu)
+    P.sat_forward(plan, V, act, loss, act_dtype=act_dtype)
+    adj, gV = P.new_adj(plan, B), torch.zeros_like(V)
+    P.sat_backward(plan, V, act, adj, gV, act_dtype=act_dtype)
+    torch.cuda.synchronize()
+    A = P.untile(act, B).float().cpu().numpy()
+    g = gV.cpu().numpy().T.astype(np.float64)
+    vals, loss_ref = oracle.forward(orc.flat, V0.astype(np.float64))
+    gref, _ = oracle.backward(orc.flat, vals)
+    cone, _, neg = plan.var_nodes()
+    act_err = 0.0
+    for var in range(1, plan.n_vars + 1):
+        if cone[var] >= 0:
+            a = A[cone[var]] if not neg[var] else 1.0 - A[cone[var]]
+            act_err = max(act_err, float(np.abs(a - vals[:, var - 1]).max()))
+    loss_err = float(np.max(np.abs(loss.cpu().numpy() - loss_ref) / np.abs(loss_ref)))
+    floor = 1e-2 * np.abs(gref).max(axis=1, keepdims=True)
+    grad_err = float(np.max(np.abs(g - gref) / (np.maximum(np.abs(gref), floor) + 1e-30)))
+    print(f"per-step error vs FP64 [{act_dtype}]: activations {act_err:.3g} abs, loss {loss_err:.3g} rel, "
+          f"gradient {grad_err:.3g} rel (floored), |g*| max {np.abs(gref).max():.3g}")
+    assert act_err < act_bound and grad_err < rel_bound
