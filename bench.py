@@ -283,7 +283,9 @@ def run_reference(args, w):
             "ms_per_step": 1e3 * secs / max(1, args.steps), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, **{k: v for k, v in w.items() if k != "kind"},
-                       "reference_batch_per_step": args.ref_samples},
+                       "optimizer": args.optimizer, "relaxation": "direct CNF" if args.direct else "Algorithm 1",
+                       "recompute_segment": args.recompute,
+                       "parallelism": "the oracle on the host cores", "reference_batch_per_step": args.ref_samples},
             "cpu_baseline": {"value": value, "unit": "unique valid solutions/s", "cores": info.get("threads"),
                              "kind": "oracle",
                              "sample": f"{args.ref_samples} samples x {w['steps']} steps per step (bounded sample)"},
