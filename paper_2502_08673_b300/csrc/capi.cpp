@@ -465,15 +465,15 @@ static sat_status plan_layout(const sat_plan* p, int32_t k, const sat::DevAct** 
             next += off[l + 1] - off[l];
         }
     int64_t S = 0;
-    for (int32_t l0 = 1; l0 <= L; l0 += k) {
+    for (int64_t l0 = 1; l0 <= L; l0 += k) {
         int64_t seg = 0;
-        for (int32_t l = l0; l < l0 + k && l <= L; l++)
+        for (int64_t l = l0; l < l0 + k && l <= L; l++)
             if (!stored[l]) seg += off[l + 1] - off[l];
         S = std::max(S, seg);
     }
-    for (int32_t l0 = 1, j = 0; l0 <= L; l0 += k, j++) {
+    for (int64_t l0 = 1, j = 0; l0 <= L; l0 += k, j++) {
         int64_t pos = next + (j % 2) * S;
-        for (int32_t l = l0; l < l0 + k && l <= L; l++)
+        for (int64_t l = l0; l < l0 + k && l <= L; l++)
             if (!stored[l]) {
                 act_off[l] = (int32_t)pos;
                 pos += off[l + 1] - off[l];
