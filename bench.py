@@ -224,8 +224,14 @@ def merge_ranks(elapsed_ms, uniq, valid, device="cuda"):
     return float(tt.item()), int(cnt[0].item()), int(cnt[1].item())
 
 
-def kernel_source_hash():
-    return hashlib.sha256((ROOT / "paper_2502_08673_b300" / "csrc" / "kernels.cu").read_bytes()).hexdigest()[:16]
+def kernel_source_hash(text=None):
+    """Hash of the step kernels' source code with comments and whitespace removed (a change
+    to the comments does not make a profile stale; any change to the code does)."""
+    if text is None:
+        text = (ROOT / "paper_2502_08673_b300" / "csrc" / "kernels.cu").read_text()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return hashlib.sha256(" ".join(text.split()).encode()).hexdigest()[:16]
 
 
 # --------------------------------------------------------------------------

@@ -26,11 +26,15 @@
  *    ascending DIMACS-variable order (sat_plan_pi_vars).  Bit arrays:
  *    [rows][ldw] uint32, ldw >= ceil(B/32), bit j of word w = sample 32 w + j.
  *  - Per-node scratch (act, adj) is tile-major: samples are grouped in tiles
- *    of SAT_TILE, and tile t owns the contiguous block [n_cone][SAT_TILE] that
- *    starts at element t * n_cone * SAT_TILE, so it holds
- *    ceil(B/SAT_TILE) * n_cone * SAT_TILE elements (sat_plan_scratch_elems);
- *    the padding samples of the last tile are written too.  act holds
- *    act_dtype elements, adj float32; both must be 16-byte aligned.
+ *    of SAT_TILE, and tile t owns the contiguous block [rows][SAT_TILE] that
+ *    starts at element t * rows * SAT_TILE, so an array holds
+ *    ceil(B/SAT_TILE) * rows * SAT_TILE elements.  act: rows = n_cone (row =
+ *    cone node) or, under recomputation, the rows of that layout; adj: the input
+ *    level plus a ring of max_span + 1 gate levels (sat_plan_layout_elems gives
+ *    both; sat_plan_scratch_elems, n_cone rows, is enough for either array
+ *    without recomputation).  The padding samples of the last tile are written
+ *    too.  act holds act_dtype elements, adj float32; both must be 16-byte
+ *    aligned.
  *  - Deterministic for a given (seed, options, GPU).
  */
 #ifndef SATSAMPLER_H
@@ -128,7 +132,7 @@ void sat_circuit_free(sat_circuit* c);
  * the adjoint) and the CNF (for the exact check) to the current device. */
 typedef struct sat_plan_info {
     uint32_t n_vars, n_pi, n_cone_pi, n_outputs, n_cone_levels, n_levels, key_words, max_span;
-    uint64_t n_cone;           /* rows of act / adj: cone inputs + cone gates */
+    uint64_t n_cone;           /* cone inputs + cone gates: rows of the full act layout */
     uint64_t n_nodes;          /* rows of the Boolean node array: inputs + all gates */
     uint64_t n_cone_gates, n_gates, n_clauses, n_fanout_edges;
     uint64_t upload_bytes;     /* bytes copied host -> device by sat_plan_create */

@@ -3,8 +3,9 @@
 // Layout: every per-sample quantity is stored node-major with the batch
 // contiguous ("SoA"): row r of V, m, v, gV is primary input r over the batch.
 // The per-node scratch (act, adj) is tile-major: a CTA owns a tile of TILE
-// samples (VEC consecutive samples per lane) and its contiguous block of
-// [n_cone][TILE] rows, and walks the levels of the circuit.  Samples are
+// samples (VEC consecutive samples per lane) and its contiguous blocks of
+// [rows][TILE] (act rows per the act layout, adj rows per the adjoint ring),
+// and walks the levels of the circuit.  Samples are
 // independent, so the only synchronisation is __syncthreads between levels.
 //
 // Relaxation (Table 1): with input negation x -> 1 - x folded in, every
@@ -182,7 +183,7 @@ __device__ __forceinline__ TileCtx tile_ctx(int64_t B, int tile0 = 0, bool split
     return c;
 }
 
-// Element offset of this lane's samples in row `row` of a tile's [n_cone][TILE] block.
+// Element offset of this lane's samples in row `row` of a tile's [rows][TILE] block.
 __device__ __forceinline__ uint32_t at(int row, const TileCtx& c) {
     return (uint32_t)row * TILE + (uint32_t)(c.lane * VEC);
 }
