@@ -151,6 +151,13 @@ sat_status sat_plan_var_nodes(const sat_plan* p, int64_t* cone_node, int64_t* fu
  * healthy; bit 2 = a bounded wait for an asynchronous copy expired, and the
  * results of that launch are invalid.  clear != 0 resets it. */
 sat_status sat_plan_status(const sat_plan* p, uint32_t* status, int32_t clear, void* stream);
+/* Diagnostic of the failure path of every asynchronous-copy wait in the step
+ * kernels (which give up after 1 s): one warp polls, with the same bounded
+ * wait but a bound of limit_us microseconds (1 .. 10^7), an mbarrier whose
+ * phase no copy completes, and sets bit 2 (the plan status bit of an expired
+ * wait) in a fresh status word, returned in *status.  The kernel then returns
+ * normally: the context stays usable.  Synchronises `stream`. */
+sat_status sat_diag_bounded_wait(uint32_t limit_us, uint32_t* status, void* stream);
 /* Elements of one act / adj scratch array for a batch of B samples (enough for
  * either array under every call that takes them without a segment). */
 sat_status sat_plan_scratch_elems(const sat_plan* p, int64_t B, uint64_t* elems);

@@ -107,6 +107,21 @@ sat_status upload(sat_plan* p, const std::vector<T>& h, const T** dst) {
     return upload_to(p->allocs, h, dst);
 }
 
+// Every row a step kernel gathers or stores through these records must lie inside its
+// tile's block: checked once on the host, so that the kernels need no per-access bounds
+// test (a TMA gather outside the tensor map would read fill values, a store would not).
+bool records_in_range(const std::vector<int2>& gate, const std::vector<int4>& edge,
+                             const std::vector<int32_t>& out_row, int64_t act_rows, int64_t adj_rows) {
+    auto ok = [](int64_t r, int64_t n) { return r >= 0 && r < n; };
+    for (const int2& g : gate)
+        if (!ok(g.x & 0x0FFFFFFF, act_rows) || !ok(g.y, act_rows)) return false;
+    for (const int4& e : edge)
+        if ((e.x != -1 && !ok(e.x, adj_rows)) || !ok(e.y & 0x7FFFFFFF, act_rows)) return false;
+    for (int32_t r : out_row)
+        if (!ok(r, act_rows)) return false;
+    return true;
+}
+
 sat_status check_device(int device) {
     int cur = -1;
     CK(cudaGetDevice(&cur));
@@ -324,6 +339,8 @@ sat_status sat_plan_create(const sat_circuit* c, const sat_cnf* cnf, sat_plan** 
     // bit 31 of the sibling field marks the last edge of each node's range
     for (size_t n = 0; n + 1 < P.fo_off.size(); n++)
         if (P.fo_off[n + 1] > P.fo_off[n]) fe[(size_t)P.fo_off[n + 1] - 1].y |= (int32_t)0x80000000u;
+    if (!records_in_range(cg, fe, P.c_out_node, (int64_t)P.n_cone, d.n_adj_rows))
+        return bail(fail(SAT_ERR_ARG, "internal error: plan records outside the scratch block"));
     std::vector<int32_t> cl_lit(P.cl_node.size());
     for (size_t i = 0; i < cl_lit.size(); i++) cl_lit[i] = (P.cl_node[i] << 1) | P.cl_neg[i];
     if ((st = upload(p, P.c_level_off, &d.c_level_off)) != SAT_OK) return bail(st);
@@ -496,6 +513,8 @@ static sat_status plan_layout(const sat_plan* p, int32_t k, const sat::DevAct** 
     sat::DevAct a;
     a.k = k;
     a.n_act_rows = next + 2 * S;
+    if (!records_in_range(gate, edge, out_row, a.n_act_rows, d.n_adj_rows))
+        return fail(SAT_ERR_ARG, "internal error: recomputation records outside the scratch block");
     sat_status st;
     if ((st = upload_to(p->lay_allocs, act_off, &a.act_off)) != SAT_OK) return st;
     if ((st = upload_to(p->lay_allocs, stored, &a.stored)) != SAT_OK) return st;
@@ -519,6 +538,25 @@ sat_status sat_plan_layout_elems(const sat_plan* p, int32_t segment, int64_t B, 
         *act_elems = tiles * (uint64_t)lay->n_act_rows * SAT_TILE_SAMPLES;
     }
     if (adj_elems) *adj_elems = tiles * (uint64_t)p->dp.n_adj_rows * SAT_TILE_SAMPLES;
+    return SAT_OK;
+}
+
+sat_status sat_diag_bounded_wait(uint32_t limit_us, uint32_t* status, void* stream) {
+    if (!status || limit_us == 0 || limit_us > 10000000u)
+        return fail(SAT_ERR_ARG, "bad argument (limit_us in 1..10^7, status non-NULL)");
+    unsigned* d = nullptr;
+    if (cudaMalloc(&d, sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SAT_ERR_OOM, "cudaMalloc failed for the status word");
+    }
+    unsigned h = 0;
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(unsigned), S(stream));
+    if (e == cudaSuccess) e = sat::launch_bounded_wait_diag(d, (uint64_t)limit_us * 1000u, S(stream));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(unsigned), cudaMemcpyDeviceToHost, S(stream));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S(stream));
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(SAT_ERR_CUDA, std::string("diagnostic kernel: ") + cudaGetErrorString(e));
+    *status = h;
     return SAT_OK;
 }
 

@@ -99,6 +99,8 @@ cudaError_t launch_retire(const uint32_t* valid, int32_t* age, uint32_t* restart
 cudaError_t launch_restart(const DevPlan& p, const uint32_t* restart, uint64_t seed, uint32_t round, float scale,
                            const float* src, int64_t lds, float* V, float* m, float* v, int64_t ldv, int64_t B,
                            cudaStream_t s);
+// Diagnostic: a bounded wait (limit_ns) on an mbarrier nothing completes; sets bit 2 of *status.
+cudaError_t launch_bounded_wait_diag(unsigned* status, uint64_t limit_ns, cudaStream_t s);
 cudaError_t launch_opt_update(const DevPlan& p, const OptParams& o, float* V, float* m, float* v,
                               const float* gV, int64_t ldv, int t, int64_t B, cudaStream_t s);
 cudaError_t launch_threshold(const DevPlan& p, const float* V, int64_t ldv, uint32_t* node_bits,

@@ -244,7 +244,7 @@ constexpr int CHUNK = SAT_CHUNK;  // gates (forward) or fan-out edges (adjoint) 
 constexpr int NSLOT = 2;   // pipeline depth per warp (gathers land one chunk ahead: 93% of waits succeed at once)
 static_assert(CHUNK == 4, "a chunk is one tile::gather4 load (4 rows) per operand");
 constexpr unsigned STATUS_WAIT_TIMEOUT = 4u;
-constexpr uint32_t WAIT_LIMIT = 1u << 24;
+constexpr uint64_t WAIT_NS = 1000000000ull;  // bound of one wait for a warp's own copies (1 s)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -351,20 +351,48 @@ __device__ __forceinline__ Stage make_stage(char* smem, unsigned* status, const 
     return st;
 }
 
-// Warp-uniform: wait for the completion of slot s.
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for the phase of `bar` with the given parity: false after limit_ns
+// nanoseconds (or 2^30 polls) without completion; the copies it counts are then given up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 1;; it++) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 15) == 0 && (global_ns() - t0 > limit_ns || it > (1u << 30))) return false;
+    }
+}
+
+// Warp-uniform: wait for the completion of slot s.  On expiry the warp records
+// STATUS_WAIT_TIMEOUT and stops waiting for the rest of the launch.
 __device__ __forceinline__ void stage_wait(Stage& st, int s) {
-    if (!st.poisoned) {
-        uint32_t it = 0;
-        while (!mbar_try_wait(st.bar + s, (st.parity >> s) & 1u)) {
-            if (++it >= WAIT_LIMIT) {
-                st.poisoned = true;
-                if ((threadIdx.x & 31) == 0) atomicOr(st.status, STATUS_WAIT_TIMEOUT);
-                break;
-            }
-        }
+    if (!st.poisoned && !mbar_wait_bounded(st.bar + s, (st.parity >> s) & 1u, WAIT_NS)) {
+        st.poisoned = true;
+        if ((threadIdx.x & 31) == 0) atomicOr(st.status, STATUS_WAIT_TIMEOUT);
     }
     st.parity ^= 1u << s;
     __syncwarp();
+}
+
+// Diagnostic: one warp waits, with the step kernels' bounded wait, on an mbarrier
+// whose phase nothing completes (expect_tx of one byte, no copy issued), and records
+// the expiry in *status like the step kernels do.  No copy is in flight, so the
+// kernel can return at once.
+__global__ void bounded_wait_diag_kernel(unsigned* status, uint64_t limit_ns) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    if (threadIdx.x == 0) mbar_expect_tx(&bar, 1u);  // the one arrival; one byte stays pending forever
+    __syncwarp();
+    if (!mbar_wait_bounded(&bar, 0u, limit_ns) && threadIdx.x == 0) atomicOr(status, STATUS_WAIT_TIMEOUT);
 }
 
 // Forward pass of one tile, input level: P = sigmoid(V) for the cone inputs (rows
@@ -1253,6 +1281,11 @@ cudaError_t launch_steps(const DevPlan& p, const DevAct& L, int act_type, const 
     case ACT_BF16: return steps_launch<__nv_bfloat16>(p, L, o, V, m, v, ldv, act, adj, loss, t0, age, n_steps, B, s);
     default: return steps_launch<__half>(p, L, o, V, m, v, ldv, act, adj, loss, t0, age, n_steps, B, s);
     }
+}
+
+cudaError_t launch_bounded_wait_diag(unsigned* status, uint64_t limit_ns, cudaStream_t s) {
+    bounded_wait_diag_kernel<<<1, 32, 0, s>>>(status, limit_ns);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_opt_update(const DevPlan& p, const OptParams& o, float* V, float* m, float* v, const float* gV,
