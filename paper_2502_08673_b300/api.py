@@ -167,6 +167,7 @@ class Dedup(_Handle):
         check(lib().sat_dedup_create(plan.handle, max_keys, max_batch, C.byref(h)))
         d = cls(h)
         d.key_words = plan.info["key_words"]
+        d.max_batch = max_batch
         return d
 
     def insert(self, keys, valid, B: int, hashes=None, is_new=None, stream=None):
@@ -502,11 +503,56 @@ def run_epochs(plan: Plan, ws: Workspace, opt: N.OptParams, steps: int, check_ev
         sat_retire(ws.valid, ws.age, ws.restart, kk, max_age, ws.B, stream)
         r = round_ + 1 + e
         if proposal is not None:
+            if ws.src is None:
+                ws.src = torch.empty_like(ws.V)
             proposal.propose(ws.src, seed, r, tau, stream)
         sat_restart(plan, ws.restart, seed, r, ws.V, ws.m, ws.v, init_scale, ws.src, stream)
         done += kk
         e += 1
     return e
+
+
+def save_checkpoint(path, ws: Workspace, dedup: Dedup | None = None, **meta):
+    """Checkpoint of a sampling run between rounds or epochs (numpy .npz): the
+    workspace's V, m, v and early-exit ages, the distinct keys found so far, and the
+    caller's metadata (for example the next round counter), which load_checkpoint
+    returns.  Everything else in a workspace is rewritten before it is read."""
+    import json
+    import torch
+    torch.cuda.synchronize()
+    arrays = {"V": ws.V.cpu().numpy(), "m": ws.m.cpu().numpy(), "v": ws.v.cpu().numpy()}
+    if ws.age is not None:
+        arrays["age"] = ws.age.cpu().numpy()
+    if dedup is not None:
+        arrays["keys"] = dedup.keys()
+    np.savez(path, meta=np.array(json.dumps(meta)), **arrays)
+
+
+def load_checkpoint(path, ws: Workspace, dedup: Dedup | None = None) -> dict:
+    """Restore a save_checkpoint into a workspace of the same plan and batch (and the
+    keys into an empty or cleared dedup set, max_batch keys per insert); returns the
+    metadata."""
+    import json
+    import torch
+    z = np.load(path)
+    for name in ("V", "m", "v"):
+        getattr(ws, name).copy_(torch.from_numpy(z[name]))
+    if "age" in z.files:
+        ws.age = torch.from_numpy(z["age"]).to(ws.V.device)
+        ws.restart = torch.zeros_like(ws.valid)
+        ws.src = None
+    if dedup is not None and "keys" in z.files:
+        keys = np.ascontiguousarray(z["keys"]).view(np.int32)
+        dedup.clear()
+        for i in range(0, len(keys), dedup.max_batch):
+            part = torch.from_numpy(keys[i:i + dedup.max_batch]).to(ws.V.device)
+            n = part.shape[0]
+            words = np.zeros((n + 31) // 32, np.uint32)
+            bits = np.packbits(np.ones(n, bool), bitorder="little")
+            words.view(np.uint8)[: len(bits)] = bits
+            dedup.insert(part, torch.from_numpy(words.view(np.int32)).to(ws.V.device), n)
+    torch.cuda.synchronize()
+    return json.loads(str(z["meta"]))
 
 
 def valid_mask(valid_words, B: int) -> np.ndarray:

@@ -2,6 +2,7 @@
 // lifetimes, device uploads and the end-to-end round loop.  Every step of the
 // path runs in the kernels of kernels.cu.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cstdint>
@@ -908,6 +909,22 @@ struct Workspace {
 
 size_t act_bytes(int t) { return t == SAT_ACT_F32 ? 4 : 2; }
 
+// NVTX ranges around a round and its phases, for profiler timelines (NVTX v3 is
+// header-only: without an attached tool the calls do nothing).
+struct NvtxPhases {
+    bool open = false;
+    explicit NvtxPhases(const char* round) { nvtxRangePushA(round); }
+    void next(const char* phase) {
+        if (open) nvtxRangePop();
+        nvtxRangePushA(phase);
+        open = true;
+    }
+    ~NvtxPhases() {
+        if (open) nvtxRangePop();
+        nvtxRangePop();
+    }
+};
+
 size_t scratch_elems(int64_t rows, int64_t B) {
     return (size_t)((B + SAT_TILE_SAMPLES - 1) / SAT_TILE_SAMPLES) * (size_t)rows * SAT_TILE_SAMPLES;
 }
@@ -968,20 +985,25 @@ static sat_status sample_early_exit(const sat_plan* p, sat_dedup* d, const sat_s
     acc.samples = (uint64_t)B;
     for (int64_t done = 0, e = 0; done < budget; e++) {
         const int kk = (int)std::min<int64_t>(k, budget - done);
+        NvtxPhases ph("sat.epoch");
+        ph.next("sat.steps");
         CK(cudaEventRecord(ev[0], str));
         for (int t0 = 1; t0 <= kk; t0 += spl)
             CK(sat::launch_steps(dp, *w.lay, o->act_dtype, op, w.V, w.m, w.v, B, w.act, w.adj, nullptr, t0,
                                  std::min(spl, kk - t0 + 1), B, str, age));
         CK(cudaEventRecord(ev[1], str));
+        ph.next("sat.verify");
         CK(sat::launch_threshold(dp, w.V, B, w.bits, w.ldw, w.keys, B, str));
         CK(sat::launch_hard_eval(dp, w.bits, w.ldw, B, str));
         CK(sat::launch_cnf_check(dp, w.bits, w.ldw, w.valid, B, str));
         CK(cudaEventRecord(ev[2], str));
+        ph.next("sat.dedup");
         uint64_t n = 0;
         if ((s = sat_dedup_count(d, &n, str)) != SAT_OK) return s;
         if (n + (uint64_t)B > d->d.pool_capacity) return fail(SAT_ERR_TABLE_FULL, "dedup table is full");
         CK(sat::launch_dedup_insert(d->d, w.keys, w.valid, B, nullptr, nullptr, d->slot_of, str));
         CK(cudaEventRecord(ev[3], str));
+        ph.next("sat.restart");
         CK(sat::launch_retire(w.valid, age, restart, kk, max_age, B, str));
         const uint32_t round = o->first_round + 1u + (uint32_t)e;
         if (o->proposal && (s = sat_mlp_propose(o->proposal, o->seed, round, o->proposal_tau, Vp, B, B, o->stream)) !=
@@ -1061,6 +1083,8 @@ sat_status sat_sample_plan(const sat_plan* p, sat_dedup* d, const sat_sample_opt
     uint64_t have = 0;
     sat_status result = SAT_PARTIAL;
     for (int r = 0; r < o->max_rounds; r++) {
+        NvtxPhases ph("sat.round");
+        ph.next("sat.init");
         CK(cudaEventRecord(ev[0], str));
         if (r == 0 && o->init_logits) {
             CK(cudaMemcpy2DAsync(w.V, B * 4, o->init_logits, o->init_ld * 4, B * 4, npi, cudaMemcpyDeviceToDevice, str));
@@ -1074,14 +1098,17 @@ sat_status sat_sample_plan(const sat_plan* p, sat_dedup* d, const sat_sample_opt
         CK(cudaMemsetAsync(w.m, 0, npi * B * 4, str));
         CK(cudaMemsetAsync(w.v, 0, npi * B * 4, str));
         CK(cudaEventRecord(ev[1], str));
+        ph.next("sat.steps");
         for (int t0 = 1; t0 <= o->steps; t0 += spl)
             CK(sat::launch_steps(dp, *w.lay, o->act_dtype, op, w.V, w.m, w.v, B, w.act, w.adj, nullptr, t0,
                                  std::min(spl, o->steps - t0 + 1), B, str));
         CK(cudaEventRecord(ev[2], str));
+        ph.next("sat.verify");
         CK(sat::launch_threshold(dp, w.V, B, w.bits, w.ldw, w.keys, B, str));
         CK(sat::launch_hard_eval(dp, w.bits, w.ldw, B, str));
         CK(sat::launch_cnf_check(dp, w.bits, w.ldw, w.valid, B, str));
         CK(cudaEventRecord(ev[3], str));
+        ph.next("sat.dedup");
         uint64_t n = 0;
         if ((s = sat_dedup_count(d, &n, str)) != SAT_OK) return s;
         if (n + (uint64_t)B > d->d.pool_capacity) return fail(SAT_ERR_TABLE_FULL, "dedup table is full");
