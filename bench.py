@@ -224,6 +224,32 @@ def merge_ranks(elapsed_ms, uniq, valid, device="cuda"):
     return float(tt.item()), int(cnt[0].item()), int(cnt[1].item())
 
 
+def distinct_keys_across_ranks(keys, device="cuda"):
+    """The exchange step of the sharded sampler: the union of the ranks' distinct keys
+    (uint32 [n, key_words] on the host, this rank's new keys).  Every rank all-gathers
+    the others' keys (padded to the longest list) and counts the distinct rows.
+    Without a process group: this rank's count."""
+    import torch
+    import torch.distributed as dist
+    keys = np.ascontiguousarray(keys, dtype=np.uint32)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        world = dist.get_world_size()
+        n = torch.tensor([keys.shape[0]], dtype=torch.int64, device=device)
+        ns = [torch.zeros_like(n) for _ in range(world)]
+        dist.all_gather(ns, n)
+        ns = [int(x.item()) for x in ns]
+        pad = np.zeros((max(ns), keys.shape[1]), np.uint32)
+        pad[: keys.shape[0]] = keys
+        mine = torch.from_numpy(pad.view(np.int32)).to(device)
+        parts = [torch.zeros_like(mine) for _ in range(world)]
+        dist.all_gather(parts, mine)
+        keys = np.concatenate([p.cpu().numpy().view(np.uint32)[:k] for p, k in zip(parts, ns)])
+    if keys.shape[0] == 0:
+        return 0
+    rows = keys.view(np.dtype((np.void, keys.shape[1] * 4))).ravel()
+    return int(np.unique(rows).shape[0])
+
+
 def kernel_source_hash(text=None):
     """Hash of the step kernels' source code with comments and whitespace removed (a change
     to the comments does not make a profile stale; any change to the code does)."""
@@ -507,6 +533,12 @@ def main():
         kernel_ms = [a.elapsed_time(b) for a, b in kev]
         launch_steps = None
     t_max, uniq_all, valid_all = merge_ranks(elapsed_ms, uniq, valid_total, device="cuda")
+    merge_s = None
+    if world > 1:
+        # the one exchange step: the union of the ranks' new distinct keys (after the timed region)
+        t_m = time.perf_counter()
+        uniq_all = distinct_keys_across_ranks(dedup.keys()[before:], device="cuda")
+        merge_s = time.perf_counter() - t_m
     value = uniq_all / (t_max / 1e3)
     run_steps = prop_steps if (mlp is not None and args.check_every <= 0) else steps
     gate_evals = info["n_cone_gates"] * B * run_steps * args.steps * world
@@ -574,8 +606,10 @@ def main():
                        "recompute_segment": args.recompute,
                        "l2_flush": "working set > L2 (activations %.1f GB)" %
                        (scratch["act"] / 1e9),
-                       "parallelism": f"replicas x{world} (disjoint Philox streams)"},
+                       "parallelism": f"replicas x{world} (disjoint Philox streams; distinct keys merged "
+                                      f"across ranks after the timed region)"},
             "gate_evals_per_s": gate_evals / (t_max / 1e3),
+            "merge_s": merge_s,
             "valid_fraction": (valid_all / (B * args.steps * world)) if args.check_every <= 0 else None,
             "unique_in_timed_steps": uniq_all,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -1,7 +1,8 @@
 """The N > 1 path of bench.py on CPU: two gloo ranks (no GPU).
 
 Ranks draw disjoint Philox round ranges and report one whole-job line: the
-slowest rank's time and the sum of their unique and valid counts.
+slowest rank's time, the sum of their valid counts and the union of their
+distinct keys (all-gathered once after the timed region).
 """
 import os
 import socket
@@ -25,7 +26,13 @@ def _worker(rank, world, port, q):
     try:
         import bench
         t, u, v = bench.merge_ranks(10.0 + 5.0 * rank, 100 * (rank + 1), 7 + rank, device="cpu")
-        q.put((rank, t, u, v, bench.round_base_of(rank)))
+        # distinct keys: rank 0 holds keys 0..99, rank 1 keys 50..179 (50 shared) -> 180 distinct
+        import numpy as np
+        ids = np.arange(0, 100) if rank == 0 else np.arange(50, 180)
+        keys = np.zeros((len(ids), 3), np.uint32)
+        keys[:, 0], keys[:, 2] = ids, ids * 7 + 1
+        d = bench.distinct_keys_across_ranks(keys, device="cpu")
+        q.put((rank, t, u, v, bench.round_base_of(rank), d))
     finally:
         dist.destroy_process_group()
 
@@ -41,14 +48,19 @@ def test_two_gloo_ranks_merge_and_disjoint_streams():
     for p in procs:
         p.join(60)
         assert p.exitcode == 0
-    for rank, t, u, v, base in out:
+    for rank, t, u, v, base, d in out:
         assert t == 15.0            # slowest rank
         assert u == 300 and v == 15  # summed over ranks
+        assert d == 180              # union of the ranks' distinct keys, on every rank
     bases = [o[4] for o in out]
     # the rounds one rank can use (2^20) never reach the next rank's range
     assert bases[1] - bases[0] >= 1 << 20
 
 
 def test_single_process_merge_is_identity():
+    import numpy as np
     import bench
     assert bench.merge_ranks(3.0, 5, 7, device="cpu") == (3.0, 5, 7)
+    keys = np.array([[1, 2], [3, 4], [1, 2], [0, 0]], np.uint32)
+    assert bench.distinct_keys_across_ranks(keys, device="cpu") == 3
+    assert bench.distinct_keys_across_ranks(np.zeros((0, 2), np.uint32), device="cpu") == 0
