@@ -402,6 +402,10 @@ def main():
     ap.add_argument("--proposal", default="none", choices=["none", "same", "heldout"],
                     help="initial logits from the learned proposal (trained untimed) instead of N(0,1)")
     ap.add_argument("--tau", type=float, default=1.0)
+    ap.add_argument("--heldout-seed", type=int, default=17,
+                    help="planted seed of the benchmarked instance under --proposal heldout (training uses 1..16)")
+    ap.add_argument("--proposal-cache", default="",
+                    help="file of trained proposal weights: loaded when it exists, else written after training")
     ap.add_argument("--proposal-steps", type=int, default=0,
                     help="optimisation steps per round when starting from the proposal (default: the workload's)")
     ap.add_argument("--proposal-train-steps", type=int, default=0, help="IMLE steps (default: 2 epochs, 64..512)")
@@ -449,7 +453,7 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    text = instance_text(w, planted_seed=17 if args.proposal == "heldout" else None)
+    text = instance_text(w, planted_seed=args.heldout_seed if args.proposal == "heldout" else None)
     cnf = P.Cnf.from_dimacs(text)
     t0 = time.perf_counter()
     circ = P.Circuit.build(cnf, direct=args.direct, reorder=args.reorder)
@@ -470,8 +474,21 @@ def main():
     round_base = round_base_of(rank)
 
     prop_log = {}
-    mlp = (train_proposal(P, torch, plan, w, args.proposal, B, opt, ad, prop_log, args.proposal_train_steps,
-                          args.proposal_rounds) if args.proposal != "none" else None)
+    mlp = None
+    if args.proposal != "none":
+        cache = Path(args.proposal_cache) if args.proposal_cache else None
+        if cache is not None and cache.exists():  # weights of an earlier training run of the same mode
+            z = np.load(cache)
+            mlp = P.Mlp.create(64, 256, plan.info["n_pi"], max_rows=max(B, 4096 * 16), seed=0)
+            mlp.set_params(z["theta"])
+            prop_log.update({"proposal_mode": args.proposal, "proposal_loaded_from": cache.name,
+                             **{k: z[k].item() for k in z.files if k != "theta"}})
+        else:
+            mlp = train_proposal(P, torch, plan, w, args.proposal, B, opt, ad, prop_log, args.proposal_train_steps,
+                                 args.proposal_rounds)
+            if cache is not None:
+                np.savez(cache, theta=mlp.params(), **{k: v for k, v in prop_log.items()
+                                                      if isinstance(v, (int, float, str))})
     prop_steps = args.proposal_steps or steps
 
     ee_events = []
@@ -635,6 +652,8 @@ def main():
                                                     "restarted every check_every steps"}
         if mlp is not None:
             line["config"]["proposal"] = {"mode": args.proposal, "tau": args.tau, "steps_per_round": prop_steps,
+                                          **({"heldout_planted_seed": args.heldout_seed}
+                                             if args.proposal == "heldout" else {}),
                                           **prop_log}
             line["plain_same_run"] = plain_cmp
         print(json.dumps(line), flush=True)
