@@ -100,21 +100,22 @@ def test_direct_relaxation_parity(gpu, name):
     assert ok.all(), (np.argwhere(~ok)[:5], g[~ok][:5], gref[~ok][:5])
 
 
-def test_fused_steps_equal_unfused(gpu):
-    """sat_steps = forward, backward, opt_update, bit for bit (Adam and GD)."""
+@pytest.mark.parametrize("act_dtype", ["f32", "bf16", "f16"])
+def test_fused_steps_equal_unfused(gpu, act_dtype):
+    """sat_steps = forward, backward, opt_update, bit for bit (Adam and GD), per activation type."""
     P, cnf, circ, plan, orc = _setup(INSTANCES["tseitin_small"]())
     B = 77
     for optname in ("adam", "gd"):
         opt = P.opt_params(optname, lr=0.05)
         V0 = torch.tensor(normal_logits(B, orc.n_pi, seed=5).T.copy(), device=gpu)
         Va, ma, va = V0.clone(), torch.zeros_like(V0), torch.zeros_like(V0)
-        act, adj = P.new_act(plan, B), P.new_adj(plan, B)
-        P.sat_steps(plan, opt, Va, ma, va, act, adj, 1, 7)
+        act, adj = P.new_act(plan, B, act_dtype), P.new_adj(plan, B)
+        P.sat_steps(plan, opt, Va, ma, va, act, adj, 1, 7, act_dtype=act_dtype)
         Vb, mb, vb = V0.clone(), torch.zeros_like(V0), torch.zeros_like(V0)
         gV = torch.zeros_like(V0)
         for t in range(1, 8):
-            P.sat_forward(plan, Vb, act)
-            P.sat_backward(plan, Vb, act, adj, gV)
+            P.sat_forward(plan, Vb, act, act_dtype=act_dtype)
+            P.sat_backward(plan, Vb, act, adj, gV, act_dtype=act_dtype)
             P.sat_opt_update(plan, opt, Vb, mb, vb, gV, t)
         torch.cuda.synchronize()
         assert torch.equal(Va, Vb), optname

@@ -97,7 +97,7 @@ def test_recompute_rows_shrink_and_sizes(gpu):
     assert plan.scratch_elems(128) == n_cone * 128
 
 
-@pytest.mark.parametrize("act_dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("act_dtype", ["f32", "bf16", "f16"])
 def test_recompute_full_waves_and_split_tail(gpu, act_dtype):
     """149 tiles: one full wave of one-CTA tiles plus a split tail; Adam with ages and GD."""
     P, cnf, circ, plan = _plan(tseitin_random_circuit(64, 640, 16, 8, seed=7).dimacs())
