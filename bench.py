@@ -45,6 +45,10 @@ WORKLOADS = {
                         batch=1024, steps=200, lr=0.1, init_scale=1.0, act_dtype="f32"),
     "tseitin1m_bf16": dict(kind="tseitin", n_pi=50000, n_gates=1000000, depth=200, n_out=256, seed=1,
                            batch=8192, steps=500, lr=0.1, init_scale=1.0, act_dtype="bf16"),
+    # the paper's own setting (plain GD, lr 10, 5 iterations, a large batch) on a synthetic stand-in
+    # of the size of its smallest instances (about 100 variables, 50 inputs, a few outputs)
+    "tseitin100_paper": dict(kind="tseitin", n_pi=50, n_gates=50, depth=5, n_out=4, seed=1,
+                             batch=1000000, steps=5, lr=10.0, init_scale=1.0, act_dtype="f32", optimizer="gd"),
 }
 ACT_BYTES = {"f32": 4, "bf16": 2, "f16": 2}
 
@@ -282,16 +286,19 @@ def cpu_baseline_entry(text, w, budget_s=15.0):
     probe = oracle_sample(text, w, 64, 20)
     per_sample_step = probe["seconds"] / (64 * 20)
     steps = w["steps"]
+    # the oracle holds FP64 state per sample and variable: keep it near 0.5 GB
+    n_vars = w.get("n_pi", 0) + w.get("n_gates", 0) or w.get("n_vars", 1)
+    cap = max(4096, min(1 << 20, int(5e8 / (8 * max(1, n_vars)))))
     n = int(max(4, min(1024, budget_s / max(per_sample_step * steps, 1e-9))))
     r = oracle_sample(text, w, n, steps)
-    if r["seconds"] < 0.5 * budget_s and n < 4096:
+    if r["seconds"] < 0.5 * budget_s and n < cap:
         # the short probe over-weights per-call work: rescale from the sized run once
-        n = int(max(n + 1, min(4096, n * budget_s / max(r["seconds"], 1e-3))))
+        n = int(max(n + 1, min(cap, n * budget_s / max(r["seconds"], 1e-3))))
         r = oracle_sample(text, w, n, steps)
     return {"value": r["unique"] / r["seconds"], "unit": "unique valid solutions/s", "cores": r["threads"],
             "kind": "oracle",
             "sample": f"{n} samples x {steps} {w.get('optimizer', 'adam')} steps (+verify) of the same workload, FP64, "
-                      f"{r['valid']} valid / {r['unique']} unique in {r['seconds']:.1f} s",
+                      f"{r['valid']} valid / {r['unique']} unique in {r['seconds']:.2f} s",
             "sample_steps_per_s": n * steps / r["seconds"]}
 
 
@@ -418,7 +425,7 @@ def main():
     ap.add_argument("--shuffle-clauses", action="store_true", help="the workload's CNF with its clauses shuffled")
     ap.add_argument("--reorder", action="store_true",
                     help="sort clauses by (largest variable, length, position) before Algorithm 1")
-    ap.add_argument("--optimizer", default="adam", choices=["adam", "gd"])
+    ap.add_argument("--optimizer", default=None, choices=["adam", "gd"], help="default: the workload's (Adam)")
     ap.add_argument("--recompute", type=int, default=0,
                     help="level-segment recomputation every K levels (0: store every activation)")
     ap.add_argument("--lr", type=float, default=0.0, help="override the workload's learning rate")
@@ -428,6 +435,7 @@ def main():
                     help="time only the proposal network's inference GEMMs (tcgen05) at the workload's batch")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
+    args.optimizer = args.optimizer or w.get("optimizer", "adam")
     w["collect_steps"] = w["steps"]  # training data for the proposal always comes from full-length rounds
     if args.batch:
         w["batch"] = args.batch
