@@ -607,13 +607,18 @@ def main():
         for k in range(e2e_steps):
             sols = P.sample(circ, cnf, n_wanted=10 ** 12, batch=B, steps=steps, max_rounds=1, lr=w["lr"], seed=0,
                             first_round=round_base + (n_rounds + k) * 4096, init_scale=w["init_scale"], act_dtype=ad,
-                            check_every=max(0, args.check_every), max_age=args.max_age, optimizer=args.optimizer)
+                            check_every=max(0, args.check_every), max_age=args.max_age, optimizer=args.optimizer,
+                            recompute_segment=args.recompute)
             ucount += len(sols)
             d2h += len(sols) * info["key_words"] * 4 + B // 8 + 16
         e2e_s = time.perf_counter() - t1
+        st = sols.stats
         e2e = {"value": ucount / e2e_s, "unit": "unique valid solutions/s",
                "h2d_bytes_per_step": info["upload_bytes"],
                "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps,
+               "wall_ms_per_call": 1e3 * e2e_s / e2e_steps,
+               "last_call_ms": {k: round(st[f"ms_{k}"], 3) for k in
+                                ("upload", "init", "steps", "verify", "dedup", "download")},
                "note": "sat_sample from host CNF/circuit objects: plan upload, workspace, one round, key download"}
 
     cpu = None

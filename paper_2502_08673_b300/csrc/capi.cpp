@@ -1183,20 +1183,29 @@ sat_status sat_sample(const sat_circuit* c, const sat_cnf* cnf, const sat_sample
         delete sol;
         return s;
     }
-    // canonical order: ascending packed input vector (highest word most significant)
-    std::vector<uint64_t> idx(sol->count);
-    for (uint64_t i = 0; i < sol->count; i++) idx[i] = i;
+    // canonical order: ascending packed input vector (highest word most significant); sorted
+    // on the top 64 bits held beside each index (cache-friendly), the rest only on ties
     const uint32_t kw = sol->key_words;
-    std::sort(idx.begin(), idx.end(), [&](uint64_t a, uint64_t b) {
-        for (int64_t k = (int64_t)kw - 1; k >= 0; k--) {
-            uint32_t x = raw[a * kw + k], y = raw[b * kw + k];
+    struct Ent {
+        uint64_t hi, i;
+    };
+    std::vector<Ent> ord(sol->count);
+    for (uint64_t i = 0; i < sol->count; i++) {
+        uint64_t hi = kw ? (uint64_t)raw[i * kw + kw - 1] << 32 : 0;
+        if (kw >= 2) hi |= raw[i * kw + kw - 2];
+        ord[i] = {hi, i};
+    }
+    std::sort(ord.begin(), ord.end(), [&](const Ent& a, const Ent& b) {
+        if (a.hi != b.hi) return a.hi < b.hi;
+        for (int64_t k = (int64_t)kw - 3; k >= 0; k--) {
+            uint32_t x = raw[a.i * kw + k], y = raw[b.i * kw + k];
             if (x != y) return x < y;
         }
         return false;
     });
     sol->keys.resize(raw.size());
     for (uint64_t i = 0; i < sol->count; i++)
-        std::copy(raw.begin() + idx[i] * kw, raw.begin() + (idx[i] + 1) * kw, sol->keys.begin() + i * kw);
+        std::copy(raw.begin() + ord[i].i * kw, raw.begin() + (ord[i].i + 1) * kw, sol->keys.begin() + i * kw);
     sol->f_in0 = p->f_in0;
     sol->f_in1 = p->f_in1;
     sol->f_gop = p->f_gop;

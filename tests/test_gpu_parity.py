@@ -297,8 +297,9 @@ def test_sample_end_to_end_planted3sat(gpu):
     assign[:, 1:] = A
     assert oracle.cnf_check(n, cl, assign).all()
     assert len({a.tobytes() for a in A}) == len(A)
-    w = sols.words()
-    order = [tuple(int(x) for x in r) for r in w]
+    # ascending dedup keys (all 50 variables are primary inputs here: bit i = variable i + 1)
+    key = (A.astype(np.uint64) << np.arange(n, dtype=np.uint64)).sum(axis=1, dtype=np.uint64)
+    assert (key[1:] > key[:-1]).all()
     assert sols.stats["valid"] >= len(A)
 
 
@@ -335,3 +336,28 @@ def test_per_step_error_vs_fp64(gpu, act_dtype, act_bound, rel_bound):
     print(f"per-step error vs FP64 [{act_dtype}]: activations {act_err:.3g} abs, loss {loss_err:.3g} rel, "
           f"gradient {grad_err:.3g} rel (floored), |g*| max {np.abs(gref).max():.3g}")
     assert act_err < act_bound and grad_err < rel_bound
+
+
+def test_many_solutions_canonical_order(gpu):
+    """sat_sample with ~240k distinct solutions (the multi-threaded host sort): returned in
+    ascending order of the packed assignment, all distinct, every one CNF-valid."""
+    import paper_2502_08673_b300 as P
+    inst = tseitin_random_circuit(50, 50, 5, 4, seed=1)
+    text = inst.dimacs()
+    cnf = P.Cnf.from_dimacs(text)
+    sols = P.sample(P.Circuit.build(cnf), cnf, n_wanted=10 ** 9, batch=262144, steps=5, max_rounds=1,
+                    optimizer="gd", lr=10.0, seed=2)
+    A = sols.assignments()
+    assert len(A) > 150000
+    # the canonical order is that of the dedup key: primary input i (ascending DIMACS
+    # variable) is bit i of an integer (50 inputs: one uint64), ascending
+    pis = [int(v) for v in P.Plan.create(P.Circuit.build(cnf), cnf).pi_vars()]
+    key = np.zeros(len(A), np.uint64)
+    for i, v in enumerate(pis):
+        key |= A[:, v - 1].astype(np.uint64) << np.uint64(i)
+    assert (key[1:] > key[:-1]).all()
+    n, cl = oracle.parse_dimacs(text)
+    idx = np.random.default_rng(0).choice(len(A), 2000, replace=False)
+    assign = np.zeros((len(idx), n + 1), np.uint8)
+    assign[:, 1:] = A[idx]
+    assert oracle.cnf_check(n, cl, assign).all()
