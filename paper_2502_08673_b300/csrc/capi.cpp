@@ -1178,34 +1178,45 @@ sat_status sat_sample(const sat_circuit* c, const sat_cnf* cnf, const sat_sample
     sol->n_pi = p->info.n_pi;
     sol->key_words = p->info.key_words;
     sol->count = acc.unique;
-    std::vector<uint32_t> raw(sol->count * sol->key_words);
-    if ((s = sat_dedup_copy_keys(pg.d, 0, sol->count, raw.data(), o->stream)) != SAT_OK) {
-        delete sol;
-        return s;
-    }
-    // canonical order: ascending packed input vector (highest word most significant); sorted
-    // on the top 64 bits held beside each index (cache-friendly), the rest only on ties
+    // canonical order: ascending packed input vector (highest word most significant), sorted
+    // on the device by the top 64 bits; keys that share them are ordered here
     const uint32_t kw = sol->key_words;
-    struct Ent {
-        uint64_t hi, i;
-    };
-    std::vector<Ent> ord(sol->count);
-    for (uint64_t i = 0; i < sol->count; i++) {
-        uint64_t hi = kw ? (uint64_t)raw[i * kw + kw - 1] << 32 : 0;
-        if (kw >= 2) hi |= raw[i * kw + kw - 2];
-        ord[i] = {hi, i};
-    }
-    std::sort(ord.begin(), ord.end(), [&](const Ent& a, const Ent& b) {
-        if (a.hi != b.hi) return a.hi < b.hi;
-        for (int64_t k = (int64_t)kw - 3; k >= 0; k--) {
-            uint32_t x = raw[a.i * kw + k], y = raw[b.i * kw + k];
-            if (x != y) return x < y;
+    sol->keys.resize(sol->count * kw);
+    if (sol->count > 0) {
+        Workspace ow;
+        uint64_t* hi = nullptr;
+        uint32_t *idx = nullptr, *sorted = nullptr;
+        const uint64_t n2 = sat::key_order_pad(sol->count);
+        if (!ow.alloc((void**)&hi, n2 * 8) || !ow.alloc((void**)&idx, n2 * 4) ||
+            !ow.alloc((void**)&sorted, sol->count * kw * 4)) {
+            delete sol;
+            return fail(SAT_ERR_OOM, "cudaMalloc failed for the solution order");
         }
-        return false;
-    });
-    sol->keys.resize(raw.size());
-    for (uint64_t i = 0; i < sol->count; i++)
-        std::copy(raw.begin() + ord[i].i * kw, raw.begin() + (ord[i].i + 1) * kw, sol->keys.begin() + i * kw);
+        cudaError_t e = sat::launch_key_order(pg.d->d.pool, (int)kw, sol->count, hi, idx, sorted, S(o->stream));
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(sol->keys.data(), sorted, sol->count * kw * 4, cudaMemcpyDeviceToHost, S(o->stream));
+        if (e == cudaSuccess) e = cudaStreamSynchronize(S(o->stream));
+        if (e != cudaSuccess) {
+            delete sol;
+            return fail(SAT_ERR_CUDA, std::string("solution order: ") + cudaGetErrorString(e));
+        }
+        if (kw > 2) {  // runs with equal top 64 bits: full-key order
+            auto row = [&](uint64_t i) { return sol->keys.data() + i * kw; };
+            for (uint64_t a = 0; a < sol->count;) {
+                uint64_t b = a + 1;
+                while (b < sol->count && row(b)[kw - 1] == row(a)[kw - 1] && row(b)[kw - 2] == row(a)[kw - 2]) b++;
+                if (b - a > 1) {
+                    std::vector<std::vector<uint32_t>> run;
+                    for (uint64_t i = a; i < b; i++) run.emplace_back(row(i), row(i) + kw);
+                    std::sort(run.begin(), run.end(), [&](const std::vector<uint32_t>& x, const std::vector<uint32_t>& y) {
+                        return std::lexicographical_compare(x.rbegin(), x.rend(), y.rbegin(), y.rend());
+                    });
+                    for (uint64_t i = a; i < b; i++) std::copy(run[i - a].begin(), run[i - a].end(), row(i));
+                }
+                a = b;
+            }
+        }
+    }
     sol->f_in0 = p->f_in0;
     sol->f_in1 = p->f_in1;
     sol->f_gop = p->f_gop;

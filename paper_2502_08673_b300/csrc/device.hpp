@@ -122,6 +122,13 @@ struct DevDedup {
 };
 
 cudaError_t launch_dedup_clear(DevDedup& d, cudaStream_t s);
+
+// Canonical order of n keys (kw uint32 words each, the highest word most significant):
+// out[j] = keys[order[j]], ascending by the top 64 bits, ties by position (full-key order
+// within a tie is left to the caller).  Scratch: hi, idx of key_order_pad(n) entries.
+uint64_t key_order_pad(uint64_t n);
+cudaError_t launch_key_order(const uint32_t* keys, int kw, uint64_t n, uint64_t* hi, uint32_t* idx, uint32_t* out,
+                             cudaStream_t s);
 // slot_of: scratch [B] (slot taken by each sample, or ~0).
 cudaError_t launch_dedup_insert(DevDedup& d, const uint32_t* keys, const uint32_t* valid, int64_t B,
                                 unsigned long long* hashes, uint8_t* is_new, unsigned long long* slot_of,

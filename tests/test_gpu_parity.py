@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import oracle
-from workloads import tseitin_random_circuit, planted_3sat, fig1_example_dimacs, normal_logits
+from workloads import tseitin_random_circuit, planted_3sat, fig1_example_dimacs, normal_logits, dimacs_text
 
 pytestmark = pytest.mark.gpu
 
@@ -361,3 +361,23 @@ def test_many_solutions_canonical_order(gpu):
     assign = np.zeros((len(idx), n + 1), np.uint8)
     assign[:, 1:] = A[idx]
     assert oracle.cnf_check(n, cl, assign).all()
+
+
+def test_canonical_order_with_equal_top_bits(gpu):
+    """Keys longer than 64 bits whose top 64 bits all agree (inputs 65..100 fixed by unit
+    clauses, 1..64 free): the device orders by the top 64 bits, the host by the full key."""
+    import paper_2502_08673_b300 as P
+    rng = np.random.default_rng(4)
+    fixed = {v: int(rng.integers(0, 2)) for v in range(65, 101)}
+    text = dimacs_text(100, [[v if b else -v] for v, b in fixed.items()])
+    cnf = P.Cnf.from_dimacs(text)
+    circ = P.Circuit.build(cnf)
+    sols = P.sample(circ, cnf, n_wanted=10 ** 9, batch=4096, steps=60, max_rounds=1, seed=1)
+    A = sols.assignments()
+    assert len(A) > 1000
+    assert all((A[:, v - 1] == b).all() for v, b in fixed.items())
+    pis = [int(v) for v in P.Plan.create(circ, cnf).pi_vars()]
+    assert pis == list(range(1, 101))
+    # full 100-bit keys as Python integers, ascending and distinct
+    keys = [int("".join(str(int(b)) for b in row[::-1]), 2) for row in A]
+    assert all(a < b for a, b in zip(keys, keys[1:]))
