@@ -1182,7 +1182,7 @@ sat_status sat_sample(const sat_circuit* c, const sat_cnf* cnf, const sat_sample
     // on the device by the top 64 bits; keys that share them are ordered here
     const uint32_t kw = sol->key_words;
     sol->keys.resize(sol->count * kw);
-    if (sol->count > 0) {
+    if (sol->count > 0 && kw > 0) {
         Workspace ow;
         uint64_t* hi = nullptr;
         uint32_t *idx = nullptr, *sorted = nullptr;

@@ -35,8 +35,8 @@ __global__ void key_prefix_kernel(const uint32_t* keys, int kw, uint64_t n, uint
     }
 }
 
-// Compare-exchange of elements i and i + j for one (k, j) stage with j >= SORT_BLOCK / 2
-// ... of the network: ascending where (i & k) == 0.
+// One (k, j) stage of the network whose pairs (i, i + j) span more than a shared-memory
+// block: compare-exchange, ascending where (i & k) == 0.
 __global__ void bitonic_global_kernel(uint64_t* hi, uint32_t* idx, uint64_t n2, uint64_t k, uint64_t j) {
     for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n2 / 2; p += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t i = (p / j) * 2 * j + (p % j), l = i + j;
@@ -111,7 +111,7 @@ uint64_t key_order_pad(uint64_t n) {
 
 cudaError_t launch_key_order(const uint32_t* keys, int kw, uint64_t n, uint64_t* hi, uint32_t* idx, uint32_t* out,
                              cudaStream_t s) {
-    if (n == 0) return cudaSuccess;
+    if (n == 0 || kw <= 0) return cudaSuccess;
     const uint64_t n2 = key_order_pad(n);
     key_prefix_kernel<<<grid_for(n2, 256), 256, 0, s>>>(keys, kw, n, n2, hi, idx);
     const uint64_t m = n2 < (uint64_t)SORT_BLOCK ? n2 : (uint64_t)SORT_BLOCK;
