@@ -105,3 +105,18 @@ def test_zero_step_budget_and_corrupt_cnf(gpu):
             P.Cnf.from_dimacs(bad)
         assert e.value.status == SAT_ERR_PARSE
     _device_still_works(P, gpu)
+
+
+def test_degenerate_instances_end_to_end(gpu):
+    """No variables at all; and free variables without clauses, where every assignment is a
+    solution and the sampler returns each of the 2^3 exactly once, in canonical order."""
+    import paper_2502_08673_b300 as P
+    cnf = P.Cnf.from_dimacs("p cnf 0 0\n")
+    sols = P.sample(P.Circuit.build(cnf), cnf, n_wanted=5, batch=64, steps=3, max_rounds=2)
+    assert len(sols) <= 1
+    cnf = P.Cnf.from_dimacs("p cnf 3 0\n")
+    sols = P.sample(P.Circuit.build(cnf), cnf, n_wanted=8, batch=1024, steps=3, max_rounds=3, seed=5)
+    A = sols.assignments()
+    assert len(A) == 8
+    key = A.astype(np.int64) @ (1 << np.arange(3))
+    assert key.tolist() == list(range(8))
