@@ -886,7 +886,12 @@ void sat_sample_opts_default(sat_sample_opts* o) {
 
 namespace {
 
+// Device buffers of one call, stream-ordered (cudaMallocAsync / cudaFreeAsync on the
+// call's stream, from the device's default pool): freeing does not synchronise the
+// device, so calls on other streams keep running.
 struct Workspace {
+    explicit Workspace(cudaStream_t s) : stream(s) {}
+    cudaStream_t stream;
     std::vector<void*> bufs;
     float *V = nullptr, *m = nullptr, *v = nullptr, *adj = nullptr;
     void* act = nullptr;
@@ -894,11 +899,11 @@ struct Workspace {
     int64_t ldw = 0;
     const sat::DevAct* lay = nullptr;  // act layout of the fused steps
     ~Workspace() {
-        for (void* b : bufs) cudaFree(b);
+        for (void* b : bufs) cudaFreeAsync(b, stream);
     }
     bool alloc(void** p, size_t n) {
         if (n == 0) n = 16;
-        if (cudaMalloc(p, n) != cudaSuccess) {
+        if (cudaMallocAsync(p, n, stream) != cudaSuccess) {
             cudaGetLastError();
             return false;
         }
@@ -1057,7 +1062,7 @@ sat_status sat_sample_plan(const sat_plan* p, sat_dedup* d, const sat_sample_opt
     if (s != SAT_OK) return s;
     cudaStream_t str = S(o->stream);
     const sat::DevPlan& dp = p->dp;
-    Workspace w;
+    Workspace w(str);
     if ((s = plan_layout(p, o->recompute_segment, &w.lay)) != SAT_OK) return s;
     w.ldw = (B + 31) / 32;
     const size_t npi = (size_t)dp.n_pi;
@@ -1183,7 +1188,7 @@ sat_status sat_sample(const sat_circuit* c, const sat_cnf* cnf, const sat_sample
     const uint32_t kw = sol->key_words;
     sol->keys.resize(sol->count * kw);
     if (sol->count > 0 && kw > 0) {
-        Workspace ow;
+        Workspace ow(S(o->stream));
         uint64_t* hi = nullptr;
         uint32_t *idx = nullptr, *sorted = nullptr;
         const uint64_t n2 = sat::key_order_pad(sol->count);
