@@ -83,52 +83,44 @@ template <> struct ActIO<float> {
         else *reinterpret_cast<float2*>(p) = make_float2(x.v[0], x.v[1]);
     }
 };
-// Two 16-bit values per 32-bit word; ldcg reads the lane's VEC values through L2 only.
+// 16-bit storage: a lane's VEC = 4 values are one 8-byte word (two 16-bit pairs), moved
+// with one load or store; ldcg reads them through L2 only.
 template <typename H, typename H2>
-__device__ __forceinline__ VF ld16_cg(const H* p, float2 (*cvt)(H2)) {
-    VF r;
-#pragma unroll
-    for (int q = 0; q < VEC; q += 2) {
-        const unsigned u = __ldcg(reinterpret_cast<const unsigned*>(p) + q / 2);
-        const float2 f = cvt(*reinterpret_cast<const H2*>(&u));
-        r.v[q] = f.x; r.v[q + 1] = f.y;
-    }
-    return r;
-}
-template <> struct ActIO<__nv_bfloat16> {
-    static __device__ __forceinline__ VF ld(const __nv_bfloat16* p) {
+struct ActIO16 {
+    static_assert(VEC == 4, "one 8-byte word per lane");
+    static __device__ __forceinline__ VF unpack(uint2 u, float2 (*cvt)(H2)) {
+        const float2 a = cvt(*reinterpret_cast<const H2*>(&u.x)), b = cvt(*reinterpret_cast<const H2*>(&u.y));
         VF r;
-#pragma unroll
-        for (int q = 0; q < VEC; q += 2) {
-            const float2 f = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(p)[q / 2]);
-            r.v[q] = f.x; r.v[q + 1] = f.y;
-        }
+        r.v[0] = a.x; r.v[1] = a.y; r.v[2] = b.x; r.v[3] = b.y;
         return r;
     }
+    static __device__ __forceinline__ uint2 pack(const VF& x, H2 (*cvt)(float2)) {
+        const H2 a = cvt(make_float2(x.v[0], x.v[1])), b = cvt(make_float2(x.v[2], x.v[3]));
+        return make_uint2(*reinterpret_cast<const unsigned*>(&a), *reinterpret_cast<const unsigned*>(&b));
+    }
+};
+template <> struct ActIO<__nv_bfloat16> {
+    using IO = ActIO16<__nv_bfloat16, __nv_bfloat162>;
+    static __device__ __forceinline__ VF ld(const __nv_bfloat16* p) {
+        return IO::unpack(*reinterpret_cast<const uint2*>(p), __bfloat1622float2);
+    }
     static __device__ __forceinline__ VF ldcg(const __nv_bfloat16* p) {
-        return ld16_cg<__nv_bfloat16, __nv_bfloat162>(p, __bfloat1622float2);
+        return IO::unpack(__ldcg(reinterpret_cast<const uint2*>(p)), __bfloat1622float2);
     }
     static __device__ __forceinline__ void st(__nv_bfloat16* p, const VF& x) {
-#pragma unroll
-        for (int q = 0; q < VEC; q += 2)
-            reinterpret_cast<__nv_bfloat162*>(p)[q / 2] = __float22bfloat162_rn(make_float2(x.v[q], x.v[q + 1]));
+        *reinterpret_cast<uint2*>(p) = IO::pack(x, __float22bfloat162_rn);
     }
 };
 template <> struct ActIO<__half> {
+    using IO = ActIO16<__half, __half2>;
     static __device__ __forceinline__ VF ld(const __half* p) {
-        VF r;
-#pragma unroll
-        for (int q = 0; q < VEC; q += 2) {
-            const float2 f = __half22float2(reinterpret_cast<const __half2*>(p)[q / 2]);
-            r.v[q] = f.x; r.v[q + 1] = f.y;
-        }
-        return r;
+        return IO::unpack(*reinterpret_cast<const uint2*>(p), __half22float2);
     }
-    static __device__ __forceinline__ VF ldcg(const __half* p) { return ld16_cg<__half, __half2>(p, __half22float2); }
+    static __device__ __forceinline__ VF ldcg(const __half* p) {
+        return IO::unpack(__ldcg(reinterpret_cast<const uint2*>(p)), __half22float2);
+    }
     static __device__ __forceinline__ void st(__half* p, const VF& x) {
-#pragma unroll
-        for (int q = 0; q < VEC; q += 2)
-            reinterpret_cast<__half2*>(p)[q / 2] = __float22half2_rn(make_float2(x.v[q], x.v[q + 1]));
+        *reinterpret_cast<uint2*>(p) = IO::pack(x, __float22half2_rn);
     }
 };
 
