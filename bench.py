@@ -179,18 +179,20 @@ def measured_peaks():
     return 6400.0, "fallback"
 
 
-def profile_traffic(workload, act_dtype):
-    """Per-step DRAM bytes of the fused step kernel from the committed ncu summary,
-    or None when absent or taken on a different kernel source."""
+def profile_traffic(workload, act_dtype, B=None, steps=None):
+    """DRAM bytes of the fused step kernel from the committed ncu summary: per sample-step
+    (one-wave capture), and per round when the summary holds the full-size launch list of
+    this batch and step count; None when absent or taken on a different kernel source."""
     f = ROOT / "profiles" / f"steps_kernel_{workload}.md"
     if not f.exists():
-        return None, None
+        return None, None, None
     text = f.read_text()
     m = re.search(r"dram_bytes_per_sample_step:\s*([0-9.eE+]+)", text)
     h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
     if not m or not h or h.group(1) != kernel_source_hash():
-        return None, None
-    return float(m.group(1)), f.name
+        return None, None, None
+    r = re.search(rf"dram_bytes_per_round_b{B}_s{steps}:\s*([0-9.eE+]+)", text) if B and steps else None
+    return float(m.group(1)), (float(r.group(1)) if r else None), f.name
 
 
 def step_kernel_launches(B, torch):
@@ -571,7 +573,7 @@ def main():
     alg = algorithmic_bytes_per_step(info, B, ad, args.recompute) * (launch_steps or run_steps)
     kavg = statistics.mean(kernel_ms)
     achieved = alg / (kavg / 1e3) / 1e9
-    dram_per_sample_step, prof = profile_traffic(args.workload, ad)
+    dram_per_sample_step, dram_per_round, prof = profile_traffic(args.workload, ad, B, launch_steps or run_steps)
 
     plain_cmp = None
     if mlp is not None:
@@ -646,7 +648,9 @@ def main():
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "kernel": "steps_kernel", "kernel_ms_avg": kavg,
                          "algorithmic_bytes_per_launch": alg,
-                         "traffic": (dram_per_sample_step * B * steps) if dram_per_sample_step else None,
+                         "traffic": (dram_per_round if dram_per_round else
+                                     (dram_per_sample_step * B * (launch_steps or run_steps))
+                                     if dram_per_sample_step else None),
                          "traffic_source": prof},
             "gpu_launches": ((7 + step_kernel_launches(B, torch)) * args.steps if args.check_every <= 0
                              else (8 + step_kernel_launches(B, torch)) * len(ee_events)),
