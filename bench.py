@@ -54,20 +54,17 @@ ACT_BYTES = {"f32": 4, "bf16": 2, "f16": 2}
 
 
 def instance_text(w, planted_seed=None):
-    from workloads import tseitin_random_circuit, planted_3sat
+    from workloads import tseitin_random_circuit, planted_3sat, dimacs_text
     if w["kind"] == "tseitin":
-        text = tseitin_random_circuit(w["n_pi"], w["n_gates"], w["depth"], w["n_out"], seed=w["seed"],
-                                      planted_seed=planted_seed).dimacs()
+        inst = tseitin_random_circuit(w["n_pi"], w["n_gates"], w["depth"], w["n_out"], seed=w["seed"],
+                                      planted_seed=planted_seed)
     else:
-        text = planted_3sat(w["n_vars"], w["n_clauses"], w["seed"]).dimacs()
+        inst = planted_3sat(w["n_vars"], w["n_clauses"], w["seed"])
     if w.get("shuffle_clauses"):
         # the same CNF with its clauses in a seeded random order (out-of-order files)
         import random
-        from oracle.dimacs import parse_dimacs
-        from workloads import dimacs_text
-        n, cl = parse_dimacs(text)
-        text = dimacs_text(n, random.Random(w["seed"]).sample(cl, len(cl)))
-    return text
+        return dimacs_text(inst.n_vars, random.Random(w["seed"]).sample(inst.clauses, len(inst.clauses)))
+    return inst.dimacs()
 
 
 def train_proposal(P, torch, plan, w, mode, B, opt, ad, log, train_steps=0, rounds=0):
