@@ -30,9 +30,9 @@
  *    starts at element t * rows * SAT_TILE, so an array holds
  *    ceil(B/SAT_TILE) * rows * SAT_TILE elements.  act: rows = n_cone (row =
  *    cone node) or, under recomputation, the rows of that layout; adj: the input
- *    level plus a ring of max_span + 1 gate levels (sat_plan_layout_elems gives
- *    both; sat_plan_scratch_elems, n_cone rows, is enough for either array
- *    without recomputation).  The padding samples of the last tile are written
+ *    level, a ring of max_span + 1 gate levels and one row of seed scales
+ *    (sat_plan_layout_elems gives both; sat_plan_scratch_elems is enough for
+ *    either array without recomputation).  The padding samples of the last tile are written
  *    too.  act holds act_dtype elements, adj float32; both must be 16-byte
  *    aligned.
  *  - Deterministic for a given (seed, options, GPU).
@@ -159,7 +159,8 @@ sat_status sat_plan_status(const sat_plan* p, uint32_t* status, int32_t clear, v
  * normally: the context stays usable.  Synchronises `stream`. */
 sat_status sat_diag_bounded_wait(uint32_t limit_us, uint32_t* status, void* stream);
 /* Elements of one act / adj scratch array for a batch of B samples (enough for
- * either array under every call that takes them without a segment). */
+ * either array under every call that takes them without a segment: max(n_cone,
+ * adj rows) rows per tile). */
 sat_status sat_plan_scratch_elems(const sat_plan* p, int64_t B, uint64_t* elems);
 /* Exact sizes: act_elems (nullable) = elements of the act array of the fused steps
  * with recomputation segment `segment` (0 = every level stored: the layout of

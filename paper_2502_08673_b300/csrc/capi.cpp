@@ -320,10 +320,13 @@ sat_status sat_plan_create(const sat_circuit* c, const sat_cnf* cnf, sat_plan** 
         } else {
             d.n_adj_rows = (int64_t)P.n_cone;
         }
+        d.seed_row = (int32_t)d.n_adj_rows;  // one more row: the seeds' scale, written per backward pass
+        d.n_adj_rows += 1;
     }
     std::vector<int4> fe(P.fo_g.size());
     {
-        // edge record: consumer's adj row, sibling, and the partial's coefficients c0, c1 as float bits
+        // edge record: consumer's adj row (the seed row for an output seed or a zero edge), sibling,
+        // and the partial's coefficients c0, c1 as float bits
         std::vector<int32_t> adj_row(P.n_cone);
         for (uint32_t i = 0; i < P.n_cone_pi; i++) adj_row[i] = (int32_t)i;
         for (int32_t l = 1; l <= d.n_clev; l++)
@@ -334,7 +337,7 @@ sat_status sat_plan_create(const sat_circuit* c, const sat_cnf* cnf, sat_plan** 
             int32_t i0, i1;
             std::memcpy(&i0, &c0, 4);
             std::memcpy(&i1, &c1, 4);
-            fe[e] = make_int4(P.fo_g[e] < 0 ? -1 : adj_row[P.fo_g[e]], P.fo_sib[e], i0, i1);
+            fe[e] = make_int4(P.fo_g[e] < 0 ? d.seed_row : adj_row[P.fo_g[e]], P.fo_sib[e], i0, i1);
         }
     }
     // bit 31 of the sibling field marks the last edge of each node's range
@@ -442,7 +445,8 @@ sat_status sat_plan_get_info(const sat_plan* p, sat_plan_info* info) {
 
 sat_status sat_plan_scratch_elems(const sat_plan* p, int64_t B, uint64_t* elems) {
     if (!p || !elems || B < 0) return fail(SAT_ERR_ARG, "bad argument");
-    *elems = (uint64_t)((B + SAT_TILE_SAMPLES - 1) / SAT_TILE_SAMPLES) * p->info.n_cone * SAT_TILE_SAMPLES;
+    const uint64_t rows = std::max<uint64_t>(p->info.n_cone, (uint64_t)p->dp.n_adj_rows);
+    *elems = (uint64_t)((B + SAT_TILE_SAMPLES - 1) / SAT_TILE_SAMPLES) * rows * SAT_TILE_SAMPLES;
     return SAT_OK;
 }
 

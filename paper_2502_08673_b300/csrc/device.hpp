@@ -34,13 +34,14 @@ struct DevPlan {
     const int2* c_gate = nullptr;       // per cone gate: (in0 | gop << 28, in1)
     const int32_t* cone_pi_row = nullptr;
     const int32_t* fo_off = nullptr;    // [n_cone + 1]
-    const int4* fo_edge = nullptr;      // (consumer's adj row or -1, sibling | last-edge-of-node << 31, c0 bits, c1 bits)
+    const int4* fo_edge = nullptr;      // (consumer's adj row (seed_row for seeds), sibling | last << 31, c0 bits, c1 bits)
     // Adjoint scratch rows of a tile: level 0 (the cone inputs) in rows [0, n_cone_pi); a
     // gate level l is live only until the backward pass has finished level l - max_span, so
     // with adj_slots > 0 level l >= 1 occupies slot (l - 1) % adj_slots of a ring of
     // adj_slots = max_span + 1 slots of adj_slot_rows rows each (adj_slots = 0: row = node).
     int64_t n_adj_rows = 0;
     int32_t adj_slots = 0, adj_slot_rows = 0;
+    int32_t seed_row = 0;               // last adj row: the output seeds' scale (the consumer row of seed edges)
     int32_t n_out = 0;
     const int32_t* c_out_node = nullptr;
     const float* out_target = nullptr;

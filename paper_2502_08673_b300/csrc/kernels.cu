@@ -550,7 +550,8 @@ __device__ void tile_loss(const DevPlan& p, const DevAct& L, const T* act, float
 // Adjoints of cone nodes [lo, hi) (gather form of Eq. 8): each warp takes a
 // contiguous run of nodes, whose fan-out edges are contiguous in the CSR and
 // are summed in CSR order.  An edge contributes ga * (c0 + c1 * A_sibling)
-// with ga the consumer's adjoint, or seed_scale for an output seed.  The
+// with ga the consumer's adjoint row, or for an output seed the seed row (the
+// per-sample weight of the loss, written at the start of the backward pass).  The
 // consumer-adjoint and sibling rows are gathered into shared memory (one
 // gather4 load each per CHUNK = 4 edges).
 // This warp's node run [u0, u1) of a cone level with the CSR offsets of its first
@@ -582,7 +583,7 @@ __device__ __forceinline__ AdjRun adj_run(const DevPlan& p, const DevAct& L, int
 
 template <typename T>
 __device__ void level_adjoint(const DevPlan& p, const DevAct& L, const AdjRun& run, const T* act, float* adj,
-                              const VF& seed_scale, Stage& st, const RowMaps& rm, const TileCtx& c) {
+                              Stage& st, const RowMaps& rm, const TileCtx& c) {
     constexpr int ROWB = TILE * (int)sizeof(T);
     constexpr int ROWF = TILE * 4;
     constexpr int SLOT = slot_bytes<T>();
@@ -604,8 +605,8 @@ __device__ void level_adjoint(const DevPlan& p, const DevAct& L, const AdjRun& r
                 if (c.lane < cnt) mine = __ldg(&L.edge[base + c.lane]);
             }
             const int nch = (cnt + CHUNK - 1) / CHUNK;
-            // per lane (= edge of the batch): tensor-map rows of the consumer adjoint (an
-            // output seed, which has none, loads a stand-in row) and of the sibling
+            // per lane (= edge of the batch): tensor-map rows of the consumer adjoint (the
+            // seed row for an output seed) and of the sibling
             const int g_row = rm.grow0 + max(mine.x, 0), s_row = rm.arow0 + (mine.y & 0x7FFFFFFF);
             // edges that close their node's sum (the node's adjoint row is stored there)
             const unsigned last_mask = __ballot_sync(FULL, c.lane < cnt && mine.y < 0);
@@ -636,12 +637,10 @@ __device__ void level_adjoint(const DevPlan& p, const DevAct& L, const AdjRun& r
 #pragma unroll
                 for (int j = 0; j < CHUNK; j++) {
                     const int el = ch * CHUNK + j;  // < 32: at most 8 chunks of a batch
-                    const int gx = __shfl_sync(FULL, mine.x, el);
                     const float c0 = __int_as_float(__shfl_sync(FULL, mine.z, el));
                     const float c1 = __int_as_float(__shfl_sync(FULL, mine.w, el));
                     if (el < cnt) {
-                        const VF ga = gx < 0 ? seed_scale
-                                             : ActIO<float>::ld(reinterpret_cast<const float*>(sb + j * ROWF) + c.lane * VEC);
+                        const VF ga = ActIO<float>::ld(reinterpret_cast<const float*>(sb + j * ROWF) + c.lane * VEC);
                         const VF sv =
                             ActIO<T>::ld(reinterpret_cast<const T*>(sb + CHUNK * ROWF + j * ROWB) + c.lane * VEC);
 #pragma unroll
@@ -722,10 +721,16 @@ __device__ void tile_backward(const DevPlan& p, const DevAct& L, const OptParams
                               float* gV, int64_t ldv, T* act, float* adj, const float* grad_loss,
                               const AdamCorr& ac, Stage& st, const float4* gcoef, const RowMaps& rm,
                               const TileCtx& c) {
-    VF seed_scale = vf_fill(1.0f);
-    if (grad_loss != nullptr)
+    // the seed row: each sample's weight of its loss (1, or grad_loss), read by the seed edges
+    if (c.warp == 0 && c.rank == 0) {
+        VF seed_scale = vf_fill(1.0f);
+        if (grad_loss != nullptr)
 #pragma unroll
-        for (int q = 0; q < VEC; q++) seed_scale.v[q] = q < c.nvalid ? grad_loss[c.b + q] : 0.0f;
+            for (int q = 0; q < VEC; q++) seed_scale.v[q] = q < c.nvalid ? grad_loss[c.b + q] : 0.0f;
+        ActIO<float>::st(adj + at(p.seed_row, c), seed_scale);
+    }
+    fence_async_global();
+    level_sync(c);
     const int top_seg = L.k > 0 && p.n_clev > 0 ? (p.n_clev - 1) / L.k : 0;
     AdjRun run = adj_run(p, L, p.n_clev, c);
     for (int l = p.n_clev; l >= 0; l--) {
@@ -733,7 +738,7 @@ __device__ void tile_backward(const DevPlan& p, const DevAct& L, const OptParams
             const int j = (l - 1) / L.k;
             if (j + 2 <= top_seg) forward_levels<T>(p, L, act, st, gcoef, rm, c, j * L.k + 1, l, true);
         }
-        level_adjoint<T>(p, L, run, act, adj, seed_scale, st, rm, c);
+        level_adjoint<T>(p, L, run, act, adj, st, rm, c);
         if (l > 0) run = adj_run(p, L, l - 1, c);
         fence_async_global();
         level_sync(c);
