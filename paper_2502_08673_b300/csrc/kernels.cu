@@ -312,6 +312,7 @@ __device__ __forceinline__ void fence_async_global() { asm volatile("fence.proxy
 struct Stage {
     char* buf;
     uint64_t* bar;
+    int* rows;            // [2][32]: the tensor-map rows of the current batch's two operands
     uint32_t parity;      // bit s: parity of the next completion of slot s
     unsigned* status;     // plan status word (device)
     bool poisoned;        // a wait expired: stop waiting, results are invalid
@@ -325,11 +326,16 @@ __host__ __device__ constexpr int slot_bytes() {
                ? (2 * CHUNK * TILE * (int)sizeof(T))
                : (CHUNK * TILE * 4 + CHUNK * TILE * (int)sizeof(T));
 }
-// Per-warp stride, rounded to 128 bytes so every slot (and every bulk-copy
-// destination inside it) stays 16-byte aligned for every warp.
+// Per warp: NSLOT slots, their mbarriers, and the batch's row table (2 x 32 int32,
+// 16-byte aligned for int4 reads); the stride is rounded to 128 bytes so every slot (and
+// every bulk-copy destination inside it) stays 16-byte aligned for every warp.
+template <typename T>
+__host__ __device__ constexpr int stage_rows_offset() {
+    return (NSLOT * slot_bytes<T>() + NSLOT * 8 + 15) / 16 * 16;
+}
 template <typename T>
 __host__ __device__ constexpr int warp_stage_bytes() {
-    return (NSLOT * slot_bytes<T>() + NSLOT * 8 + 127) / 128 * 128;
+    return (stage_rows_offset<T>() + 2 * 32 * 4 + 127) / 128 * 128;
 }
 
 template <typename T>
@@ -337,6 +343,7 @@ __device__ __forceinline__ Stage make_stage(char* smem, unsigned* status, const 
     Stage st;
     st.buf = smem + c.warp * warp_stage_bytes<T>();
     st.bar = reinterpret_cast<uint64_t*>(st.buf + NSLOT * slot_bytes<T>());
+    st.rows = reinterpret_cast<int*>(st.buf + stage_rows_offset<T>());
     st.parity = 0;
     st.status = status;
     st.poisoned = false;
@@ -462,25 +469,27 @@ __device__ void forward_levels(const DevPlan& p, const DevAct& L, T* act, Stage&
                 if (c.lane < cnt) mine = __ldg(&L.gate[base + c.lane - p.n_cone_pi]);
             }
             const int nch = (cnt + CHUNK - 1) / CHUNK;
-            // per lane (= gate of the batch): tensor-map rows of both inputs and the gate code
-            const int x_row = rm.arow0 + (mine.x & 0x0FFFFFFF), y_row = rm.arow0 + mine.y;
+            // per lane (= gate of the batch): tensor-map rows of both inputs, into the warp's
+            // row table (lanes past cnt repeat the last gate, so a partial chunk does too), and
+            // the gate code
+            {
+                const int x_row = rm.arow0 + (mine.x & 0x0FFFFFFF), y_row = rm.arow0 + mine.y;
+                const int x_last = __shfl_sync(FULL, x_row, cnt - 1), y_last = __shfl_sync(FULL, y_row, cnt - 1);
+                st.rows[c.lane] = c.lane < cnt ? x_row : x_last;
+                st.rows[32 + c.lane] = c.lane < cnt ? y_row : y_last;
+                __syncwarp();
+            }
             const int gop_mine = (int)((uint32_t)mine.x >> 28);
             T* out = act + at(base + orow, c);
             auto issue = [&](int ch) {
                 const int s = ch % NSLOT;
                 // first inputs of the chunk's 4 gates -> rows 0..3, second inputs -> rows 4..7
-                // (a partial chunk repeats its last gate; gate indices stay below 32)
-                int xr[CHUNK], yr[CHUNK];
-#pragma unroll
-                for (int j = 0; j < CHUNK; j++) {
-                    const int gl = min(ch * CHUNK + j, cnt - 1);
-                    xr[j] = __shfl_sync(FULL, x_row, gl);
-                    yr[j] = __shfl_sync(FULL, y_row, gl);
-                }
                 if (c.lane == 0) {
+                    const int4 xr = *reinterpret_cast<const int4*>(st.rows + ch * CHUNK);
+                    const int4 yr = *reinterpret_cast<const int4*>(st.rows + 32 + ch * CHUNK);
                     mbar_expect_tx(st.bar + s, (uint32_t)(2 * CHUNK * ROWB));
-                    gather4(st.buf + s * SLOT, rm.act, xr[0], xr[1], xr[2], xr[3], st.bar + s);
-                    gather4(st.buf + s * SLOT + CHUNK * ROWB, rm.act, yr[0], yr[1], yr[2], yr[3], st.bar + s);
+                    gather4(st.buf + s * SLOT, rm.act, xr.x, xr.y, xr.z, xr.w, st.bar + s);
+                    gather4(st.buf + s * SLOT + CHUNK * ROWB, rm.act, yr.x, yr.y, yr.z, yr.w, st.bar + s);
                 }
             };
             for (int ch = 0; ch < NSLOT - 1 && ch < nch; ch++) issue(ch);
@@ -606,26 +615,27 @@ __device__ void level_adjoint(const DevPlan& p, const DevAct& L, const AdjRun& r
             }
             const int nch = (cnt + CHUNK - 1) / CHUNK;
             // per lane (= edge of the batch): tensor-map rows of the consumer adjoint (the
-            // seed row for an output seed) and of the sibling
-            const int g_row = rm.grow0 + max(mine.x, 0), s_row = rm.arow0 + (mine.y & 0x7FFFFFFF);
+            // seed row for an output seed) and of the sibling, into the warp's row table (lanes
+            // past cnt repeat the last edge, so a partial chunk does too)
+            {
+                const int g_row = rm.grow0 + max(mine.x, 0), s_row = rm.arow0 + (mine.y & 0x7FFFFFFF);
+                const int g_last = __shfl_sync(FULL, g_row, cnt - 1), s_last = __shfl_sync(FULL, s_row, cnt - 1);
+                st.rows[c.lane] = c.lane < cnt ? g_row : g_last;
+                st.rows[32 + c.lane] = c.lane < cnt ? s_row : s_last;
+                __syncwarp();
+            }
             // edges that close their node's sum (the node's adjoint row is stored there)
             const unsigned last_mask = __ballot_sync(FULL, c.lane < cnt && mine.y < 0);
             auto issue = [&](int ch) {
                 const int s = ch % NSLOT;
-                // consumer adjoints -> the 4 fp32 rows, siblings -> the 4 act rows (the tail of
-                // a partial chunk repeats its last edge; edge indices stay below 32)
-                int gr[CHUNK], sr[CHUNK];
-#pragma unroll
-                for (int j = 0; j < CHUNK; j++) {
-                    const int el = min(ch * CHUNK + j, cnt - 1);
-                    gr[j] = __shfl_sync(FULL, g_row, el);
-                    sr[j] = __shfl_sync(FULL, s_row, el);
-                }
+                // consumer adjoints -> the 4 fp32 rows, siblings -> the 4 act rows
                 if (c.lane == 0) {
+                    const int4 gr = *reinterpret_cast<const int4*>(st.rows + ch * CHUNK);
+                    const int4 sr = *reinterpret_cast<const int4*>(st.rows + 32 + ch * CHUNK);
                     char* sb = st.buf + s * SLOT;
                     mbar_expect_tx(st.bar + s, (uint32_t)(CHUNK * ROWF + CHUNK * ROWB));
-                    gather4(sb, rm.adj, gr[0], gr[1], gr[2], gr[3], st.bar + s);
-                    gather4_hint(sb + CHUNK * ROWF, rm.act, sr[0], sr[1], sr[2], sr[3], st.bar + s, stream_policy);
+                    gather4(sb, rm.adj, gr.x, gr.y, gr.z, gr.w, st.bar + s);
+                    gather4_hint(sb + CHUNK * ROWF, rm.act, sr.x, sr.y, sr.z, sr.w, st.bar + s, stream_policy);
                 }
             };
             for (int ch = 0; ch < NSLOT - 1 && ch < nch; ch++) issue(ch);
