@@ -313,6 +313,7 @@ struct Stage {
     char* buf;
     uint64_t* bar;
     int* rows;            // [2][32]: the tensor-map rows of the current batch's two operands
+    float4* coef;         // [32]: the batch's gate coefficients (forward) or edge (c0, c1) pairs
     uint32_t parity;      // bit s: parity of the next completion of slot s
     unsigned* status;     // plan status word (device)
     bool poisoned;        // a wait expired: stop waiting, results are invalid
@@ -335,7 +336,7 @@ __host__ __device__ constexpr int stage_rows_offset() {
 }
 template <typename T>
 __host__ __device__ constexpr int warp_stage_bytes() {
-    return (stage_rows_offset<T>() + 2 * 32 * 4 + 127) / 128 * 128;
+    return (stage_rows_offset<T>() + 2 * 32 * 4 + 32 * 16 + 127) / 128 * 128;
 }
 
 template <typename T>
@@ -344,6 +345,7 @@ __device__ __forceinline__ Stage make_stage(char* smem, unsigned* status, const 
     st.buf = smem + c.warp * warp_stage_bytes<T>();
     st.bar = reinterpret_cast<uint64_t*>(st.buf + NSLOT * slot_bytes<T>());
     st.rows = reinterpret_cast<int*>(st.buf + stage_rows_offset<T>());
+    st.coef = reinterpret_cast<float4*>(st.buf + stage_rows_offset<T>() + 2 * 32 * 4);
     st.parity = 0;
     st.status = status;
     st.poisoned = false;
@@ -477,9 +479,9 @@ __device__ void forward_levels(const DevPlan& p, const DevAct& L, T* act, Stage&
                 const int x_last = __shfl_sync(FULL, x_row, cnt - 1), y_last = __shfl_sync(FULL, y_row, cnt - 1);
                 st.rows[c.lane] = c.lane < cnt ? x_row : x_last;
                 st.rows[32 + c.lane] = c.lane < cnt ? y_row : y_last;
+                st.coef[c.lane] = gcoef[(uint32_t)mine.x >> 28];  // this lane's gate's (k0, k1, k2, k3)
                 __syncwarp();
             }
-            const int gop_mine = (int)((uint32_t)mine.x >> 28);
             T* out = act + at(base + orow, c);
             auto issue = [&](int ch) {
                 const int s = ch % NSLOT;
@@ -502,9 +504,8 @@ __device__ void forward_levels(const DevPlan& p, const DevAct& L, T* act, Stage&
 #pragma unroll
                 for (int j = 0; j < CHUNK; j++) {
                     const int gl = ch * CHUNK + j;  // < 32: at most 8 chunks of a batch
-                    const int gop = __shfl_sync(FULL, gop_mine, gl);
                     if (gl < cnt) {
-                        const float4 k = gcoef[gop];
+                        const float4 k = st.coef[gl];
                         const VF x = ActIO<T>::ld(reinterpret_cast<const T*>(sb + j * ROWB) + c.lane * VEC);
                         const VF y = ActIO<T>::ld(reinterpret_cast<const T*>(sb + (CHUNK + j) * ROWB) + c.lane * VEC);
                         VF z;
@@ -622,6 +623,7 @@ __device__ void level_adjoint(const DevPlan& p, const DevAct& L, const AdjRun& r
                 const int g_last = __shfl_sync(FULL, g_row, cnt - 1), s_last = __shfl_sync(FULL, s_row, cnt - 1);
                 st.rows[c.lane] = c.lane < cnt ? g_row : g_last;
                 st.rows[32 + c.lane] = c.lane < cnt ? s_row : s_last;
+                reinterpret_cast<float2*>(st.coef)[c.lane] = make_float2(__int_as_float(mine.z), __int_as_float(mine.w));
                 __syncwarp();
             }
             // edges that close their node's sum (the node's adjoint row is stored there)
@@ -647,9 +649,9 @@ __device__ void level_adjoint(const DevPlan& p, const DevAct& L, const AdjRun& r
 #pragma unroll
                 for (int j = 0; j < CHUNK; j++) {
                     const int el = ch * CHUNK + j;  // < 32: at most 8 chunks of a batch
-                    const float c0 = __int_as_float(__shfl_sync(FULL, mine.z, el));
-                    const float c1 = __int_as_float(__shfl_sync(FULL, mine.w, el));
                     if (el < cnt) {
+                        const float2 cc = reinterpret_cast<const float2*>(st.coef)[el];
+                        const float c0 = cc.x, c1 = cc.y;
                         const VF ga = ActIO<float>::ld(reinterpret_cast<const float*>(sb + j * ROWF) + c.lane * VEC);
                         const VF sv =
                             ActIO<T>::ld(reinterpret_cast<const T*>(sb + CHUNK * ROWF + j * ROWB) + c.lane * VEC);
