@@ -501,18 +501,22 @@ __device__ void forward_levels(const DevPlan& p, const DevAct& L, T* act, Stage&
                 stage_wait(st, s);
                 const char* sb = st.buf + s * SLOT;
                 T* out_ch = out + ch * CHUNK * TILE;
+                auto gate = [&](int j) {  // gate ch * CHUNK + j (< 32: at most 8 chunks of a batch)
+                    const float4 k = st.coef[ch * CHUNK + j];
+                    const VF x = ActIO<T>::ld(reinterpret_cast<const T*>(sb + j * ROWB) + c.lane * VEC);
+                    const VF y = ActIO<T>::ld(reinterpret_cast<const T*>(sb + (CHUNK + j) * ROWB) + c.lane * VEC);
+                    VF z;
 #pragma unroll
-                for (int j = 0; j < CHUNK; j++) {
-                    const int gl = ch * CHUNK + j;  // < 32: at most 8 chunks of a batch
-                    if (gl < cnt) {
-                        const float4 k = st.coef[gl];
-                        const VF x = ActIO<T>::ld(reinterpret_cast<const T*>(sb + j * ROWB) + c.lane * VEC);
-                        const VF y = ActIO<T>::ld(reinterpret_cast<const T*>(sb + (CHUNK + j) * ROWB) + c.lane * VEC);
-                        VF z;
+                    for (int q = 0; q < VEC; q++) z.v[q] = gate_apply(k, x.v[q], y.v[q]);
+                    ActIO<T>::st(out_ch + j * TILE, z);
+                };
+                if ((ch + 1) * CHUNK <= cnt) {  // a full chunk
 #pragma unroll
-                        for (int q = 0; q < VEC; q++) z.v[q] = gate_apply(k, x.v[q], y.v[q]);
-                        ActIO<T>::st(out_ch + j * TILE, z);
-                    }
+                    for (int j = 0; j < CHUNK; j++) gate(j);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < CHUNK; j++)
+                        if (ch * CHUNK + j < cnt) gate(j);
                 }
                 fence_async_shared();
                 __syncwarp();
@@ -646,24 +650,27 @@ __device__ void level_adjoint(const DevPlan& p, const DevAct& L, const AdjRun& r
                 const int s = ch % NSLOT;
                 stage_wait(st, s);
                 const char* sb = st.buf + s * SLOT;
+                auto edge = [&](int j) {  // edge ch * CHUNK + j (< 32: at most 8 chunks of a batch)
+                    const int el = ch * CHUNK + j;
+                    const float2 cc = reinterpret_cast<const float2*>(st.coef)[el];
+                    const VF ga = ActIO<float>::ld(reinterpret_cast<const float*>(sb + j * ROWF) + c.lane * VEC);
+                    const VF sv = ActIO<T>::ld(reinterpret_cast<const T*>(sb + CHUNK * ROWF + j * ROWB) + c.lane * VEC);
 #pragma unroll
-                for (int j = 0; j < CHUNK; j++) {
-                    const int el = ch * CHUNK + j;  // < 32: at most 8 chunks of a batch
-                    if (el < cnt) {
-                        const float2 cc = reinterpret_cast<const float2*>(st.coef)[el];
-                        const float c0 = cc.x, c1 = cc.y;
-                        const VF ga = ActIO<float>::ld(reinterpret_cast<const float*>(sb + j * ROWF) + c.lane * VEC);
-                        const VF sv =
-                            ActIO<T>::ld(reinterpret_cast<const T*>(sb + CHUNK * ROWF + j * ROWB) + c.lane * VEC);
-#pragma unroll
-                        for (int q = 0; q < VEC; q++) acc.v[q] = fmaf(ga.v[q], fmaf(c1, sv.v[q], c0), acc.v[q]);
-                        if ((last_mask >> el) & 1u) {
-                            st_row_hint(node_row, acc, keep_policy);
-                            node_row += TILE;
-                            acc = vf_fill(0.0f);
-                            k++;
-                        }
+                    for (int q = 0; q < VEC; q++) acc.v[q] = fmaf(ga.v[q], fmaf(cc.y, sv.v[q], cc.x), acc.v[q]);
+                    if ((last_mask >> el) & 1u) {
+                        st_row_hint(node_row, acc, keep_policy);
+                        node_row += TILE;
+                        acc = vf_fill(0.0f);
+                        k++;
                     }
+                };
+                if ((ch + 1) * CHUNK <= cnt) {  // a full chunk
+#pragma unroll
+                    for (int j = 0; j < CHUNK; j++) edge(j);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < CHUNK; j++)
+                        if (ch * CHUNK + j < cnt) edge(j);
                 }
                 fence_async_shared();
                 __syncwarp();
