@@ -236,6 +236,7 @@ constexpr int CHUNK = SAT_CHUNK;  // gates (forward) or fan-out edges (adjoint) 
 constexpr int NSLOT = 2;   // pipeline depth per warp (gathers land one chunk ahead: 93% of waits succeed at once)
 static_assert(CHUNK == 4, "a chunk is one tile::gather4 load (4 rows) per operand");
 constexpr unsigned STATUS_WAIT_TIMEOUT = 4u;
+constexpr int EDGE_BATCH = 64;  // fan-out edges per batch of the adjoint: two records per lane
 constexpr uint64_t WAIT_NS = 1000000000ull;  // bound of one wait for a warp's own copies (1 s)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -312,8 +313,8 @@ __device__ __forceinline__ void fence_async_global() { asm volatile("fence.proxy
 struct Stage {
     char* buf;
     uint64_t* bar;
-    int* rows;            // [2][32]: the tensor-map rows of the current batch's two operands
-    float4* coef;         // [32]: the batch's gate coefficients (forward) or edge (c0, c1) pairs
+    int* rows;            // [2][EDGE_BATCH]: the tensor-map rows of the current batch's two operands
+    float4* coef;         // the batch's gate coefficients (forward, 32) or edge (c0, c1) pairs (EDGE_BATCH)
     uint32_t parity;      // bit s: parity of the next completion of slot s
     unsigned* status;     // plan status word (device)
     bool poisoned;        // a wait expired: stop waiting, results are invalid
@@ -336,7 +337,7 @@ __host__ __device__ constexpr int stage_rows_offset() {
 }
 template <typename T>
 __host__ __device__ constexpr int warp_stage_bytes() {
-    return (stage_rows_offset<T>() + 2 * 32 * 4 + 32 * 16 + 127) / 128 * 128;
+    return (stage_rows_offset<T>() + 2 * EDGE_BATCH * 4 + 32 * 16 + 127) / 128 * 128;
 }
 
 template <typename T>
@@ -345,7 +346,7 @@ __device__ __forceinline__ Stage make_stage(char* smem, unsigned* status, const 
     st.buf = smem + c.warp * warp_stage_bytes<T>();
     st.bar = reinterpret_cast<uint64_t*>(st.buf + NSLOT * slot_bytes<T>());
     st.rows = reinterpret_cast<int*>(st.buf + stage_rows_offset<T>());
-    st.coef = reinterpret_cast<float4*>(st.buf + stage_rows_offset<T>() + 2 * 32 * 4);
+    st.coef = reinterpret_cast<float4*>(st.buf + stage_rows_offset<T>() + 2 * EDGE_BATCH * 4);
     st.parity = 0;
     st.status = status;
     st.poisoned = false;
@@ -478,7 +479,7 @@ __device__ void forward_levels(const DevPlan& p, const DevAct& L, T* act, Stage&
                 const int x_row = rm.arow0 + (mine.x & 0x0FFFFFFF), y_row = rm.arow0 + mine.y;
                 const int x_last = __shfl_sync(FULL, x_row, cnt - 1), y_last = __shfl_sync(FULL, y_row, cnt - 1);
                 st.rows[c.lane] = c.lane < cnt ? x_row : x_last;
-                st.rows[32 + c.lane] = c.lane < cnt ? y_row : y_last;
+                st.rows[EDGE_BATCH + c.lane] = c.lane < cnt ? y_row : y_last;
                 st.coef[c.lane] = gcoef[(uint32_t)mine.x >> 28];  // this lane's gate's (k0, k1, k2, k3)
                 __syncwarp();
             }
@@ -488,7 +489,7 @@ __device__ void forward_levels(const DevPlan& p, const DevAct& L, T* act, Stage&
                 // first inputs of the chunk's 4 gates -> rows 0..3, second inputs -> rows 4..7
                 if (c.lane == 0) {
                     const int4 xr = *reinterpret_cast<const int4*>(st.rows + ch * CHUNK);
-                    const int4 yr = *reinterpret_cast<const int4*>(st.rows + 32 + ch * CHUNK);
+                    const int4 yr = *reinterpret_cast<const int4*>(st.rows + EDGE_BATCH + ch * CHUNK);
                     mbar_expect_tx(st.bar + s, (uint32_t)(2 * CHUNK * ROWB));
                     gather4(st.buf + s * SLOT, rm.act, xr.x, xr.y, xr.z, xr.w, st.bar + s);
                     gather4(st.buf + s * SLOT + CHUNK * ROWB, rm.act, yr.x, yr.y, yr.z, yr.w, st.bar + s);
@@ -611,33 +612,43 @@ __device__ void level_adjoint(const DevPlan& p, const DevAct& L, const AdjRun& r
         int k = 0;                         // nodes of this run stored so far
         float* node_row = adj + at(run.arow + (ua - u0), c);  // where the next node's adjoint goes
         VF acc = vf_fill(0.0f);
-        for (int base = e_begin; base < e_end; base += 32) {
-            const int cnt = min(32, e_end - base);
-            int4 mine = run.first;
+        for (int base = e_begin; base < e_end; base += EDGE_BATCH) {
+            // up to 64 edges: edge base + lane in `mine`, base + 32 + lane in `mine2`
+            const int cnt = min(EDGE_BATCH, e_end - base);
+            int4 mine = run.first, mine2 = make_int4(-1, 0, 0, 0);
             if (ua != u0 || base != e_begin) {
                 mine = make_int4(-1, 0, 0, 0);
                 if (c.lane < cnt) mine = __ldg(&L.edge[base + c.lane]);
             }
+            if (32 + c.lane < cnt) mine2 = __ldg(&L.edge[base + 32 + c.lane]);
             const int nch = (cnt + CHUNK - 1) / CHUNK;
-            // per lane (= edge of the batch): tensor-map rows of the consumer adjoint (the
-            // seed row for an output seed) and of the sibling, into the warp's row table (lanes
-            // past cnt repeat the last edge, so a partial chunk does too)
+            // per edge: tensor-map rows of the consumer adjoint (the seed row for an output seed)
+            // and of the sibling, into the warp's row table (entries past cnt repeat the last
+            // edge, so a partial chunk does too), and the partial's (c0, c1)
             {
                 const int g_row = rm.grow0 + max(mine.x, 0), s_row = rm.arow0 + (mine.y & 0x7FFFFFFF);
-                const int g_last = __shfl_sync(FULL, g_row, cnt - 1), s_last = __shfl_sync(FULL, s_row, cnt - 1);
+                const int g_row2 = rm.grow0 + max(mine2.x, 0), s_row2 = rm.arow0 + (mine2.y & 0x7FFFFFFF);
+                const bool last_lo = cnt <= 32;  // the batch's last edge is in `mine`
+                const int g_last = __shfl_sync(FULL, last_lo ? g_row : g_row2, (cnt - 1) & 31);
+                const int s_last = __shfl_sync(FULL, last_lo ? s_row : s_row2, (cnt - 1) & 31);
                 st.rows[c.lane] = c.lane < cnt ? g_row : g_last;
-                st.rows[32 + c.lane] = c.lane < cnt ? s_row : s_last;
-                reinterpret_cast<float2*>(st.coef)[c.lane] = make_float2(__int_as_float(mine.z), __int_as_float(mine.w));
+                st.rows[32 + c.lane] = 32 + c.lane < cnt ? g_row2 : g_last;
+                st.rows[EDGE_BATCH + c.lane] = c.lane < cnt ? s_row : s_last;
+                st.rows[EDGE_BATCH + 32 + c.lane] = 32 + c.lane < cnt ? s_row2 : s_last;
+                float2* cc = reinterpret_cast<float2*>(st.coef);
+                cc[c.lane] = make_float2(__int_as_float(mine.z), __int_as_float(mine.w));
+                cc[32 + c.lane] = make_float2(__int_as_float(mine2.z), __int_as_float(mine2.w));
                 __syncwarp();
             }
             // edges that close their node's sum (the node's adjoint row is stored there)
-            const unsigned last_mask = __ballot_sync(FULL, c.lane < cnt && mine.y < 0);
+            const unsigned last_lo = __ballot_sync(FULL, c.lane < cnt && mine.y < 0);
+            const unsigned last_hi = __ballot_sync(FULL, 32 + c.lane < cnt && mine2.y < 0);
             auto issue = [&](int ch) {
                 const int s = ch % NSLOT;
                 // consumer adjoints -> the 4 fp32 rows, siblings -> the 4 act rows
                 if (c.lane == 0) {
                     const int4 gr = *reinterpret_cast<const int4*>(st.rows + ch * CHUNK);
-                    const int4 sr = *reinterpret_cast<const int4*>(st.rows + 32 + ch * CHUNK);
+                    const int4 sr = *reinterpret_cast<const int4*>(st.rows + EDGE_BATCH + ch * CHUNK);
                     char* sb = st.buf + s * SLOT;
                     mbar_expect_tx(st.bar + s, (uint32_t)(CHUNK * ROWF + CHUNK * ROWB));
                     gather4(sb, rm.adj, gr.x, gr.y, gr.z, gr.w, st.bar + s);
@@ -650,14 +661,15 @@ __device__ void level_adjoint(const DevPlan& p, const DevAct& L, const AdjRun& r
                 const int s = ch % NSLOT;
                 stage_wait(st, s);
                 const char* sb = st.buf + s * SLOT;
-                auto edge = [&](int j) {  // edge ch * CHUNK + j (< 32: at most 8 chunks of a batch)
-                    const int el = ch * CHUNK + j;
-                    const float2 cc = reinterpret_cast<const float2*>(st.coef)[el];
+                // bit j: edge ch * CHUNK + j closes its node (CHUNK divides 32)
+                const unsigned chunk_last = ch * CHUNK < 32 ? last_lo >> (ch * CHUNK) : last_hi >> (ch * CHUNK - 32);
+                auto edge = [&](int j) {  // edge ch * CHUNK + j (< 64: at most 16 chunks of a batch)
+                    const float2 cc = reinterpret_cast<const float2*>(st.coef)[ch * CHUNK + j];
                     const VF ga = ActIO<float>::ld(reinterpret_cast<const float*>(sb + j * ROWF) + c.lane * VEC);
                     const VF sv = ActIO<T>::ld(reinterpret_cast<const T*>(sb + CHUNK * ROWF + j * ROWB) + c.lane * VEC);
 #pragma unroll
                     for (int q = 0; q < VEC; q++) acc.v[q] = fmaf(ga.v[q], fmaf(cc.y, sv.v[q], cc.x), acc.v[q]);
-                    if ((last_mask >> el) & 1u) {
+                    if ((chunk_last >> j) & 1u) {
                         st_row_hint(node_row, acc, keep_policy);
                         node_row += TILE;
                         acc = vf_fill(0.0f);
