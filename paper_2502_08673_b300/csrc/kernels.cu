@@ -431,10 +431,11 @@ __device__ void tile_inputs(const DevPlan& p, const float* __restrict__ V, int64
 
 // Forward pass over cone levels l_lo .. l_hi (all of them, or with scratch_only the
 // levels the layout does not keep: the re-evaluation of a segment).  Within a level each
-// warp takes a contiguous run of gates; 32 gate records come in one coalesced load and
-// are broadcast by shuffles; the two input rows of each gate are gathered into shared
-// memory (two gather4 loads per CHUNK = 4 gates), NSLOT-1 chunks ahead of the
-// computation.  gcoef: the 16 bilinear coefficient sets in shared memory.
+// warp takes a contiguous run of gates; 32 gate records come in one coalesced load, and
+// their input rows and coefficients go into the warp's row and coefficient tables in
+// shared memory; the two input rows of each gate are gathered into shared memory (two
+// gather4 loads per CHUNK = 4 gates, issued by lane 0 from the row table), NSLOT-1 chunks
+// ahead of the computation.  gcoef: the 16 bilinear coefficient sets in shared memory.
 template <typename T>
 __device__ void forward_levels(const DevPlan& p, const DevAct& L, T* act, Stage& st, const float4* gcoef,
                                const RowMaps& rm, const TileCtx& c, int l_lo, int l_hi, bool scratch_only) {
@@ -566,9 +567,10 @@ __device__ void tile_loss(const DevPlan& p, const DevAct& L, const T* act, float
 // contiguous run of nodes, whose fan-out edges are contiguous in the CSR and
 // are summed in CSR order.  An edge contributes ga * (c0 + c1 * A_sibling)
 // with ga the consumer's adjoint row, or for an output seed the seed row (the
-// per-sample weight of the loss, written at the start of the backward pass).  The
-// consumer-adjoint and sibling rows are gathered into shared memory (one
-// gather4 load each per CHUNK = 4 edges).
+// per-sample weight of the loss, written at the start of the backward pass).  Up to 64
+// edge records (two per lane) fill the warp's row and coefficient tables; the
+// consumer-adjoint and sibling rows are gathered into shared memory (one gather4 load
+// each per CHUNK = 4 edges).
 // This warp's node run [u0, u1) of a cone level with the CSR offsets of its first
 // 31 nodes and its first 32 fan-out edges, loaded ahead (before the barrier of
 // the level above) so that the three dependent loads do not stall the level.
