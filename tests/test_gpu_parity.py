@@ -385,12 +385,15 @@ def test_canonical_order_with_equal_top_bits(gpu):
 
 @pytest.mark.parametrize("name,opt_name,lr,steps,atol", [
     ("planted3sat_50_200", "gd", 0.5, 100, 1e-5), ("planted3sat_50_200", "adam", 0.02, 100, 1e-4),
-    ("tseitin_small", "gd", 0.5, 100, 2e-5), ("tseitin_small", "adam", 0.02, 100, 1e-3)])
+    ("tseitin_small", "gd", 0.5, 100, 2e-5), ("tseitin_small", "adam", 0.02, 100, 1e-3),
+    ("tseitin_2k_20k_d40", "gd", 0.5, 100, 1e-4), ("tseitin_2k_20k_d40", "adam", 0.1, 100, 0.3)])
 def test_long_trajectory(gpu, name, opt_name, lr, steps, atol):
     """100 fused steps (GD and Adam), GPU FP32 against the FP64 oracle from the same V0: the
     FP32 rounding stays within `atol` over the whole trajectory, 10x the measured maxima
     (planted 3-SAT: 8.6e-7 GD, 1.1e-5 Adam; 16-level Tseitin circuit: 1.7e-6 GD, 1.0e-4
-    Adam).  Thresholded bits agree wherever the oracle's logit is not within 10 x atol of 0."""
+    Adam; the 40-level 20k-gate workload: 9.0e-6 GD, 2.9e-2 Adam, whose normalised step
+    turns the rounding of near-zero gradients into steps of up to lr).  Thresholded bits
+    agree wherever the oracle's logit is not within 10 x atol of 0."""
     P, cnf, circ, plan, orc = _setup(INSTANCES[name]())
     B = 96
     V0 = normal_logits(B, orc.n_pi, seed=8, scale=0.5)
