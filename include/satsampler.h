@@ -15,7 +15,9 @@
  *  - Every call returns sat_status; no C++ exception crosses this boundary.
  *    On failure sat_last_error() (thread-local) describes the cause.
  *  - Objects returned through an `out` pointer are owned by the caller and
- *    released by the matching *_free, which accepts NULL.
+ *    released by the matching *_free, which accepts NULL.  A plan, dedup set or
+ *    network holds device memory: free it only after the work queued on it has
+ *    finished (synchronise its streams first; *_free does not wait).
  *  - Inputs are never modified.  "Device" pointers are CUDA global-memory
  *    pointers on the current device; "host" pointers are ordinary memory.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
