@@ -598,14 +598,19 @@ def main():
     torch.cuda.empty_cache()
     e2e = None
     if not args.no_e2e:
-        # the user-facing call with host inputs: plan upload, rounds, key download
+        # the user-facing call with host inputs: plan upload, rounds, key download; one
+        # untimed call first (it grows the library's workspace pool, which later calls reuse)
         e2e_steps = max(1, min(args.steps, 2))
-        t1 = time.perf_counter()
         ucount = 0
         d2h = 0
-        for k in range(e2e_steps):
+        for k in range(-1, e2e_steps):
+            if k == 0:
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                ucount = 0
+                d2h = 0
             sols = P.sample(circ, cnf, n_wanted=10 ** 12, batch=B, steps=steps, max_rounds=1, lr=w["lr"], seed=0,
-                            first_round=round_base + (n_rounds + k) * 4096, init_scale=w["init_scale"], act_dtype=ad,
+                            first_round=round_base + (n_rounds + (k if k >= 0 else e2e_steps)) * 4096, init_scale=w["init_scale"], act_dtype=ad,
                             check_every=max(0, args.check_every), max_age=args.max_age, optimizer=args.optimizer,
                             recompute_segment=args.recompute)
             ucount += len(sols)
@@ -614,7 +619,7 @@ def main():
         st = sols.stats
         e2e = {"value": ucount / e2e_s, "unit": "unique valid solutions/s",
                "h2d_bytes_per_step": info["upload_bytes"],
-               "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps,
+               "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps, "warmup_calls": 1,
                "wall_ms_per_call": 1e3 * e2e_s / e2e_steps,
                "last_call_ms": {k: round(st[f"ms_{k}"], 3) for k in
                                 ("upload", "init", "steps", "verify", "dedup", "download")},

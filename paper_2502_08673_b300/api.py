@@ -561,6 +561,19 @@ def valid_mask(valid_words, B: int) -> np.ndarray:
     return bits[:B].astype(bool)
 
 
+def cached_memory() -> tuple[int, int]:
+    """(reserved, in use) bytes of the library pool that serves the end-to-end calls'
+    workspaces on the current device; the reserve is kept between calls."""
+    r, u = C.c_uint64(0), C.c_uint64(0)
+    check(lib().sat_cached_memory(C.byref(r), C.byref(u)))
+    return r.value, u.value
+
+
+def release_cached_memory() -> None:
+    """Return the library pool's idle reserve on the current device to the device."""
+    check(lib().sat_release_cached_memory())
+
+
 def sample(circuit: Circuit, cnf: Cnf, n_wanted: int, batch=1024, steps=200, max_rounds=1, optimizer="adam",
            lr=0.1, beta1=0.9, beta2=0.999, eps=1e-8, seed=0, first_round=0, init_scale=1.0, act_dtype="f32",
            steps_per_launch=0, proposal: "Mlp | None" = None, tau: float = 1.0, check_every=0, max_age=0,

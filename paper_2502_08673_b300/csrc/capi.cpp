@@ -15,6 +15,7 @@
 #include <new>
 #include <sstream>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/satsampler.h"
@@ -63,10 +64,33 @@ struct sat_dedup {
     unsigned long long* slot_of = nullptr;
 };
 
+// Allocator whose value-initialisation leaves elements uninitialised: the key buffer is
+// written in full by the download, so resizing it need not zero it first.
+template <typename T>
+struct uninit_allocator : std::allocator<T> {
+    template <typename U>
+    struct rebind {
+        using other = uninit_allocator<U>;
+    };
+    uninit_allocator() = default;
+    template <typename U>
+    uninit_allocator(const uninit_allocator<U>&) noexcept {}
+    template <typename U>
+    void construct(U* p) noexcept {
+        ::new ((void*)p) U;
+    }
+    template <typename U, typename... A>
+    void construct(U* p, A&&... a) {
+        ::new ((void*)p) U(std::forward<A>(a)...);
+    }
+};
+
+using KeyBuffer = std::vector<uint32_t, uninit_allocator<uint32_t>>;
+
 struct sat_solutions {
     uint32_t n_vars = 0, n_pi = 0, key_words = 0;
     uint64_t count = 0;
-    std::vector<uint32_t> keys;        // [count][key_words], canonical order
+    KeyBuffer keys;                    // [count][key_words], canonical order
     std::vector<int32_t> f_in0, f_in1;
     std::vector<uint8_t> f_gop;
     std::vector<int64_t> var_full;
@@ -890,9 +914,95 @@ void sat_sample_opts_default(sat_sample_opts* o) {
 
 namespace {
 
-// Device buffers of one call, stream-ordered (cudaMallocAsync / cudaFreeAsync on the
-// call's stream, from the device's default pool): freeing does not synchronise the
-// device, so calls on other streams keep running.
+// The library's own stream-ordered memory pool of each device.  It keeps the memory it
+// has reserved when buffers are freed (release threshold: unlimited), so a repeated
+// call maps no new device memory; sat_release_cached_memory hands it back.
+constexpr int MAX_DEVICES = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[MAX_DEVICES] = {};
+
+cudaError_t library_pool(cudaMemPool_t* out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if ((e = cudaMemPoolCreate(&pool, &props)) != cudaSuccess) return e;
+        uint64_t keep = ~0ull;
+        if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return e;
+        }
+        g_pools[dev] = pool;
+    }
+    *out = g_pools[dev];
+    return cudaSuccess;
+}
+
+// A pinned host buffer, kept between calls, through which sat_sample downloads the
+// ordered keys: a device-to-host copy into pageable memory runs at a fraction of the
+// link's rate.  One call uses it at a time; a concurrent call copies directly.  Growing it
+// frees the old buffer (cudaFreeHost, which waits for the device).
+struct PinnedStage {
+    std::mutex mu;
+    void* p = nullptr;
+    size_t cap = 0;
+};
+PinnedStage g_stage;
+
+// Key buffers of freed solution sets (at most two, 1 MiB to 256 MiB each), kept for the
+// next sat_sample: a fresh buffer of several MB costs a page fault per page when the
+// download first writes it.
+struct KeyCache {
+    std::mutex mu;
+    std::vector<KeyBuffer> bufs;
+};
+KeyCache g_keys;
+constexpr size_t KEY_CACHE_MIN = (size_t)1 << 20, KEY_CACHE_MAX = (size_t)1 << 28;
+
+// A buffer of n words: the smallest cached one that holds them, else a new one with an
+// eighth to spare (the next call's solution count differs a little).
+KeyBuffer take_key_buffer(size_t n) {
+    KeyBuffer out;
+    {
+        std::lock_guard<std::mutex> lk(g_keys.mu);
+        int best = -1;
+        for (int i = 0; i < (int)g_keys.bufs.size(); i++)
+            if (g_keys.bufs[i].capacity() >= n && (best < 0 || g_keys.bufs[i].capacity() < g_keys.bufs[best].capacity()))
+                best = i;
+        if (best >= 0) {
+            out = std::move(g_keys.bufs[best]);
+            g_keys.bufs.erase(g_keys.bufs.begin() + best);
+        }
+    }
+    if (out.capacity() < n) out.reserve(n + n / 8);
+    out.resize(n);
+    return out;
+}
+
+void give_key_buffer(KeyBuffer&& b) {
+    const size_t bytes = b.capacity() * sizeof(uint32_t);
+    if (bytes < KEY_CACHE_MIN || bytes > KEY_CACHE_MAX) return;
+    std::lock_guard<std::mutex> lk(g_keys.mu);
+    if (g_keys.bufs.size() >= 2) {  // keep the two largest
+        auto small = std::min_element(g_keys.bufs.begin(), g_keys.bufs.end(),
+                                      [](const KeyBuffer& x, const KeyBuffer& y) { return x.capacity() < y.capacity(); });
+        if (small->capacity() >= b.capacity()) return;
+        g_keys.bufs.erase(small);
+    }
+    g_keys.bufs.push_back(std::move(b));
+}
+
+// Device buffers of one call, stream-ordered (allocated and freed on the call's stream,
+// from the library pool): freeing does not synchronise the device, so calls on other
+// streams keep running.  An allocation the pool cannot serve is retried once after the
+// pool's idle reserve is returned to the device.
 struct Workspace {
     explicit Workspace(cudaStream_t s) : stream(s) {}
     cudaStream_t stream;
@@ -907,9 +1017,18 @@ struct Workspace {
     }
     bool alloc(void** p, size_t n) {
         if (n == 0) n = 16;
-        if (cudaMallocAsync(p, n, stream) != cudaSuccess) {
+        cudaMemPool_t pool = nullptr;
+        if (library_pool(&pool) != cudaSuccess) {
             cudaGetLastError();
             return false;
+        }
+        if (cudaMallocFromPoolAsync(p, n, pool, stream) != cudaSuccess) {
+            cudaGetLastError();
+            cudaMemPoolTrimTo(pool, 0);
+            if (cudaMallocFromPoolAsync(p, n, pool, stream) != cudaSuccess) {
+                cudaGetLastError();
+                return false;
+            }
         }
         bufs.push_back(*p);
         return true;
@@ -939,6 +1058,43 @@ size_t scratch_elems(int64_t rows, int64_t B) {
 }
 
 }  // namespace
+
+sat_status sat_cached_memory(uint64_t* reserved_bytes, uint64_t* used_bytes) {
+    if (!reserved_bytes || !used_bytes) return fail(SAT_ERR_ARG, "NULL argument");
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = library_pool(&pool);
+    uint64_t r = 0, u = 0;
+    if (e == cudaSuccess) e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &r);
+    if (e == cudaSuccess) e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &u);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SAT_ERR_CUDA, std::string("memory pool: ") + cudaGetErrorString(e));
+    }
+    *reserved_bytes = r;
+    *used_bytes = u;
+    return SAT_OK;
+}
+
+sat_status sat_release_cached_memory(void) {
+    {
+        std::lock_guard<std::mutex> lk(g_stage.mu);
+        if (g_stage.p) cudaFreeHost(g_stage.p);
+        g_stage.p = nullptr;
+        g_stage.cap = 0;
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_keys.mu);
+        g_keys.bufs.clear();
+    }
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = library_pool(&pool);
+    if (e == cudaSuccess) e = cudaMemPoolTrimTo(pool, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SAT_ERR_CUDA, std::string("memory pool: ") + cudaGetErrorString(e));
+    }
+    return SAT_OK;
+}
 
 // Early exit: epochs of check_every steps over the whole batch; after each, the
 // valid samples are harvested into the dedup set and they (and samples older
@@ -1190,7 +1346,7 @@ sat_status sat_sample(const sat_circuit* c, const sat_cnf* cnf, const sat_sample
     // canonical order: ascending packed input vector (highest word most significant), sorted
     // on the device by the top 64 bits; keys that share them are ordered here
     const uint32_t kw = sol->key_words;
-    sol->keys.resize(sol->count * kw);
+    sol->keys = take_key_buffer(sol->count * kw);
     if (sol->count > 0 && kw > 0) {
         Workspace ow(S(o->stream));
         uint64_t* hi = nullptr;
@@ -1201,10 +1357,25 @@ sat_status sat_sample(const sat_circuit* c, const sat_cnf* cnf, const sat_sample
             delete sol;
             return fail(SAT_ERR_OOM, "cudaMalloc failed for the solution order");
         }
+        const size_t bytes = sol->count * kw * 4;
+        std::unique_lock<std::mutex> lk(g_stage.mu, std::try_to_lock);
+        if (lk.owns_lock() && g_stage.cap < bytes) {
+            if (g_stage.p) cudaFreeHost(g_stage.p);
+            g_stage.p = nullptr;
+            g_stage.cap = 0;
+            size_t want = (size_t)1 << 20;  // powers of two from 1 MiB: few regrowths
+            while (want < bytes) want <<= 1;
+            if (cudaMallocHost(&g_stage.p, want) == cudaSuccess)
+                g_stage.cap = want;
+            else
+                cudaGetLastError();
+        }
+        void* dst = lk.owns_lock() && g_stage.cap >= bytes ? g_stage.p : (void*)sol->keys.data();
         cudaError_t e = sat::launch_key_order(pg.d->d.pool, (int)kw, sol->count, hi, idx, sorted, S(o->stream));
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(sol->keys.data(), sorted, sol->count * kw * 4, cudaMemcpyDeviceToHost, S(o->stream));
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst, sorted, bytes, cudaMemcpyDeviceToHost, S(o->stream));
         if (e == cudaSuccess) e = cudaStreamSynchronize(S(o->stream));
+        if (e == cudaSuccess && dst != (void*)sol->keys.data()) std::memcpy(sol->keys.data(), dst, bytes);
+        if (lk.owns_lock()) lk.unlock();
         if (e != cudaSuccess) {
             delete sol;
             return fail(SAT_ERR_CUDA, std::string("solution order: ") + cudaGetErrorString(e));
@@ -1278,6 +1449,10 @@ sat_status sat_solutions_copy(const sat_solutions* s, uint64_t first, uint64_t c
     return SAT_OK;
 }
 
-void sat_solutions_free(sat_solutions* s) { delete s; }
+void sat_solutions_free(sat_solutions* s) {
+    if (!s) return;
+    give_key_buffer(std::move(s->keys));
+    delete s;
+}
 
 }  // extern "C"

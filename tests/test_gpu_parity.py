@@ -303,6 +303,36 @@ def test_sample_end_to_end_planted3sat(gpu):
     assert sols.stats["valid"] >= len(A)
 
 
+def test_workspace_pool_kept_between_calls_and_released(gpu):
+    """The end-to-end call's workspace comes from the library pool, which keeps its reserve
+    after the call (nothing left in use) until released; repeated calls with one seed return
+    the same solutions before and after a release."""
+    import paper_2502_08673_b300 as P
+    text = planted_3sat(50, 200, 1).dimacs()
+    cnf = P.Cnf.from_dimacs(text)
+    circ = P.Circuit.build(cnf)
+    P.release_cached_memory()
+
+    def run():
+        s = P.sample(circ, cnf, n_wanted=10 ** 9, batch=2048, steps=100, max_rounds=1, lr=0.1, seed=4)
+        torch.cuda.synchronize()
+        return s.assignments()
+
+    A = run()
+    reserved, used = P.cached_memory()
+    # at least V, m and v of the batch: 3 x 50 inputs x 2048 samples x 4 B
+    assert reserved >= 3 * 50 * 2048 * 4
+    assert used == 0
+    B = run()
+    assert P.cached_memory() == (reserved, 0)
+    P.release_cached_memory()
+    assert P.cached_memory() == (0, 0)
+    C_ = run()
+    assert len(A) > 0
+    np.testing.assert_array_equal(A, B)
+    np.testing.assert_array_equal(A, C_)
+
+
 @pytest.mark.parametrize("act_dtype,act_bound,rel_bound", [("f32", 1e-5, 1e-4), ("bf16", 0.06, 2.0),
                                                            ("f16", 0.01, 0.5)])
 def test_per_step_error_vs_fp64(gpu, act_dtype, act_bound, rel_bound):
@@ -339,7 +369,7 @@ def test_per_step_error_vs_fp64(gpu, act_dtype, act_bound, rel_bound):
 
 
 def test_many_solutions_canonical_order(gpu):
-    """sat_sample with ~240k distinct solutions (the multi-threaded host sort): returned in
+    """sat_sample with ~240k distinct solutions (ordered on the device): returned in
     ascending order of the packed assignment, all distinct, every one CNF-valid."""
     import paper_2502_08673_b300 as P
     inst = tseitin_random_circuit(50, 50, 5, 4, seed=1)
