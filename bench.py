@@ -192,9 +192,19 @@ def profile_traffic(workload, act_dtype, B=None, steps=None):
     return float(m.group(1)), (float(r.group(1)) if r else None), f.name
 
 
-def step_kernel_launches(B, torch):
-    """Launches of the fused step kernel per call: whole waves of one-CTA tiles, plus a
-    partial last wave of at most half the SMs as 2-CTA clusters (the library's policy)."""
+def resident_bytes_per_launch(info, B, optimizer):
+    """HBM bytes of one launch of the shared-memory resident step kernel: the cone inputs'
+    V (and Adam's m, v) read and written once for all the launch's steps, and the loss;
+    activations and adjoints never leave shared memory."""
+    return B * (info["n_cone_pi"] * (24 if optimizer == "adam" else 8) + 4)
+
+
+def step_kernel_launches(B, torch, kind="tiled"):
+    """Launches of the fused step kernel per call: one for the resident kernel; for the
+    tiled one, whole waves of one-CTA tiles plus a partial last wave of at most half the
+    SMs as 2-CTA clusters (the library's policy)."""
+    if kind == "resident":
+        return 1
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     tiles = -(-B // 128)
     main = tiles - tiles % sms
@@ -567,10 +577,15 @@ def main():
     run_steps = prop_steps if (mlp is not None and args.check_every <= 0) else steps
     gate_evals = info["n_cone_gates"] * B * run_steps * args.steps * world
     peak, peak_kind = measured_peaks()
-    alg = algorithmic_bytes_per_step(info, B, ad, args.recompute) * (launch_steps or run_steps)
+    skind = plan.step_kernel(ad)
+    if skind == "resident":
+        alg = resident_bytes_per_launch(info, B, args.optimizer)
+        dram_per_sample_step, dram_per_round, prof = None, None, None
+    else:
+        alg = algorithmic_bytes_per_step(info, B, ad, args.recompute) * (launch_steps or run_steps)
+        dram_per_sample_step, dram_per_round, prof = profile_traffic(args.workload, ad, B, launch_steps or run_steps)
     kavg = statistics.mean(kernel_ms)
     achieved = alg / (kavg / 1e3) / 1e9
-    dram_per_sample_step, dram_per_round, prof = profile_traffic(args.workload, ad, B, launch_steps or run_steps)
 
     plain_cmp = None
     if mlp is not None:
@@ -648,14 +663,17 @@ def main():
             "unique_in_timed_steps": uniq_all,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
-                         "kernel": "steps_kernel", "kernel_ms_avg": kavg,
+                         "kernel": "resident_steps_kernel" if skind == "resident" else "steps_kernel",
+                         "byte_model": ("V, m, v once per launch (activations and adjoints in shared memory)"
+                                        if skind == "resident" else "stored-activation schedule"),
+                         "kernel_ms_avg": kavg,
                          "algorithmic_bytes_per_launch": alg,
                          "traffic": (dram_per_round if dram_per_round else
                                      (dram_per_sample_step * B * (launch_steps or run_steps))
                                      if dram_per_sample_step else None),
                          "traffic_source": prof},
-            "gpu_launches": ((7 + step_kernel_launches(B, torch)) * args.steps if args.check_every <= 0
-                             else (8 + step_kernel_launches(B, torch)) * len(ee_events)),
+            "gpu_launches": ((7 + step_kernel_launches(B, torch, skind)) * args.steps if args.check_every <= 0
+                             else (8 + step_kernel_launches(B, torch, skind)) * len(ee_events)),
             "transform_s": transform_s,
             "plan": {k: info[k] for k in ("n_pi", "n_cone_pi", "n_cone_gates", "n_gates", "n_clauses",
                                           "n_cone_levels", "max_span")},

@@ -172,6 +172,26 @@ sat_status sat_plan_scratch_elems(const sat_plan* p, int64_t B, uint64_t* elems)
  * allocations and copies: make the first call before any stream capture). */
 sat_status sat_plan_layout_elems(const sat_plan* p, int32_t segment, int64_t B, uint64_t* act_elems,
                                  uint64_t* adj_elems);
+/* Which kernel runs the fused steps of this plan (sat_steps, sat_steps_aged,
+ * sat_steps_recompute, sat_steps_noalloc and the rounds of sat_sample_plan).
+ *   TILED: one CTA (or a 2-CTA cluster) per 128-sample tile, the activations and
+ *     adjoints in the tile's act / adj scratch in device memory, rows staged through
+ *     shared memory by TMA gathers.
+ *   RESIDENT: one CTA per 32 samples, every activation, adjoint and the inputs' V, m, v
+ *     in shared memory for all the launch's steps (device memory sees V, m, v read and
+ *     written once, and the loss); for circuits whose state fits: 32 x (cone nodes x
+ *     activation bytes + adjoint rows x 4 + cone inputs x 12) bytes <= 200 KiB.  The
+ *     act / adj scratch is then left untouched.
+ *   AUTO (the default): RESIDENT when the plan fits it with the call's act_dtype, else
+ *     TILED.
+ * Both kernels perform the same operations in the same order: V, m, v and the loss are
+ * bit-identical.  SAT_STEP_KERNEL_RESIDENT is refused (SAT_ERR_ARG) for a plan that fits it
+ * with no act_dtype; a step call whose act_dtype does not fit it returns SAT_ERR_CUDA.
+ * Set it before, not during, calls that use the plan.  sat_plan_step_kernel reports the
+ * kernel a step call with act_dtype would use (TILED or RESIDENT). */
+typedef enum { SAT_STEP_KERNEL_AUTO = 0, SAT_STEP_KERNEL_TILED = 1, SAT_STEP_KERNEL_RESIDENT = 2 } sat_step_kernel;
+sat_status sat_plan_set_step_kernel(sat_plan* p, int32_t kind);
+sat_status sat_plan_step_kernel(const sat_plan* p, int32_t act_dtype, int32_t* kind);
 void sat_plan_free(sat_plan* p);
 
 /* ------------------------------------------- hot-path kernels (device) ---
@@ -403,6 +423,8 @@ typedef struct sat_sample_opts {
                                    the budget stays max_rounds x steps descent steps of the batch */
     int32_t max_age;            /* early exit: restart samples unsolved after max_age steps (0 = steps) */
     int32_t recompute_segment;  /* > 0: level-segment recomputation (sat_steps_recompute); 0 = store all */
+    int32_t step_kernel;        /* sat_sample: sat_step_kernel of the plan it builds (sat_sample_plan uses
+                                   the plan's own setting) */
 } sat_sample_opts;
 
 typedef struct sat_sample_stats {

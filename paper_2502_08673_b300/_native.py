@@ -56,7 +56,7 @@ class SampleOpts(C.Structure):
                 ("act_dtype", C.c_int32), ("steps_per_launch", C.c_int32), ("init_logits", C.c_void_p),
                 ("init_ld", C.c_int64), ("stream", C.c_void_p), ("proposal", C.c_void_p),
                 ("proposal_tau", C.c_float), ("check_every", C.c_int32), ("max_age", C.c_int32),
-                ("recompute_segment", C.c_int32)]
+                ("recompute_segment", C.c_int32), ("step_kernel", C.c_int32)]
 
 
 class SampleStats(C.Structure):
@@ -90,6 +90,8 @@ PROTOTYPES = {
     "sat_cached_memory": (I32, [C.POINTER(U64), C.POINTER(U64)]),
     "sat_release_cached_memory": (I32, []),
     "sat_plan_status": (I32, [P, C.POINTER(U32), I32, P]),
+    "sat_plan_set_step_kernel": (I32, [P, I32]),
+    "sat_plan_step_kernel": (I32, [P, I32, C.POINTER(I32)]),
     "sat_plan_free": (None, [P]),
     "sat_init_normal": (I32, [P, U64, U32, F32, P, I64, I64, P]),
     "sat_forward": (I32, [P, I32, P, I64, P, P, I64, P]),

@@ -131,6 +131,20 @@ class Plan(_Handle):
         check(lib().sat_plan_status(self._h, C.byref(v), int(clear), _stream(stream)))
         return v.value
 
+    STEP_KERNELS = {"auto": 0, "tiled": 1, "resident": 2}
+    ACT_CODES = {"f32": 0, "bf16": 1, "f16": 2}
+
+    def set_step_kernel(self, kind: str = "auto") -> None:
+        """Kernel of the fused steps: "tiled", "resident" (shared-memory resident, for
+        circuits that fit) or "auto" (resident when it fits)."""
+        check(lib().sat_plan_set_step_kernel(self._h, self.STEP_KERNELS[kind]))
+
+    def step_kernel(self, act_dtype: str = "f32") -> str:
+        """The kernel ("tiled" or "resident") that a step call with act_dtype would use."""
+        k = C.c_int32()
+        check(lib().sat_plan_step_kernel(self._h, self.ACT_CODES[act_dtype], C.byref(k)))
+        return {1: "tiled", 2: "resident"}[k.value]
+
     def scratch_elems(self, B: int) -> int:
         n = C.c_uint64()
         check(lib().sat_plan_scratch_elems(self._h, B, C.byref(n)))
@@ -577,7 +591,7 @@ def release_cached_memory() -> None:
 def sample(circuit: Circuit, cnf: Cnf, n_wanted: int, batch=1024, steps=200, max_rounds=1, optimizer="adam",
            lr=0.1, beta1=0.9, beta2=0.999, eps=1e-8, seed=0, first_round=0, init_scale=1.0, act_dtype="f32",
            steps_per_launch=0, proposal: "Mlp | None" = None, tau: float = 1.0, check_every=0, max_age=0,
-           recompute_segment=0, stream=None):
+           recompute_segment=0, step_kernel="auto", stream=None):
     """End to end from host objects (the C call sat_sample); check_every > 0 = early exit;
     recompute_segment > 0 = level-segment recomputation in the fused steps."""
     o = N.SampleOpts()
@@ -591,6 +605,7 @@ def sample(circuit: Circuit, cnf: Cnf, n_wanted: int, batch=1024, steps=200, max
     o.proposal_tau = tau
     o.check_every, o.max_age = check_every, max_age
     o.recompute_segment = recompute_segment
+    o.step_kernel = Plan.STEP_KERNELS[step_kernel]
     h = C.c_void_p()
     st = N.SampleStats()
     status = check(lib().sat_sample(circuit.handle, cnf.handle, C.byref(o), n_wanted, C.byref(h), C.byref(st)),

@@ -23,6 +23,10 @@
 #include "host.hpp"
 
 static_assert(SAT_TILE == SAT_TILE_SAMPLES, "ABI tile width");
+static_assert((int)SAT_STEP_KERNEL_AUTO == (int)sat::STEP_KERNEL_AUTO &&
+                  (int)SAT_STEP_KERNEL_TILED == (int)sat::STEP_KERNEL_TILED &&
+                  (int)SAT_STEP_KERNEL_RESIDENT == (int)sat::STEP_KERNEL_RESIDENT,
+              "ABI step kernel codes");
 
 struct sat_cnf {
     sat::Cnf cnf;
@@ -298,6 +302,28 @@ sat_status sat_circuit_dump(const sat_circuit* c, char* buf, size_t cap, size_t*
 void sat_circuit_free(sat_circuit* c) { delete c; }
 
 // ---------------------------------------------------------------- plan --
+sat_status sat_plan_set_step_kernel(sat_plan* p, int32_t kind) {
+    if (!p) return fail(SAT_ERR_ARG, "NULL plan");
+    if (kind < SAT_STEP_KERNEL_AUTO || kind > SAT_STEP_KERNEL_RESIDENT) return fail(SAT_ERR_ARG, "bad step kernel");
+    if (kind == SAT_STEP_KERNEL_RESIDENT && !sat::resident_config(p->dp, sat::ACT_BF16, nullptr, nullptr))
+        return fail(SAT_ERR_ARG, "the plan does not fit the shared-memory resident kernel");
+    p->dp.step_kernel = kind;
+    return SAT_OK;
+}
+
+sat_status sat_plan_step_kernel(const sat_plan* p, int32_t act_dtype, int32_t* kind) {
+    if (!p || !kind) return fail(SAT_ERR_ARG, "NULL argument");
+    if (act_dtype < SAT_ACT_F32 || act_dtype > SAT_ACT_F16) return fail(SAT_ERR_ARG, "bad act_dtype");
+    const bool fits = sat::resident_config(p->dp, act_dtype, nullptr, nullptr);
+    if (p->dp.step_kernel == SAT_STEP_KERNEL_TILED || (p->dp.step_kernel == SAT_STEP_KERNEL_AUTO && !fits))
+        *kind = SAT_STEP_KERNEL_TILED;
+    else if (fits)
+        *kind = SAT_STEP_KERNEL_RESIDENT;
+    else
+        return fail(SAT_ERR_ARG, "resident step kernel requested, but the plan does not fit it with this act_dtype");
+    return SAT_OK;
+}
+
 void sat_plan_free(sat_plan* p) {
     if (!p) return;
     for (void* a : p->allocs) cudaFree(a);
@@ -910,6 +936,7 @@ void sat_sample_opts_default(sat_sample_opts* o) {
     o->check_every = 0;
     o->max_age = 0;
     o->recompute_segment = 0;
+    o->step_kernel = SAT_STEP_KERNEL_AUTO;
 }
 
 namespace {
@@ -1317,6 +1344,10 @@ sat_status sat_sample(const sat_circuit* c, const sat_cnf* cnf, const sat_sample
     sat_plan* p = nullptr;
     sat_status s = sat_plan_create(c, cnf, &p);
     if (s != SAT_OK) return s;
+    if (o->step_kernel != SAT_STEP_KERNEL_AUTO && (s = sat_plan_set_step_kernel(p, o->step_kernel)) != SAT_OK) {
+        sat_plan_free(p);
+        return s;
+    }
     struct PG {
         sat_plan* p;
         sat_dedup* d = nullptr;

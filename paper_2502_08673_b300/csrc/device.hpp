@@ -58,6 +58,7 @@ struct DevPlan {
     int32_t key_words = 0;              // ceil(n_pi / 32)
     unsigned int* status = nullptr;     // device status word (bit 2: an async-copy wait expired)
     DevAct full;                        // the full act layout (row = node)
+    int32_t step_kernel = 0;            // fused steps: STEP_KERNEL_AUTO / _TILED / _RESIDENT
     // host mirrors of the level offsets (launch loops need them)
     const int32_t* h_c_level_off = nullptr;
     const int32_t* h_f_level_off = nullptr;
@@ -70,6 +71,11 @@ inline __host__ __device__ int64_t adj_level_row(const DevPlan& p, int l, int32_
 }
 
 enum ActType { ACT_F32 = 0, ACT_BF16 = 1, ACT_F16 = 2 };
+
+// Kernel of the fused steps: AUTO takes the shared-memory resident kernel when the
+// plan's per-sample state fits (resident_config), else the tiled one.
+enum StepKernel { STEP_KERNEL_AUTO = 0, STEP_KERNEL_TILED = 1, STEP_KERNEL_RESIDENT = 2 };
+constexpr size_t RESIDENT_SMEM_MAX = 200u * 1024u;  // dynamic shared memory of one resident CTA
 
 struct OptParams {
     int opt = 0;  // 0 Adam, 1 GD
@@ -91,6 +97,12 @@ cudaError_t launch_backward(const DevPlan& p, int act_type, const float* V, int6
 cudaError_t launch_steps(const DevPlan& p, const DevAct& lay, int act_type, const OptParams& o, float* V, float* m,
                          float* v, int64_t ldv, void* act, float* adj, float* loss, int t0, int n_steps, int64_t B,
                          cudaStream_t s, const int32_t* age = nullptr);
+// The shared-memory resident kernel of the fused steps (32 samples per CTA): whether the
+// plan fits it with activations of act_type, its warps per CTA and dynamic shared memory.
+bool resident_config(const DevPlan& p, int act_type, int* warps, size_t* smem);
+cudaError_t launch_steps_resident(const DevPlan& p, int act_type, const OptParams& o, float* V, float* m, float* v,
+                                  int64_t ldv, float* loss, int t0, int n_steps, int64_t B, cudaStream_t s,
+                                  const int32_t* age = nullptr);
 // Early exit: restart[b] = valid(b) or age[b] + k >= max_age (bit-packed like valid);
 // age[b] = 0 where restarting, else age[b] + k.
 cudaError_t launch_retire(const uint32_t* valid, int32_t* age, uint32_t* restart, int k, int max_age, int64_t B,

@@ -23,6 +23,7 @@
 #include <cmath>
 
 #include "device.hpp"
+#include "relax.cuh"
 #include "tmap.hpp"
 
 namespace sat {
@@ -38,6 +39,9 @@ static_assert(TILE == SAT_TILE_SAMPLES, "tile width must match the ABI");
 // (their smaller staging slots leave room; measured best for each).
 template <typename T>
 __host__ __device__ constexpr int step_threads() { return sizeof(T) == 4 ? 640 : 768; }
+static_assert(step_threads<float>() / 32 == loss_partials<float>() &&
+                  step_threads<__half>() / 32 == loss_partials<__half>(),
+              "the tiled loss sums one partial per warp");
 constexpr int UBATCH = 2;              // input rows per warp in the input-level passes
 constexpr unsigned FULL = 0xffffffffu;
 
@@ -124,27 +128,7 @@ template <> struct ActIO<__half> {
     }
 };
 
-__device__ __forceinline__ float sigmoidf_(float v) { return 1.0f / (1.0f + expf(-v)); }
 
-// Bilinear coefficients (k0, k1, k2, k3) of gate code gop = op | neg0 << 2 |
-// neg1 << 3, with a' = n0 + s0 a and b' = n1 + s1 b (s = 1 - 2 n):
-//   AND a'b':         (n0 n1,             s0 n1,         n0 s1,         s0 s1)
-//   OR a'+b'-a'b':    (n0 + n1 - n0 n1,   s0 (1 - n1),   s1 (1 - n0),  -s0 s1)
-//   XOR a'+b'-2a'b':  (n0 + n1 - 2 n0 n1, s0 (1 - 2 n1), s1 (1 - 2 n0), -2 s0 s1)
-__device__ __forceinline__ float4 gate_coeffs(uint32_t gop) {
-    const float n0 = (float)((gop >> 2) & 1u), n1 = (float)((gop >> 3) & 1u);
-    const float s0 = 1.0f - 2.0f * n0, s1 = 1.0f - 2.0f * n1;
-    switch (gop & 3u) {
-    case 0: return make_float4(n0 * n1, s0 * n1, n0 * s1, s0 * s1);
-    case 1: return make_float4(n0 + n1 - n0 * n1, s0 * (1.0f - n1), s1 * (1.0f - n0), -s0 * s1);
-    default: return make_float4(n0 + n1 - 2.0f * n0 * n1, s0 * (1.0f - 2.0f * n1), s1 * (1.0f - 2.0f * n0),
-                                -2.0f * s0 * s1);
-    }
-}
-
-__device__ __forceinline__ float gate_apply(const float4& k, float a, float b) {
-    return fmaf(fmaf(k.w, a, k.z), b, fmaf(k.y, a, k.x));
-}
 
 // A tile is processed by one CTA, or (split mode) by the two CTAs of a
 // thread-block cluster, which divide every level's rows between their warps
@@ -189,15 +173,6 @@ __device__ __forceinline__ void level_sync(const TileCtx& c) {
         __syncthreads();
 }
 
-// Adam bias corrections at step t >= 1 (PyTorch: step_size = lr / (1 - b1^t),
-// sqrt(1 - b2^t)) in FP32: 1 - b^t = -expm1(t log1p(b - 1)).  b - 1 is exact in
-// FP32 for b in [1/2, 2], so both corrections keep ~1e-7 relative accuracy even
-// where b^t is within 1e-3 of 1 (b2 = 0.999 at t = 1).
-__device__ __forceinline__ void adam_bias(const OptParams& o, int t, float& step_size, float& bc2s) {
-    const float tf = (float)t;
-    step_size = o.lr / -expm1f(tf * log1pf(o.b1 - 1.0f));
-    bc2s = sqrtf(-expm1f(tf * log1pf(o.b2 - 1.0f)));
-}
 
 // Per-sample corrections of this lane's samples: step t, plus age[b] when
 // samples restart at different steps (early exit), else the same t for all.
@@ -699,25 +674,6 @@ __device__ void level_adjoint(const DevPlan& p, const DevAct& L, const AdjRun& r
     }
 }
 
-// dL/dV = Pbar * P (1 - P) for one sample, then GD (Eq. 9) or Adam (PyTorch's
-// formulation, no weight decay) on V, m, v at element r.
-template <bool UPDATE>
-__device__ __forceinline__ void input_update(const OptParams& o, float* V, float* m, float* v, float* gV, int64_t r,
-                                             float vv, float pbar, float mm, float ss, float step_size, float bc2s) {
-    const float P = sigmoidf_(vv);
-    const float g = pbar * P * (1.0f - P);
-    if (!UPDATE) {
-        gV[r] = g;
-    } else if (o.opt == 1) {
-        V[r] = fmaf(-o.lr, g, vv);
-    } else {
-        const float m1 = fmaf(1.0f - o.b1, g - mm, mm);
-        const float v1 = fmaf(o.b2, ss, (1.0f - o.b2) * g * g);
-        m[r] = m1;
-        v[r] = v1;
-        V[r] = vv - step_size * (m1 / (sqrtf(v1) / bc2s + o.eps));
-    }
-}
 
 // Discard, from L2, this tile's adjoint rows of cone level l (level 0 = the
 // inputs); the whole CTA shares the 128-byte lines.
@@ -1306,6 +1262,11 @@ cudaError_t launch_steps(const DevPlan& p, const DevAct& L, int act_type, const 
                          float* v, int64_t ldv, void* act, float* adj, float* loss, int t0, int n_steps, int64_t B,
                          cudaStream_t s, const int32_t* age) {
     if (B == 0 || n_steps <= 0) return cudaSuccess;
+    if (p.step_kernel != STEP_KERNEL_TILED) {
+        if (resident_config(p, act_type, nullptr, nullptr))
+            return launch_steps_resident(p, act_type, o, V, m, v, ldv, loss, t0, n_steps, B, s, age);
+        if (p.step_kernel == STEP_KERNEL_RESIDENT) return cudaErrorInvalidValue;
+    }
     switch (act_type) {
     case ACT_F32: return steps_launch<float>(p, L, o, V, m, v, ldv, act, adj, loss, t0, age, n_steps, B, s);
     case ACT_BF16: return steps_launch<__nv_bfloat16>(p, L, o, V, m, v, ldv, act, adj, loss, t0, age, n_steps, B, s);

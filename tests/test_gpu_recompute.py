@@ -20,10 +20,14 @@ torch = pytest.importorskip("torch")
 
 
 def _plan(text):
+    """A plan on the tiled step kernel (the one with act layouts; small circuits would
+    otherwise run on the shared-memory resident kernel, which keeps no act scratch)."""
     import paper_2502_08673_b300 as P
     cnf = P.Cnf.from_dimacs(text)
     circ = P.Circuit.build(cnf)
-    return P, cnf, circ, P.Plan.create(circ, cnf)
+    plan = P.Plan.create(circ, cnf)
+    plan.set_step_kernel("tiled")
+    return P, cnf, circ, plan
 
 
 def _mid_output_text(seed=4):
@@ -117,7 +121,7 @@ def test_sampler_with_recompute_same_solutions(gpu):
     text = tseitin_random_circuit(64, 640, 16, 8, seed=3).dimacs()
     cnf = P.Cnf.from_dimacs(text)
     circ = P.Circuit.build(cnf)
-    kw = dict(n_wanted=10 ** 9, batch=512, steps=60, max_rounds=2, lr=0.1, seed=9)
+    kw = dict(n_wanted=10 ** 9, batch=512, steps=60, max_rounds=2, lr=0.1, seed=9, step_kernel="tiled")
     a = P.sample(circ, cnf, **kw)
     b = P.sample(circ, cnf, recompute_segment=6, **kw)
     assert len(a) > 0
