@@ -36,6 +36,10 @@ def test_null_objects_are_rejected():
     a, g = C.c_uint64(), C.c_uint64()
     _err(L.sat_plan_layout_elems(None, 8, 128, C.byref(a), C.byref(g)))
     _err(L.sat_threshold(None, None, 0, None, 0, None, 0, None))
+    k = C.c_int32()
+    _err(L.sat_plan_set_step_kernel(None, 0))
+    _err(L.sat_plan_step_kernel(None, 0, C.byref(k)))
+    _err(L.sat_cached_memory(None, None))
     assert L.sat_solutions_count(None) == 0
 
 
