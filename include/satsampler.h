@@ -328,6 +328,14 @@ sat_status sat_dedup_insert(sat_dedup* d, const uint32_t* keys, const uint32_t* 
                             uint8_t* is_new, void* stream);
 /* Number of stored keys (synchronises `stream`). */
 sat_status sat_dedup_count(const sat_dedup* d, uint64_t* n, void* stream);
+/* sat_dedup_insert without its two host synchronisations (the capacity check before the
+ * launch and the status read after it), for loops that keep the device busy: the kernels
+ * guard the pool on the device, and a batch that did not fit or hit the probe limit is
+ * recorded in the set's status word (its keys are then incomplete).  sat_dedup_check
+ * synchronises the stream and returns SAT_ERR_TABLE_FULL if any insert so far failed. */
+sat_status sat_dedup_insert_async(sat_dedup* d, const uint32_t* keys, const uint32_t* valid, int64_t B,
+                                  void* stream);
+sat_status sat_dedup_check(const sat_dedup* d, void* stream);
 /* Copies stored keys [first, first+count) to host memory (synchronous). */
 sat_status sat_dedup_copy_keys(const sat_dedup* d, uint64_t first, uint64_t count, uint32_t* host_keys, void* stream);
 sat_status sat_dedup_clear(sat_dedup* d, void* stream);

@@ -108,6 +108,8 @@ PROTOTYPES = {
     "sat_cnf_check": (I32, [P, P, I64, P, I64, P]),
     "sat_dedup_create": (I32, [P, U64, I64, PP]),
     "sat_dedup_insert": (I32, [P, P, P, I64, P, P, P]),
+    "sat_dedup_insert_async": (I32, [P, P, P, I64, P]),
+    "sat_dedup_check": (I32, [P, P]),
     "sat_dedup_count": (I32, [P, C.POINTER(U64), P]),
     "sat_dedup_copy_keys": (I32, [P, U64, U64, P, P]),
     "sat_dedup_clear": (I32, [P, P]),

@@ -184,9 +184,19 @@ class Dedup(_Handle):
         d.max_batch = max_batch
         return d
 
-    def insert(self, keys, valid, B: int, hashes=None, is_new=None, stream=None):
+    def insert(self, keys, valid, B: int, hashes=None, is_new=None, stream=None, sync=True):
+        """Insert a batch; sync=False skips the host synchronisations (sat_dedup_insert_async:
+        failures are reported later by check())."""
+        if not sync:
+            assert hashes is None and is_new is None
+            check(lib().sat_dedup_insert_async(self._h, _ptr(keys), _ptr(valid), B, _stream(stream)))
+            return
         check(lib().sat_dedup_insert(self._h, _ptr(keys), _ptr(valid), B, _ptr(hashes), _ptr(is_new),
                                      _stream(stream)))
+
+    def check(self, stream=None) -> None:
+        """Raise SatError(SAT_ERR_TABLE_FULL) if any insert so far did not fit."""
+        check(lib().sat_dedup_check(self._h, _stream(stream)))
 
     def count(self, stream=None) -> int:
         n = C.c_uint64()

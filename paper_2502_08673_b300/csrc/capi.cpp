@@ -895,6 +895,28 @@ sat_status sat_dedup_insert(sat_dedup* d, const uint32_t* keys, const uint32_t* 
     return SAT_OK;
 }
 
+sat_status sat_dedup_insert_async(sat_dedup* d, const uint32_t* keys, const uint32_t* valid, int64_t B,
+                                  void* stream) {
+    if (!d) return fail(SAT_ERR_ARG, "NULL dedup");
+    if (B < 0 || B > d->max_batch) return fail(SAT_ERR_ARG, "B outside 0..max_batch");
+    if (B > 0 && (!keys || !valid)) return fail(SAT_ERR_ARG, "NULL buffer");
+    sat_status s = check_device(d->device);
+    if (s != SAT_OK) return s;
+    // the commit kernel refuses slots past the pool's capacity (status bit 1) and the insert
+    // kernel stops at the probe limit (bit 0): nothing is written out of bounds
+    CK(sat::launch_dedup_insert(d->d, keys, valid, B, nullptr, nullptr, d->slot_of, S(stream)));
+    return SAT_OK;
+}
+
+sat_status sat_dedup_check(const sat_dedup* d, void* stream) {
+    if (!d) return fail(SAT_ERR_ARG, "NULL dedup");
+    unsigned int status = 0;
+    CK(cudaMemcpyAsync(&status, d->d.status, sizeof(status), cudaMemcpyDeviceToHost, S(stream)));
+    CK(cudaStreamSynchronize(S(stream)));
+    if (status) return fail(SAT_ERR_TABLE_FULL, "dedup table full or probe limit reached");
+    return SAT_OK;
+}
+
 sat_status sat_dedup_copy_keys(const sat_dedup* d, uint64_t first, uint64_t count, uint32_t* host_keys,
                                void* stream) {
     if (!d || (count && !host_keys)) return fail(SAT_ERR_ARG, "NULL argument");

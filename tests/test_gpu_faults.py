@@ -64,6 +64,22 @@ def test_dedup_table_too_small(gpu):
         dd.insert(ws.keys, ws.valid, 256)
     assert e.value.status == SAT_ERR_TABLE_FULL
     assert dd.count() == 0
+    # the asynchronous insert finds the overflow on the device (here every one of 256 random
+    # assignments of a clause-free CNF is valid and distinct); check() reports it
+    cnf0 = P.Cnf.from_dimacs("p cnf 20 0\n")
+    plan0 = P.Plan.create(P.Circuit.build(cnf0), cnf0)
+    ws0 = P.new_workspace(plan0, 256)
+    P.sat_init_normal(plan0, ws0.V, seed=0, round_=0)
+    P.sat_threshold(plan0, ws0.V, ws0.bits, ws0.keys)
+    P.sat_hard_eval(plan0, ws0.bits, 256)
+    P.sat_cnf_check(plan0, ws0.bits, ws0.valid, 256)
+    assert P.valid_mask(ws0.valid, 256).all()
+    dd2 = P.Dedup.create(plan0, max_keys=100, max_batch=256)
+    dd2.insert(ws0.keys, ws0.valid, 256, sync=False)
+    with pytest.raises(P.SatError) as e2:
+        dd2.check()
+    assert e2.value.status == SAT_ERR_TABLE_FULL
+    assert dd2.count() <= 100
     # the end-to-end loop on the plan reports the same code
     from paper_2502_08673_b300 import _native as N
     o = N.SampleOpts()
@@ -120,3 +136,22 @@ def test_degenerate_instances_end_to_end(gpu):
     assert len(A) == 8
     key = A.astype(np.int64) @ (1 << np.arange(3))
     assert key.tolist() == list(range(8))
+
+
+def test_async_insert_equals_sync(gpu):
+    """sat_dedup_insert_async stores the same distinct keys as sat_dedup_insert."""
+    import paper_2502_08673_b300 as P
+    text = planted_3sat(50, 200, 1).dimacs()
+    cnf = P.Cnf.from_dimacs(text)
+    plan = P.Plan.create(P.Circuit.build(cnf), cnf)
+    ws = P.new_workspace(plan, 4096)
+    a = P.Dedup.create(plan, max_keys=40000, max_batch=4096)
+    b = P.Dedup.create(plan, max_keys=40000, max_batch=4096)
+    for r in range(6):
+        P.run_round(plan, ws, P.opt_params("adam", lr=0.1), steps=60, seed=1, round_=r)
+        a.insert(ws.keys, ws.valid, 4096)
+        b.insert(ws.keys, ws.valid, 4096, sync=False)
+    b.check()
+    ka, kb = a.keys(), b.keys()
+    assert len(ka) > 0
+    assert sorted(map(bytes, ka)) == sorted(map(bytes, kb))
