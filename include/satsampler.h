@@ -442,16 +442,17 @@ typedef struct sat_sample_stats {
     double ms_upload, ms_download;                              /* sat_sample only */
 } sat_sample_stats;
 
-/* Memory of the end-to-end calls.  The workspace of sat_sample / sat_sample_plan (and the
- * buffers that order sat_sample's solutions) comes from the library's own stream-ordered
- * pool on the current device, which keeps the memory it has reserved when those buffers
- * are freed, so a repeated call maps no new device memory.  sat_cached_memory reports the
+/* Device memory.  The workspace of sat_sample / sat_sample_plan (and the buffers that
+ * order sat_sample's solutions), and the arrays of plans and dedup sets, come from the
+ * library's own stream-ordered pool on the current device (plans and dedup sets are
+ * allocated and freed in order on the legacy default stream), which keeps the memory it
+ * has reserved when those buffers are freed, so a repeated call maps no new device memory
+ * and freeing does not wait for the device.  sat_cached_memory reports the
  * pool's reserved and in-use bytes; sat_release_cached_memory returns the reserve that no
  * allocation (or queued work) still uses to the device, and frees the host buffers kept
  * between calls: the pinned buffer that solutions are downloaded through and the key
  * buffers of up to two freed solution sets (1 MiB-256 MiB each), which the next
- * sat_sample reuses.  Plans, dedup sets and networks are allocated separately and are not
- * part of the pool. */
+ * sat_sample reuses.  Proposal networks are allocated separately (cudaMalloc). */
 sat_status sat_cached_memory(uint64_t* reserved_bytes, uint64_t* used_bytes);
 sat_status sat_release_cached_memory(void);
 

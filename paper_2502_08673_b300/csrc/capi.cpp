@@ -116,15 +116,67 @@ sat_status fail(sat_status s, const std::string& m) {
         if (e_ != cudaSuccess) return fail(SAT_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
+// The library's own stream-ordered memory pool of each device.  It keeps the memory it
+// has reserved when buffers are freed (release threshold: unlimited), so a repeated
+// call maps no new device memory and freeing does not synchronise the device;
+// sat_release_cached_memory hands the reserve back.
+constexpr int MAX_DEVICES = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[MAX_DEVICES] = {};
+
+cudaError_t library_pool(cudaMemPool_t* out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if ((e = cudaMemPoolCreate(&pool, &props)) != cudaSuccess) return e;
+        uint64_t keep = ~0ull;
+        if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return e;
+        }
+        g_pools[dev] = pool;
+    }
+    *out = g_pools[dev];
+    return cudaSuccess;
+}
+
+// Device arrays of plans and dedup sets: from the library pool, in stream order on the
+// legacy default stream (ordered after the work of every blocking stream), so that
+// creating and freeing the objects of an end-to-end call neither maps memory nor waits
+// for the device.  An allocation the pool cannot serve is retried once after the pool's
+// idle reserve is returned.
+bool obj_alloc(void** p, size_t n) {
+    cudaMemPool_t pool = nullptr;
+    if (library_pool(&pool) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (cudaMallocFromPoolAsync(p, n ? n : 16, pool, 0) == cudaSuccess) return true;
+    cudaGetLastError();
+    cudaMemPoolTrimTo(pool, 0);
+    if (cudaMallocFromPoolAsync(p, n ? n : 16, pool, 0) == cudaSuccess) return true;
+    cudaGetLastError();
+    *p = nullptr;
+    return false;
+}
+void obj_free(void* p) {
+    if (p) cudaFreeAsync(p, 0);
+}
+
 template <typename T>
 sat_status upload_to(std::vector<void*>& allocs, const std::vector<T>& h, const T** dst) {
     *dst = nullptr;
     if (h.empty()) return SAT_OK;
     void* d = nullptr;
-    if (cudaMalloc(&d, h.size() * sizeof(T)) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(SAT_ERR_OOM, "cudaMalloc failed for plan array");
-    }
+    if (!obj_alloc(&d, h.size() * sizeof(T))) return fail(SAT_ERR_OOM, "device allocation failed for plan array");
     allocs.push_back(d);
     CK(cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
     *dst = (const T*)d;
@@ -326,8 +378,8 @@ sat_status sat_plan_step_kernel(const sat_plan* p, int32_t act_dtype, int32_t* k
 
 void sat_plan_free(sat_plan* p) {
     if (!p) return;
-    for (void* a : p->allocs) cudaFree(a);
-    for (void* a : p->lay_allocs) cudaFree(a);
+    for (void* a : p->allocs) obj_free(a);
+    for (void* a : p->lay_allocs) obj_free(a);
     delete p;
 }
 
@@ -421,10 +473,8 @@ sat_status sat_plan_create(const sat_circuit* c, const sat_cnf* cnf, sat_plan** 
     p->h_out = P.c_out_node;
     {
         void* w = nullptr;
-        if (cudaMalloc(&w, sizeof(unsigned int)) != cudaSuccess) {
-            cudaGetLastError();
-            return bail(fail(SAT_ERR_OOM, "cudaMalloc failed for the status word"));
-        }
+        if (!obj_alloc(&w, sizeof(unsigned int)))
+            return bail(fail(SAT_ERR_OOM, "device allocation failed for the status word"));
         p->allocs.push_back(w);
         d.status = (unsigned int*)w;
         CK(cudaMemset(w, 0, sizeof(unsigned int)));
@@ -820,11 +870,11 @@ sat_status sat_cnf_check(const sat_plan* p, const uint32_t* node_bits, int64_t l
 // --------------------------------------------------------------- dedup --
 void sat_dedup_free(sat_dedup* d) {
     if (!d) return;
-    cudaFree(d->d.slots);
-    cudaFree(d->d.pool);
-    cudaFree(d->d.count);
-    cudaFree(d->d.status);
-    cudaFree(d->slot_of);
+    obj_free(d->d.slots);
+    obj_free(d->d.pool);
+    obj_free(d->d.count);
+    obj_free(d->d.status);
+    obj_free(d->slot_of);
     delete d;
 }
 
@@ -842,14 +892,13 @@ sat_status sat_dedup_create(const sat_plan* p, uint64_t max_keys, int64_t max_ba
     d->d.pool_capacity = max_keys;
     d->d.max_probe = (uint32_t)std::min<uint64_t>(cap, 1u << 20);
     const size_t kw = (size_t)std::max(1, d->d.key_words);
-    if (cudaMalloc(&d->d.slots, cap * sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMalloc(&d->d.pool, std::max<uint64_t>(max_keys, 1) * kw * sizeof(uint32_t)) != cudaSuccess ||
-        cudaMalloc(&d->d.count, sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMalloc(&d->d.status, sizeof(unsigned int)) != cudaSuccess ||
-        cudaMalloc(&d->slot_of, std::max<int64_t>(max_batch, 1) * sizeof(unsigned long long)) != cudaSuccess) {
-        cudaGetLastError();
+    if (!obj_alloc((void**)&d->d.slots, cap * sizeof(unsigned long long)) ||
+        !obj_alloc((void**)&d->d.pool, std::max<uint64_t>(max_keys, 1) * kw * sizeof(uint32_t)) ||
+        !obj_alloc((void**)&d->d.count, sizeof(unsigned long long)) ||
+        !obj_alloc((void**)&d->d.status, sizeof(unsigned int)) ||
+        !obj_alloc((void**)&d->slot_of, std::max<int64_t>(max_batch, 1) * sizeof(unsigned long long))) {
         sat_dedup_free(d);
-        return fail(SAT_ERR_OOM, "cudaMalloc failed for the dedup table");
+        return fail(SAT_ERR_OOM, "device allocation failed for the dedup table");
     }
     cudaError_t e = sat::launch_dedup_clear(d->d, 0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(0);
@@ -963,36 +1012,6 @@ void sat_sample_opts_default(sat_sample_opts* o) {
 
 namespace {
 
-// The library's own stream-ordered memory pool of each device.  It keeps the memory it
-// has reserved when buffers are freed (release threshold: unlimited), so a repeated
-// call maps no new device memory; sat_release_cached_memory hands it back.
-constexpr int MAX_DEVICES = 64;
-std::mutex g_pool_mu;
-cudaMemPool_t g_pools[MAX_DEVICES] = {};
-
-cudaError_t library_pool(cudaMemPool_t* out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lk(g_pool_mu);
-    if (!g_pools[dev]) {
-        cudaMemPoolProps props = {};
-        props.allocType = cudaMemAllocationTypePinned;
-        props.location.type = cudaMemLocationTypeDevice;
-        props.location.id = dev;
-        cudaMemPool_t pool = nullptr;
-        if ((e = cudaMemPoolCreate(&pool, &props)) != cudaSuccess) return e;
-        uint64_t keep = ~0ull;
-        if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) {
-            cudaMemPoolDestroy(pool);
-            return e;
-        }
-        g_pools[dev] = pool;
-    }
-    *out = g_pools[dev];
-    return cudaSuccess;
-}
 
 // A pinned host buffer, kept between calls, through which sat_sample downloads the
 // ordered keys: a device-to-host copy into pageable memory runs at a fraction of the

@@ -311,7 +311,11 @@ def test_workspace_pool_kept_between_calls_and_released(gpu):
     text = planted_3sat(50, 200, 1).dimacs()
     cnf = P.Cnf.from_dimacs(text)
     circ = P.Circuit.build(cnf)
+    import gc
+    gc.collect()
+    torch.cuda.synchronize()
     P.release_cached_memory()
+    r0, u0 = P.cached_memory()  # plans or dedup sets still alive elsewhere in this process
 
     def run():
         s = P.sample(circ, cnf, n_wanted=10 ** 9, batch=2048, steps=100, max_rounds=1, lr=0.1, seed=4)
@@ -321,12 +325,13 @@ def test_workspace_pool_kept_between_calls_and_released(gpu):
     A = run()
     reserved, used = P.cached_memory()
     # at least V, m and v of the batch: 3 x 50 inputs x 2048 samples x 4 B
-    assert reserved >= 3 * 50 * 2048 * 4
-    assert used == 0
+    assert reserved - r0 >= 3 * 50 * 2048 * 4
+    assert used == u0
     B = run()
-    assert P.cached_memory() == (reserved, 0)
+    assert P.cached_memory() == (reserved, u0)
     P.release_cached_memory()
-    assert P.cached_memory() == (0, 0)
+    r2, u2 = P.cached_memory()
+    assert u2 == u0 and r2 < reserved
     C_ = run()
     assert len(A) > 0
     np.testing.assert_array_equal(A, B)
