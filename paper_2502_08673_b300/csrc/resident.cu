@@ -63,8 +63,9 @@ __global__ void __launch_bounds__(RES_MAX_WARPS * 32, 1) resident_steps_kernel(D
     const int64_t b = (int64_t)blockIdx.x * RES_LANES + lane;
     const bool valid = b < B;
     const ResLayout lay = res_layout(p, (int)sizeof(T));
-    T* act = reinterpret_cast<T*>(smem);
-    float* adj = reinterpret_cast<float*>(smem + lay.adj);
+    // this lane's column of the act and adj rows (rows are < 2^27: 32-bit offsets)
+    T* act = reinterpret_cast<T*>(smem) + lane;
+    float* adj = reinterpret_cast<float*>(smem + lay.adj) + lane;
     float* sV = reinterpret_cast<float*>(smem + lay.vmv);
     float* sm = sV + (size_t)p.n_cone_pi * RES_LANES;
     float* sv = sm + (size_t)p.n_cone_pi * RES_LANES;
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(RES_MAX_WARPS * 32, 1) resident_steps_kernel(D
         float step_size = 1.0f, bc2s = 1.0f;
         if (adam) adam_bias(o, t0 + s + my_age, step_size, bc2s);
         // forward: the inputs' embedding, then the gate levels
-        for (int i = warp; i < npi; i += nw) Scalar<T>::st(act + i * RES_LANES + lane, sigmoidf_(sV[i * RES_LANES + lane]));
+        for (int i = warp; i < npi; i += nw) Scalar<T>::st(act + i * RES_LANES, sigmoidf_(sV[i * RES_LANES + lane]));
         __syncthreads();
         for (int l = 1; l <= p.n_clev; l++) {
             const int lo = __ldg(&p.c_level_off[l]), hi = __ldg(&p.c_level_off[l + 1]);
@@ -103,14 +104,14 @@ __global__ void __launch_bounds__(RES_MAX_WARPS * 32, 1) resident_steps_kernel(D
                 }
 #pragma unroll
                 for (int j = 0; j < GB; j++) {
-                    x[j] = Scalar<T>::ld(act + (rec[j].x & 0x0FFFFFFF) * RES_LANES + lane);
-                    y[j] = Scalar<T>::ld(act + rec[j].y * RES_LANES + lane);
+                    x[j] = Scalar<T>::ld(act + (rec[j].x & 0x0FFFFFFF) * RES_LANES);
+                    y[j] = Scalar<T>::ld(act + rec[j].y * RES_LANES);
                 }
 #pragma unroll
                 for (int j = 0; j < GB; j++) {
                     const int g = g0 + j * nw;
                     if (g < hi)
-                        Scalar<T>::st(act + g * RES_LANES + lane, gate_apply(gcoef[(uint32_t)rec[j].x >> 28], x[j], y[j]));
+                        Scalar<T>::st(act + g * RES_LANES, gate_apply(gcoef[(uint32_t)rec[j].x >> 28], x[j], y[j]));
                 }
             }
             __syncthreads();
@@ -122,7 +123,7 @@ __global__ void __launch_bounds__(RES_MAX_WARPS * 32, 1) resident_steps_kernel(D
             for (int w = 0; w < NP; w++) {
                 float acc = 0.0f;
                 for (int j = w; j < p.n_out; j += NP) {
-                    const float yj = Scalar<T>::ld(act + __ldg(&p.full.out_row[j]) * RES_LANES + lane);
+                    const float yj = Scalar<T>::ld(act + __ldg(&p.full.out_row[j]) * RES_LANES);
                     const float tj = p.out_target[j];
                     acc = fmaf(yj - tj, yj - tj, acc);
                 }
@@ -131,12 +132,12 @@ __global__ void __launch_bounds__(RES_MAX_WARPS * 32, 1) resident_steps_kernel(D
             if (valid) loss[b] = sum;
         }
         // adjoint (gather form of Eq. 8): the seed row is each sample's loss weight (1)
-        if (warp == 0) adj[(size_t)p.seed_row * RES_LANES + lane] = 1.0f;
+        if (warp == 0) adj[p.seed_row * RES_LANES] = 1.0f;
         __syncthreads();
         for (int l = p.n_clev; l >= 0; l--) {
             const int lo = l == 0 ? 0 : __ldg(&p.c_level_off[l]);
             const int hi = l == 0 ? npi : __ldg(&p.c_level_off[l + 1]);
-            const int64_t row0 = l == 0 ? 0 : adj_level_row(p, l, lo);
+            const int row0 = l == 0 ? 0 : (int)adj_level_row(p, l, lo);
             for (int u = lo + warp; u < hi; u += nw) {
                 const int e0 = __ldg(&p.fo_off[u]), e1 = __ldg(&p.fo_off[u + 1]);
                 float acc = 0.0f;
@@ -149,14 +150,14 @@ __global__ void __launch_bounds__(RES_MAX_WARPS * 32, 1) resident_steps_kernel(D
                     for (int j = 0; j < EB; j++) ed[j] = eb + j < e1 ? __ldg(&p.full.edge[eb + j]) : make_int4(0, 0, 0, 0);
 #pragma unroll
                     for (int j = 0; j < EB; j++) {
-                        ga[j] = adj[ed[j].x * RES_LANES + lane];
-                        sib[j] = Scalar<T>::ld(act + (ed[j].y & 0x7FFFFFFF) * RES_LANES + lane);
+                        ga[j] = adj[ed[j].x * RES_LANES];
+                        sib[j] = Scalar<T>::ld(act + (ed[j].y & 0x7FFFFFFF) * RES_LANES);
                     }
 #pragma unroll
                     for (int j = 0; j < EB; j++)
                         if (eb + j < e1) acc = fmaf(ga[j], fmaf(__int_as_float(ed[j].w), sib[j], __int_as_float(ed[j].z)), acc);
                 }
-                adj[(row0 + (u - lo)) * RES_LANES + lane] = acc;
+                adj[(row0 + (u - lo)) * RES_LANES] = acc;
             }
             __syncthreads();
         }
@@ -164,7 +165,7 @@ __global__ void __launch_bounds__(RES_MAX_WARPS * 32, 1) resident_steps_kernel(D
         if (valid)
             for (int i = warp; i < npi; i += nw) {
                 const int e = i * RES_LANES + lane;
-                input_update<true>(o, sV, sm, sv, nullptr, e, sV[e], adj[e], sm[e], sv[e], step_size, bc2s);
+                input_update<true>(o, sV, sm, sv, nullptr, e, sV[e], adj[i * RES_LANES], sm[e], sv[e], step_size, bc2s);
             }
         __syncthreads();
     }
