@@ -185,13 +185,10 @@ template <typename T>
 cudaError_t resident_launch(const DevPlan& p, const OptParams& o, float* V, float* m, float* v, int64_t ldv,
                             float* loss, int t0, const int32_t* age, int n_steps, int64_t B, int warps, size_t smem,
                             cudaStream_t s) {
-    static bool prepared = false;  // one opt-in per type (idempotent, so a race is harmless)
-    if (!prepared) {
-        cudaError_t e = cudaFuncSetAttribute(resident_steps_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)RESIDENT_SMEM_MAX);
-        if (e != cudaSuccess) return e;
-        prepared = true;
-    }
+    // the opt-in to the dynamic shared memory, once per type (thread-safe static initialisation)
+    static const cudaError_t prepared = cudaFuncSetAttribute(
+        resident_steps_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RESIDENT_SMEM_MAX);
+    if (prepared != cudaSuccess) return prepared;
     const unsigned grid = (unsigned)((B + RES_LANES - 1) / RES_LANES);
     resident_steps_kernel<T><<<grid, warps * 32, smem, s>>>(p, o, V, m, v, ldv, loss, t0, age, n_steps, B);
     return cudaGetLastError();
