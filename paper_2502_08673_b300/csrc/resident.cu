@@ -54,7 +54,7 @@ __host__ __device__ inline ResLayout res_layout(const DevPlan& p, int act_bytes)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(RES_MAX_WARPS * 32, 1) resident_steps_kernel(DevPlan p, OptParams o, float* V, float* m,
+__global__ void __maxnreg__(80) resident_steps_kernel(DevPlan p, OptParams o, float* V, float* m,
                                                                            float* v, int64_t ldv, float* loss, int t0,
                                                                            const int32_t* age, int n_steps, int64_t B) {
     extern __shared__ __align__(16) char smem[];
@@ -92,27 +92,28 @@ __global__ void __launch_bounds__(RES_MAX_WARPS * 32, 1) resident_steps_kernel(D
             const int lo = __ldg(&p.c_level_off[l]), hi = __ldg(&p.c_level_off[l + 1]);
             // GB gates of this warp at a time: their records and inputs are all loaded before
             // the first result is stored (a gate's inputs lie on lower levels, so no result of
-            // this level is among them)
+            // this level is among them); the last few gates of the warp's share one by one
             constexpr int GB = 4;
-            for (int g0 = lo + warp; g0 < hi; g0 += GB * nw) {
+            int g = lo + warp;
+            for (; g + (GB - 1) * nw < hi; g += GB * nw) {
                 int2 rec[GB];
                 float x[GB], y[GB];
 #pragma unroll
-                for (int j = 0; j < GB; j++) {
-                    const int g = g0 + j * nw;
-                    rec[j] = g < hi ? __ldg(&p.full.gate[g - npi]) : make_int2(0, 0);
-                }
+                for (int j = 0; j < GB; j++) rec[j] = __ldg(&p.full.gate[g + j * nw - npi]);
 #pragma unroll
                 for (int j = 0; j < GB; j++) {
                     x[j] = Scalar<T>::ld(act + (rec[j].x & 0x0FFFFFFF) * RES_LANES);
                     y[j] = Scalar<T>::ld(act + rec[j].y * RES_LANES);
                 }
 #pragma unroll
-                for (int j = 0; j < GB; j++) {
-                    const int g = g0 + j * nw;
-                    if (g < hi)
-                        Scalar<T>::st(act + g * RES_LANES, gate_apply(gcoef[(uint32_t)rec[j].x >> 28], x[j], y[j]));
-                }
+                for (int j = 0; j < GB; j++)
+                    Scalar<T>::st(act + (g + j * nw) * RES_LANES, gate_apply(gcoef[(uint32_t)rec[j].x >> 28], x[j], y[j]));
+            }
+            for (; g < hi; g += nw) {
+                const int2 rec = __ldg(&p.full.gate[g - npi]);
+                const float x = Scalar<T>::ld(act + (rec.x & 0x0FFFFFFF) * RES_LANES);
+                const float y = Scalar<T>::ld(act + rec.y * RES_LANES);
+                Scalar<T>::st(act + g * RES_LANES, gate_apply(gcoef[(uint32_t)rec.x >> 28], x, y));
             }
             __syncthreads();
         }
@@ -141,13 +142,15 @@ __global__ void __launch_bounds__(RES_MAX_WARPS * 32, 1) resident_steps_kernel(D
             for (int u = lo + warp; u < hi; u += nw) {
                 const int e0 = __ldg(&p.fo_off[u]), e1 = __ldg(&p.fo_off[u + 1]);
                 float acc = 0.0f;
-                // EB edges at a time: records and operands loaded first, then summed in CSR order
+                // EB edges at a time (records and operands loaded first, then summed in CSR
+                // order), the rest one by one
                 constexpr int EB = 4;
-                for (int eb = e0; eb < e1; eb += EB) {
+                int e = e0;
+                for (; e + EB <= e1; e += EB) {
                     int4 ed[EB];
                     float ga[EB], sib[EB];
 #pragma unroll
-                    for (int j = 0; j < EB; j++) ed[j] = eb + j < e1 ? __ldg(&p.full.edge[eb + j]) : make_int4(0, 0, 0, 0);
+                    for (int j = 0; j < EB; j++) ed[j] = __ldg(&p.full.edge[e + j]);
 #pragma unroll
                     for (int j = 0; j < EB; j++) {
                         ga[j] = adj[ed[j].x * RES_LANES];
@@ -155,7 +158,13 @@ __global__ void __launch_bounds__(RES_MAX_WARPS * 32, 1) resident_steps_kernel(D
                     }
 #pragma unroll
                     for (int j = 0; j < EB; j++)
-                        if (eb + j < e1) acc = fmaf(ga[j], fmaf(__int_as_float(ed[j].w), sib[j], __int_as_float(ed[j].z)), acc);
+                        acc = fmaf(ga[j], fmaf(__int_as_float(ed[j].w), sib[j], __int_as_float(ed[j].z)), acc);
+                }
+                for (; e < e1; e++) {
+                    const int4 ed = __ldg(&p.full.edge[e]);
+                    const float ga = adj[ed.x * RES_LANES];
+                    const float sib = Scalar<T>::ld(act + (ed.y & 0x7FFFFFFF) * RES_LANES);
+                    acc = fmaf(ga, fmaf(__int_as_float(ed.w), sib, __int_as_float(ed.z)), acc);
                 }
                 adj[(row0 + (u - lo)) * RES_LANES] = acc;
             }
