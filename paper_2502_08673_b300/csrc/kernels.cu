@@ -911,17 +911,17 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 ctr, uint2 key) {
 }
 
 // V[r][b] = scale * sqrt(-2 ln u1) cos(2 pi u2), (u1, u2) from counter (b, r, round, 0).
+// Samples on x (coalesced within a row), rows on y, both grid-stride.
 __global__ void init_normal_kernel(int32_t n_pi, uint64_t seed, uint32_t round, float scale, float* V, int64_t ldv,
                                    int64_t B) {
-    const int64_t n = (int64_t)n_pi * B;
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = k / B, b = k % B;
-        const uint4 o = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)r, round, 0u), key);
-        const float u1 = (float)((o.x >> 8) + 1u) * (1.0f / 16777216.0f);
-        const float u2 = (float)(o.y >> 8) * (1.0f / 16777216.0f);
-        V[r * ldv + b] = scale * sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
-    }
+    for (int64_t r = blockIdx.y; r < n_pi; r += gridDim.y)
+        for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < B; b += (int64_t)gridDim.x * blockDim.x) {
+            const uint4 o = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)r, round, 0u), key);
+            const float u1 = (float)((o.x >> 8) + 1u) * (1.0f / 16777216.0f);
+            const float u2 = (float)(o.y >> 8) * (1.0f / 16777216.0f);
+            V[r * ldv + b] = scale * sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+        }
 }
 
 // ------------------------------------------------------- early exit -----
@@ -1233,7 +1233,7 @@ cudaError_t launch_init_normal(const DevPlan& p, uint64_t seed, uint32_t round, 
                                int64_t B, cudaStream_t s) {
     const int64_t n = (int64_t)p.n_pi * B;
     if (n == 0) return cudaSuccess;
-    const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 148 * 32);
+    const dim3 grid((unsigned)std::min<int64_t>((B + 255) / 256, 1024), (unsigned)std::min<int64_t>(p.n_pi, 65535));
     init_normal_kernel<<<grid, 256, 0, s>>>(p.n_pi, seed, round, scale, V, ldv, B);
     return cudaGetLastError();
 }
