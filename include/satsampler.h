@@ -332,7 +332,9 @@ sat_status sat_dedup_count(const sat_dedup* d, uint64_t* n, void* stream);
  * launch and the status read after it), for loops that keep the device busy: the kernels
  * guard the pool on the device, and a batch that did not fit or hit the probe limit is
  * recorded in the set's status word (its keys are then incomplete).  sat_dedup_check
- * synchronises the stream and returns SAT_ERR_TABLE_FULL if any insert so far failed. */
+ * synchronises the stream and returns SAT_ERR_TABLE_FULL if any insert so far failed.
+ * Inserts into one set share its scratch: issue them on one stream (or synchronise
+ * between streams) so that they do not overlap. */
 sat_status sat_dedup_insert_async(sat_dedup* d, const uint32_t* keys, const uint32_t* valid, int64_t B,
                                   void* stream);
 sat_status sat_dedup_check(const sat_dedup* d, void* stream);
