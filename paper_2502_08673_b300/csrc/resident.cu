@@ -41,20 +41,21 @@ struct Scalar<__half> {
 
 // Shared-memory layout (bytes from the start of the dynamic block): act rows [n_cone][32]
 // of T, adj rows [n_adj_rows][32] of float (the plan's adjoint rows: inputs, the level
-// ring and the seed row), then V, m, v of the cone inputs, [n_cone_pi][32] float each.
+// ring and the seed row), then V (and for Adam m, v) of the cone inputs, [n_cone_pi][32]
+// float each (n_state = 3 rows per input with Adam, 1 with GD).
 struct ResLayout {
     size_t adj, vmv, total;
 };
-__host__ __device__ inline ResLayout res_layout(const DevPlan& p, int act_bytes) {
+__host__ __device__ inline ResLayout res_layout(const DevPlan& p, int act_bytes, int n_state) {
     ResLayout r;
     r.adj = ((size_t)p.full.n_act_rows * RES_LANES * act_bytes + 15) / 16 * 16;
     r.vmv = r.adj + (size_t)p.n_adj_rows * RES_LANES * 4;
-    r.total = r.vmv + (size_t)3 * p.n_cone_pi * RES_LANES * 4;
+    r.total = r.vmv + (size_t)n_state * p.n_cone_pi * RES_LANES * 4;
     return r;
 }
 
 template <typename T>
-__global__ void __maxnreg__(80) resident_steps_kernel(DevPlan p, OptParams o, float* V, float* m,
+__global__ void __maxnreg__(64) resident_steps_kernel(DevPlan p, OptParams o, float* V, float* m,
                                                                            float* v, int64_t ldv, float* loss, int t0,
                                                                            const int32_t* age, int n_steps, int64_t B) {
     extern __shared__ __align__(16) char smem[];
@@ -62,7 +63,8 @@ __global__ void __maxnreg__(80) resident_steps_kernel(DevPlan p, OptParams o, fl
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int64_t b = (int64_t)blockIdx.x * RES_LANES + lane;
     const bool valid = b < B;
-    const ResLayout lay = res_layout(p, (int)sizeof(T));
+    const bool adam = o.opt == 0;
+    const ResLayout lay = res_layout(p, (int)sizeof(T), adam ? 3 : 1);
     // this lane's column of the act and adj rows (rows are < 2^27: 32-bit offsets)
     T* act = reinterpret_cast<T*>(smem) + lane;
     float* adj = reinterpret_cast<float*>(smem + lay.adj) + lane;
@@ -70,14 +72,15 @@ __global__ void __maxnreg__(80) resident_steps_kernel(DevPlan p, OptParams o, fl
     float* sm = sV + (size_t)p.n_cone_pi * RES_LANES;
     float* sv = sm + (size_t)p.n_cone_pi * RES_LANES;
     const int npi = p.n_cone_pi;
-    const bool adam = o.opt == 0;
     if (threadIdx.x < 16) gcoef[threadIdx.x] = gate_coeffs(threadIdx.x);
     for (int i = warp; i < npi; i += nw) {
         const int64_t r = (int64_t)__ldg(&p.cone_pi_row[i]) * ldv + b;
         const int e = i * RES_LANES + lane;
         sV[e] = valid ? V[r] : 0.0f;
-        sm[e] = valid && adam ? m[r] : 0.0f;
-        sv[e] = valid && adam ? v[r] : 0.0f;
+        if (adam) {
+            sm[e] = valid ? m[r] : 0.0f;
+            sv[e] = valid ? v[r] : 0.0f;
+        }
     }
     const int my_age = age != nullptr && valid ? __ldg(age + b) : 0;
     __syncthreads();
@@ -174,7 +177,8 @@ __global__ void __maxnreg__(80) resident_steps_kernel(DevPlan p, OptParams o, fl
         if (valid)
             for (int i = warp; i < npi; i += nw) {
                 const int e = i * RES_LANES + lane;
-                input_update<true>(o, sV, sm, sv, nullptr, e, sV[e], adj[i * RES_LANES], sm[e], sv[e], step_size, bc2s);
+                input_update<true>(o, sV, sm, sv, nullptr, e, sV[e], adj[i * RES_LANES], adam ? sm[e] : 0.0f,
+                                   adam ? sv[e] : 0.0f, step_size, bc2s);
             }
         __syncthreads();
     }
@@ -206,7 +210,7 @@ cudaError_t resident_launch(const DevPlan& p, const OptParams& o, float* V, floa
 }  // namespace
 
 bool resident_config(const DevPlan& p, int act_type, int* warps, size_t* smem) {
-    const ResLayout lay = res_layout(p, act_type == ACT_F32 ? 4 : 2);
+    const ResLayout lay = res_layout(p, act_type == ACT_F32 ? 4 : 2, 3);  // Adam's size: fits either way
     int widest = p.n_cone_pi;
     if (p.h_c_level_off)
         for (int l = 1; l <= p.n_clev; l++) widest = std::max(widest, p.h_c_level_off[l + 1] - p.h_c_level_off[l]);
@@ -222,8 +226,8 @@ cudaError_t launch_steps_resident(const DevPlan& p, int act_type, const OptParam
                                   const int32_t* age) {
     if (B == 0 || n_steps <= 0) return cudaSuccess;
     int warps = 1;
-    size_t smem = 0;
-    if (!resident_config(p, act_type, &warps, &smem)) return cudaErrorInvalidValue;
+    if (!resident_config(p, act_type, &warps, nullptr)) return cudaErrorInvalidValue;
+    const size_t smem = res_layout(p, act_type == ACT_F32 ? 4 : 2, o.opt == 0 ? 3 : 1).total;
     switch (act_type) {
     case ACT_F32: return resident_launch<float>(p, o, V, m, v, ldv, loss, t0, age, n_steps, B, warps, smem, s);
     case ACT_BF16:
