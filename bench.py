@@ -263,11 +263,15 @@ def distinct_keys_across_ranks(keys, device="cuda"):
     return int(np.unique(rows).shape[0])
 
 
+STEP_KERNEL_SOURCES = ("kernels.cu", "relax.cuh", "device.hpp", "tmap.hpp")
+
+
 def kernel_source_hash(text=None):
-    """Hash of the step kernels' source code with comments and whitespace removed (a change
-    to the comments does not make a profile stale; any change to the code does)."""
+    """Hash of the tiled step kernel's source code (the files it is compiled from) with
+    comments and whitespace removed (a change to the comments does not make a profile
+    stale; any change to the code does)."""
     if text is None:
-        text = (ROOT / "paper_2502_08673_b300" / "csrc" / "kernels.cu").read_text()
+        text = "\n".join((ROOT / "paper_2502_08673_b300" / "csrc" / f).read_text() for f in STEP_KERNEL_SOURCES)
     text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
     text = re.sub(r"//[^\n]*", " ", text)
     return hashlib.sha256(" ".join(text.split()).encode()).hexdigest()[:16]
