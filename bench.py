@@ -675,6 +675,9 @@ def main():
                          "kernel": "resident_steps_kernel" if skind == "resident" else "steps_kernel",
                          "byte_model": ("V, m, v once per launch (activations and adjoints in shared memory)"
                                         if skind == "resident" else "stored-activation schedule"),
+                         "note": ("the resident kernel barely uses HBM: it is bound by instruction issue and "
+                                  "shared-memory latency (profiles/resident_steps_kernel_small_circuits.md)"
+                                  if skind == "resident" else None),
                          "kernel_ms_avg": kavg,
                          "algorithmic_bytes_per_launch": alg,
                          "traffic": (dram_per_round if dram_per_round else
