@@ -42,12 +42,12 @@ __device__ __forceinline__ void adam_bias(const OptParams& o, int t, float& step
     bc2s = sqrtf(-expm1f(tf * log1pf(o.b2 - 1.0f)));
 }
 
-// dL/dV = Pbar * P (1 - P) for one sample, then GD (Eq. 9) or Adam (PyTorch's
-// formulation, no weight decay) on V, m, v at element r.
+// dL/dV = Pbar * P (1 - P) for one sample with P = sigmoid(vv) given, then GD (Eq. 9) or
+// Adam (PyTorch's formulation, no weight decay) on V, m, v at element r.
 template <bool UPDATE>
-__device__ __forceinline__ void input_update(const OptParams& o, float* V, float* m, float* v, float* gV, int64_t r,
-                                             float vv, float pbar, float mm, float ss, float step_size, float bc2s) {
-    const float P = sigmoidf_(vv);
+__device__ __forceinline__ void input_update_p(const OptParams& o, float* V, float* m, float* v, float* gV, int64_t r,
+                                               float vv, float P, float pbar, float mm, float ss, float step_size,
+                                               float bc2s) {
     const float g = pbar * P * (1.0f - P);
     if (!UPDATE) {
         gV[r] = g;
@@ -60,6 +60,13 @@ __device__ __forceinline__ void input_update(const OptParams& o, float* V, float
         v[r] = v1;
         V[r] = vv - step_size * (m1 / (sqrtf(v1) / bc2s + o.eps));
     }
+}
+
+// The same with P computed here.
+template <bool UPDATE>
+__device__ __forceinline__ void input_update(const OptParams& o, float* V, float* m, float* v, float* gV, int64_t r,
+                                             float vv, float pbar, float mm, float ss, float step_size, float bc2s) {
+    input_update_p<UPDATE>(o, V, m, v, gV, r, vv, sigmoidf_(vv), pbar, mm, ss, step_size, bc2s);
 }
 
 // Partial sums of the per-sample loss: outputs j = w, w + n, w + 2n, ... go to partial w

@@ -177,8 +177,10 @@ __global__ void __maxnreg__(64) resident_steps_kernel(DevPlan p, OptParams o, fl
         if (valid)
             for (int i = warp; i < npi; i += nw) {
                 const int e = i * RES_LANES + lane;
-                input_update<true>(o, sV, sm, sv, nullptr, e, sV[e], adj[i * RES_LANES], adam ? sm[e] : 0.0f,
-                                   adam ? sv[e] : 0.0f, step_size, bc2s);
+                // P = sigmoid(V): with FP32 activations the embedding row holds exactly that value
+                const float P = sizeof(T) == 4 ? Scalar<T>::ld(act + i * RES_LANES) : sigmoidf_(sV[e]);
+                input_update_p<true>(o, sV, sm, sv, nullptr, e, sV[e], P, adj[i * RES_LANES], adam ? sm[e] : 0.0f,
+                                     adam ? sv[e] : 0.0f, step_size, bc2s);
             }
         __syncthreads();
     }
