@@ -19,7 +19,7 @@ namespace sat {
 namespace {
 
 constexpr int RES_LANES = 32;     // samples per CTA (one per lane)
-constexpr int RES_MAX_WARPS = 16;  // warps per CTA for the widest levels
+constexpr int RES_MAX_WARPS = 32;  // warps per CTA for the widest levels
 
 template <typename T>
 struct Scalar;
@@ -216,8 +216,9 @@ bool resident_config(const DevPlan& p, int act_type, int* warps, size_t* smem) {
     int widest = p.n_cone_pi;
     if (p.h_c_level_off)
         for (int l = 1; l <= p.n_clev; l++) widest = std::max(widest, p.h_c_level_off[l + 1] - p.h_c_level_off[l]);
-    // one warp per 12 nodes of the widest level, 1 .. RES_MAX_WARPS
-    const int w = std::min(RES_MAX_WARPS, std::max(1, (widest + 11) / 12));
+    // two warps for narrow circuits, else one warp per 8 nodes of the widest level, up to
+    // RES_MAX_WARPS (1,024 threads at 64 registers fill the register file)
+    const int w = widest <= 24 ? 2 : std::min(RES_MAX_WARPS, std::max(1, (widest + 7) / 8));
     if (warps) *warps = w;
     if (smem) *smem = lay.total;
     return lay.total <= RESIDENT_SMEM_MAX && p.n_cone < (1 << 27) && p.seed_row >= 0 && p.seed_row < p.n_adj_rows;
