@@ -283,12 +283,20 @@ sat_status sat_restart(const sat_plan* p, const uint32_t* restart, uint64_t seed
  * a deployment variant.  The act/adj scratch comes from one fixed array of
  * SAT_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads the
  * library holds until the process exits; the call itself allocates nothing.
- * A plan and batch whose scratch exceeds the array are rejected with
- * SAT_ERR_ARG.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress), so make that first call before any stream
- * capture.  All calls share the array: calls whose executions overlap on the
- * GPU (other streams, other threads) race and give undefined results.  Nothing
- * in the array needs clearing: every scratch row is written before it is read. */
+ * The arguments are those of sat_steps without act/adj, checked the same way
+ * (SAT_ERR_ARG for a plan of another device than the current one, bad
+ * optimiser parameters, NULL buffers).  A plan whose fused steps run on the
+ * shared-memory resident kernel (sat_plan_step_kernel) needs no scratch and
+ * is not limited by the array.  For the tiled kernel, a plan and batch whose
+ * act/adj scratch exceeds the array (sat_plan_scratch_elems: the same rows,
+ * each block rounded up to 256 bytes) are rejected with SAT_ERR_ARG before
+ * any launch.  The first call on a device that needs the array looks up its
+ * device address (cudaGetSymbolAddress) and keeps it for the process, so make
+ * that first call before any stream capture, and do not use the library
+ * across a cudaDeviceReset (which also frees every plan).  All calls share the
+ * array: calls whose executions overlap on the GPU (other streams, other
+ * threads) race and give undefined results.  Nothing in the array needs
+ * clearing: every scratch row is written before it is read. */
 #define SAT_NOALLOC_SCRATCH_BYTES (64u << 20)
 sat_status sat_steps_noalloc(const sat_plan* p, sat_act_dtype act_dtype, const sat_opt_params* o, float* V, float* m,
                              float* v, int64_t ldv, float* loss, int32_t t0, int32_t n_steps, int64_t B,
@@ -392,7 +400,16 @@ sat_status sat_mlp_imle_select(sat_mlp* m, const void* zc, const uint32_t* keys,
  * and grad_host ([n_params]) are host pointers (nullable).  Synchronises. */
 sat_status sat_mlp_loss_grad(sat_mlp* m, const void* z, const uint32_t* keys, int32_t key_words, int64_t S,
                              float* loss_host, float* grad_host, void* stream);
-/* One IMLE step with K candidates per target and Adam (lr, PyTorch defaults otherwise). */
+/* One Adam step of the master weights with a given gradient grad (device float
+ * [n_params], the parameter order above): step count t = previous + 1, then
+ *   m <- b1 m + (1 - b1) g,  v <- b2 v + (1 - b2) g^2,
+ *   theta <- theta - lr / (1 - b1^t) * m / (sqrt(v) / sqrt(1 - b2^t) + eps)
+ * with b1 = 0.9, b2 = 0.999, eps = 1e-8 (PyTorch's Adam, no weight decay); the
+ * BF16 copies of the weights are refreshed.  The paper has no learned part; the
+ * optimiser is the one the proposal's configuration names. */
+sat_status sat_mlp_apply_grad(sat_mlp* m, const float* grad, float lr, void* stream);
+/* One IMLE step with K candidates per target: sat_mlp_imle_select on fresh noise,
+ * sat_mlp_loss_grad at the chosen rows, then sat_mlp_apply_grad with that gradient. */
 sat_status sat_mlp_train_step(sat_mlp* m, const uint32_t* keys, int32_t key_words, int64_t S, int32_t K, float lr,
                               uint64_t seed, uint32_t round, float* loss_host, void* stream);
 /* Train the proposal on distinct solutions: sols holds n full assignments in the

@@ -56,6 +56,7 @@ def lib():
         L.orc_threads.restype = ctypes.c_int
         L.orc_forward.argtypes = [P, ctypes.c_int, P, P, P]
         L.orc_backward.argtypes = [P, ctypes.c_int, P, P, P]
+        L.orc_backward_mag.argtypes = [P, ctypes.c_int, P, P, P]
         L.orc_gd.argtypes = [ctypes.c_long, P, P, ctypes.c_double]
         L.orc_adam.argtypes = [ctypes.c_long, P, P, P, P, ctypes.c_int,
                                ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]
@@ -75,7 +76,7 @@ def ptr(a: np.ndarray):
 from .dimacs import parse_dimacs, cnf_satisfied, DimacsError  # noqa: E402,F401
 from .transform import factorize, direct_circuit, Circuit, Definition  # noqa: E402,F401
 from .sampler import (  # noqa: E402,F401
-    FlatCircuit, flatten, forward, backward, adam_step, gd_step, hard_eval,
+    FlatCircuit, flatten, forward, backward, backward_magnitude, adam_step, gd_step, hard_eval,
     full_assignment, cnf_check, solution_hash, philox4x32_10, init_normal,
     sample_round, verify, Oracle,
 )

@@ -12,6 +12,10 @@ library's proposal network computes so its CUDA kernels can be checked:
 * IMLE selection (Li and Malik, 2018): for every target, among its K candidate
   noise vectors pick the one whose output has the least summed BCE to it
   (first index on ties).
+* The magnitude of the backward pass (every factor in absolute value), which
+  scales the rounding error of a low-precision evaluation of the gradient.
+* The noise z ~ N(0, I): Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
+  blocks turned into normals by the Box-Muller transform.
 
 Parameter vector order: W1 [h][n_in], b1 [h], W2 [h][h], b2 [h], W3 [n_out][h], b3 [n_out].
 """
@@ -78,6 +82,51 @@ def grad(theta, Z, T, n_in, h, n_out):
     da1 = (da2 @ W2) * gelu_grad(p1)
     dW1, db1 = da1.T @ Z, da1.sum(0)
     return np.concatenate([a.ravel() for a in (dW1, db1, dW2, db2, dW3, db3)])
+
+
+def grad_magnitude(theta, Z, D, n_in, h, n_out):
+    """The backward pass of `grad` with every factor in absolute value, seeded with
+    |D| [S][n_out] in place of dL/dy: the sums of absolute terms behind each gradient
+    entry.  With D = dL/dy it bounds |grad| entry by entry (triangle inequality), with
+    equality when every term is non-negative."""
+    W1, b1, W2, b2, W3, b3 = unpack(theta, n_in, h, n_out)
+    _, (Z, p1, h1, p2, h2) = forward(theta, Z, n_in, h, n_out)
+    dy = np.abs(np.asarray(D, dtype=np.float64))
+    dW3, db3 = dy.T @ np.abs(h2), dy.sum(0)
+    da2 = (dy @ np.abs(W3)) * np.abs(gelu_grad(p2))
+    dW2, db2 = da2.T @ np.abs(h1), da2.sum(0)
+    da1 = (da2 @ np.abs(W2)) * np.abs(gelu_grad(p1))
+    dW1, db1 = da1.T @ np.abs(Z), da1.sum(0)
+    return np.concatenate([a.ravel() for a in (dW1, db1, dW2, db2, dW3, db3)])
+
+
+def output_grad(theta, Z, T, n_in, h, n_out):
+    """dL/dy of the mean BCE: (sigmoid(y) - t) / (S n_out)."""
+    y, _ = forward(theta, Z, n_in, h, n_out)
+    return (1.0 / (1.0 + np.exp(-y)) - T) / y.size
+
+
+def noise(rows, n_in, seed, rnd):
+    """z [rows][n_in]: the Philox4x32-10 block at counter (row, c, rnd, 1) under key
+    (seed low word, seed high word) gives z[row][4c .. 4c+3]; each pair of words (x, y)
+    becomes u1 = ((x >> 8) + 1) / 2^24, u2 = (y >> 8) / 2^24 and the Box-Muller pair
+    r cos(2 pi u2), r sin(2 pi u2) with r = sqrt(-2 ln u1)."""
+    from .sampler import philox4x32_10
+    key = [seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF]
+    z = np.zeros((rows, n_in))
+    for r in range(rows):
+        for c in range((n_in + 3) // 4):
+            o = philox4x32_10([r, c, rnd, 1], key)
+            vals = []
+            for x, y in ((o[0], o[1]), (o[2], o[3])):
+                u1 = ((x >> 8) + 1) / 16777216.0
+                u2 = (y >> 8) / 16777216.0
+                rad = np.sqrt(-2.0 * np.log(u1))
+                vals += [rad * np.cos(2.0 * np.pi * u2), rad * np.sin(2.0 * np.pi * u2)]
+            for i, v in enumerate(vals):
+                if 4 * c + i < n_in:
+                    z[r, 4 * c + i] = v
+    return z
 
 
 def imle_select(theta, Zc, T, K, n_in, h, n_out):

@@ -141,6 +141,33 @@ void orc_backward(const orc_circuit *c, int S, const double *vals, double *adj, 
     }
 }
 
+/* Magnitude of the chain rule's terms: the reverse sweep of orc_backward with every
+ * fan-out term |dL/dy * dy/dx| added in absolute value, seeded with |2 (Y - T)|.
+ * gVmag[s][j] = amag[pi] * P (1 - P) bounds |dL/dV| (triangle inequality), with
+ * equality when no node sums terms of both signs (a single output over a fan-out-free
+ * cone).  Rounding error of a floating-point adjoint is proportional to this sum of
+ * absolute terms, not to the (possibly cancelled) adjoint itself: it scales tolerances. */
+void orc_backward_mag(const orc_circuit *c, int S, const double *vals, double *amag, double *gVmag) {
+#pragma omp parallel for schedule(static)
+    for (int s = 0; s < S; s++) {
+        const double *p = vals + (size_t)s * c->n_nodes;
+        double *a = amag + (size_t)s * c->n_nodes;
+        memset(a, 0, sizeof(double) * (size_t)c->n_nodes);
+        for (int o = 0; o < c->n_out; o++)
+            a[c->out_node[o]] += fabs(2.0 * (p[c->out_node[o]] - c->target[o]));
+        for (int k = c->n_instr - 1; k >= 0; k--) {
+            double ay = a[c->ins_out[k]];
+            int off = c->ins_off[k];
+            for (int i = 0; i < c->ins_cnt[k]; i++)
+                a[c->lit_node[off + i]] += ay * fabs(instr_partial(c, p, k, i));
+        }
+        for (int j = 0; j < c->n_pi; j++) {
+            double P = p[c->pi_node[j]];
+            gVmag[(size_t)s * c->n_pi + j] = a[c->pi_node[j]] * P * (1.0 - P);
+        }
+    }
+}
+
 void orc_gd(long n, double *V, const double *g, double lr) {
     for (long i = 0; i < n; i++) V[i] -= lr * g[i];
 }

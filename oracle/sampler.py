@@ -111,6 +111,18 @@ def backward(fc: FlatCircuit, vals: np.ndarray):
     return gV, adj
 
 
+def backward_magnitude(fc: FlatCircuit, vals: np.ndarray):
+    """Sum of the absolute chain-rule terms behind each dL/dV (Eq. 8 with every fan-out
+    term taken in absolute value, seeded with |2(Y - T)|): an upper bound of |dL/dV| and
+    the scale of the rounding error of any floating-point evaluation of it."""
+    S = vals.shape[0]
+    amag = np.empty_like(vals)
+    gmag = np.empty((S, len(fc.pi_node)), np.float64)
+    cs = fc.cstruct()
+    lib().orc_backward_mag(ctypes_ref(cs), S, ptr(vals), ptr(amag), ptr(gmag))
+    return gmag
+
+
 def ctypes_ref(s):
     import ctypes
     return ctypes.byref(s)

@@ -124,6 +124,7 @@ PROTOTYPES = {
     "sat_mlp_propose": (I32, [P, U64, U32, F32, P, I64, I64, P]),
     "sat_mlp_imle_select": (I32, [P, P, P, I32, I64, I32, P, P, P]),
     "sat_mlp_loss_grad": (I32, [P, P, P, I32, I64, P, P, P]),
+    "sat_mlp_apply_grad": (I32, [P, P, F32, P]),
     "sat_mlp_train_step": (I32, [P, P, I32, I64, I32, F32, U64, U32, P, P]),
     "sat_mlp_train": (I32, [P, P, P, U64, I32, I64, I32, F32, U64, P, P]),
     "sat_mlp_status": (I32, [P, C.POINTER(U32)]),

@@ -307,6 +307,10 @@ class Mlp(_Handle):
                                   C.byref(loss), _stream(stream)))
         return float(loss.value)
 
+    def apply_grad(self, grad, lr: float, stream=None) -> None:
+        """One Adam step with a given gradient (device float32 [n_params]; sat_mlp_apply_grad)."""
+        check(lib().sat_mlp_apply_grad(self._h, _ptr(grad), lr, _stream(stream)))
+
     def train_step(self, keys, S: int, K: int, lr: float, seed: int, round_: int, stream=None) -> float:
         loss = C.c_float()
         check(lib().sat_mlp_train_step(self._h, _ptr(keys), keys.shape[1], S, K, lr, seed, round_, C.byref(loss),

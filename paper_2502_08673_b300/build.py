@@ -24,7 +24,7 @@ def needs_build() -> bool:
     if not LIB.exists():
         return True
     t = LIB.stat().st_mtime
-    deps = sources() + sorted(CSRC.glob("*.hpp")) + [PKG.parent / "include" / "satsampler.h"]
+    deps = sources() + sorted(CSRC.glob("*.hpp")) + sorted(CSRC.glob("*.cuh")) + [PKG.parent / "include" / "satsampler.h"]
     return any(p.stat().st_mtime > t for p in deps)
 
 

@@ -242,6 +242,8 @@ bool opt_ok(const sat_opt_params* o) {
 namespace sat {
 sat_status report_error(sat_status s, const std::string& msg) { return fail(s, msg); }
 const DevPlan* plan_device(const sat_plan* p) { return &p->dp; }
+sat_status check_plan_call(const sat_plan* p, int64_t B, int64_t ldv) { return check_layout(p, B, ldv); }
+bool opt_params_ok(const sat_opt_params* o) { return opt_ok(o); }
 }  // namespace sat
 
 extern "C" {

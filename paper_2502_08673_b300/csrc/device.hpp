@@ -1,7 +1,9 @@
 // Device-side plan and kernel launchers (internal; the C ABI wraps these).
 #pragma once
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
+#include <mutex>
 
 #define SAT_TILE_SAMPLES 128  // samples per scratch tile (SAT_TILE in the C ABI)
 
@@ -72,6 +74,35 @@ inline __host__ __device__ int64_t adj_level_row(const DevPlan& p, int l, int32_
 
 enum ActType { ACT_F32 = 0, ACT_BF16 = 1, ACT_F16 = 2 };
 
+// A set-up step that must run once on every device: attributes set with
+// cudaFuncSetAttribute (the dynamic shared-memory opt-in) hold for the device that was
+// current when they were set, so a plan on a second GPU needs them set there too.
+// run(f) calls f() the first time it is called with a given device current and
+// returns that result on every later call with the same device current.
+class PerDeviceOnce {
+  public:
+    template <typename F>
+    cudaError_t run(F&& f) {
+        int dev = -1;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+        if (done_[dev].load(std::memory_order_acquire)) return result_[dev];
+        std::lock_guard<std::mutex> lock(mu_);
+        if (!done_[dev].load(std::memory_order_relaxed)) {
+            result_[dev] = f();
+            done_[dev].store(true, std::memory_order_release);
+        }
+        return result_[dev];
+    }
+
+  private:
+    static constexpr int kMaxDevices = 64;
+    std::mutex mu_;
+    std::atomic<bool> done_[kMaxDevices] = {};
+    cudaError_t result_[kMaxDevices] = {};
+};
+
 // Kernel of the fused steps: AUTO takes the shared-memory resident kernel when the
 // plan's per-sample state fits (resident_config), else the tiled one.
 enum StepKernel { STEP_KERNEL_AUTO = 0, STEP_KERNEL_TILED = 1, STEP_KERNEL_RESIDENT = 2 };
@@ -100,6 +131,9 @@ cudaError_t launch_steps(const DevPlan& p, const DevAct& lay, int act_type, cons
 // The shared-memory resident kernel of the fused steps (32 samples per CTA): whether the
 // plan fits it with activations of act_type, its warps per CTA and dynamic shared memory.
 bool resident_config(const DevPlan& p, int act_type, int* warps, size_t* smem);
+// Whether launch_steps runs the resident kernel for this plan and act_type (AUTO and the
+// plan fits it, or RESIDENT); the tiled kernel otherwise, which uses the act/adj scratch.
+bool steps_use_resident(const DevPlan& p, int act_type);
 cudaError_t launch_steps_resident(const DevPlan& p, int act_type, const OptParams& o, float* V, float* m, float* v,
                                   int64_t ldv, float* loss, int t0, int n_steps, int64_t B, cudaStream_t s,
                                   const int32_t* age = nullptr);

@@ -33,6 +33,7 @@
 #include <cstdint>
 #include <cstring>
 
+#include "device.hpp"
 #include "gemm.hpp"
 #include "tmap.hpp"
 
@@ -534,8 +535,9 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 template <int BN>
 cudaError_t gemm_launch(const GemmArgs& g, int sms, cudaStream_t s) {
     using C = Cfg<BN>;
-    static cudaError_t attr =
-        cudaFuncSetAttribute(gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    static PerDeviceOnce once;  // the shared-memory opt-in holds per device
+    const cudaError_t attr = once.run(
+        [] { return cudaFuncSetAttribute(gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM); });
     if (attr != cudaSuccess) return attr;
     CUtensorMap ma, mb;
     if (!make_map(&ma, g.A, g.M, g.K, g.lda, BM) || !make_map(&mb, g.B, g.N, g.K, g.ldb, BN))

@@ -127,4 +127,9 @@ struct DevPlan;
 sat_status report_error(sat_status s, const std::string& msg);
 // The device-side view of a plan.
 const DevPlan* plan_device(const sat_plan* p);
+// The checks every per-step entry point makes first: p not NULL, 0 <= B < 2^31, ldv >= B
+// (ldv < 0: no V argument), and p's device is the current device (SAT_ERR_ARG otherwise).
+sat_status check_plan_call(const sat_plan* p, int64_t B, int64_t ldv);
+// Optimiser parameters the kernels accept (Adam with beta1, beta2 in [0, 1), or GD).
+bool opt_params_ok(const sat_opt_params* o);
 }  // namespace sat

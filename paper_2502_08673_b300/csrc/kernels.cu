@@ -856,10 +856,11 @@ constexpr size_t stage_smem() {
     return (size_t)(step_threads<T>() / 32) * warp_stage_bytes<T>();
 }
 
-// Opt the step kernels into the dynamic shared memory they use (once per type).
+// Opt the step kernels into the dynamic shared memory they use (once per type and device).
 template <typename T>
 cudaError_t prepare_tile_kernels() {
-    static cudaError_t done = [] {
+    static PerDeviceOnce once;
+    return once.run([] {
         const int bytes = (int)stage_smem<T>();
         cudaError_t e = cudaFuncSetAttribute(forward_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         if (e == cudaSuccess)
@@ -869,8 +870,7 @@ cudaError_t prepare_tile_kernels() {
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(steps_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         return e;
-    }();
-    return done;
+    });
 }
 
 __global__ void opt_update_kernel(DevPlan p, OptParams o, float* V, float* m, float* v, const float* gV, int64_t ldv,
@@ -1262,11 +1262,9 @@ cudaError_t launch_steps(const DevPlan& p, const DevAct& L, int act_type, const 
                          float* v, int64_t ldv, void* act, float* adj, float* loss, int t0, int n_steps, int64_t B,
                          cudaStream_t s, const int32_t* age) {
     if (B == 0 || n_steps <= 0) return cudaSuccess;
-    if (p.step_kernel != STEP_KERNEL_TILED) {
-        if (resident_config(p, act_type, nullptr, nullptr))
-            return launch_steps_resident(p, act_type, o, V, m, v, ldv, loss, t0, n_steps, B, s, age);
-        if (p.step_kernel == STEP_KERNEL_RESIDENT) return cudaErrorInvalidValue;
-    }
+    if (steps_use_resident(p, act_type))
+        return launch_steps_resident(p, act_type, o, V, m, v, ldv, loss, t0, n_steps, B, s, age);
+    if (p.step_kernel == STEP_KERNEL_RESIDENT) return cudaErrorInvalidValue;
     switch (act_type) {
     case ACT_F32: return steps_launch<float>(p, L, o, V, m, v, ldv, act, adj, loss, t0, age, n_steps, B, s);
     case ACT_BF16: return steps_launch<__nv_bfloat16>(p, L, o, V, m, v, ldv, act, adj, loss, t0, age, n_steps, B, s);

@@ -499,6 +499,26 @@ sat_status sat_mlp_loss_grad(sat_mlp* m, const void* z, const uint32_t* keys, in
     return SAT_OK;
 }
 
+// One Adam step of the master weights with gradient G (device [np]); then the BF16 copies.
+static sat_status adam_apply(sat_mlp* m, const float* G, float lr, cudaStream_t s) {
+    m->t++;
+    const double b1 = 0.9, b2 = 0.999;
+    const float step_size = (float)((double)lr / (1.0 - std::pow(b1, m->t)));
+    const float bc2s = (float)std::sqrt(1.0 - std::pow(b2, m->t));
+    adam_kernel<<<blocks((int64_t)m->np, 256), 256, 0, s>>>(m->P, G, m->M1, m->M2, m->np, lr, (float)b1, (float)b2,
+                                                            1e-8f, step_size, bc2s);
+    const int64_t nmax = std::max<int64_t>(std::max<int64_t>((int64_t)m->h * m->n_in, (int64_t)m->h * m->h),
+                                           std::max<int64_t>((int64_t)m->n_out * m->h, (int64_t)m->h * m->n_out_p));
+    refresh_kernel<<<blocks(nmax, 256), 256, 0, s>>>(view_of(m));
+    if (cudaGetLastError() != cudaSuccess) return sat::report_error(SAT_ERR_CUDA, "MLP update launch failed");
+    return SAT_OK;
+}
+
+sat_status sat_mlp_apply_grad(sat_mlp* m, const float* grad, float lr, void* stream) {
+    if (!m || !grad) return sat::report_error(SAT_ERR_ARG, "NULL argument");
+    return adam_apply(m, grad, lr, (cudaStream_t)stream);
+}
+
 sat_status sat_mlp_train_step(sat_mlp* m, const uint32_t* keys, int32_t key_words, int64_t S, int32_t K, float lr,
                               uint64_t seed, uint32_t round, float* loss_host, void* stream) {
     if (!m || !keys || S <= 0 || K < 1 || S * K > m->cap || key_words * 32 < m->n_out)
@@ -508,17 +528,7 @@ sat_status sat_mlp_train_step(sat_mlp* m, const uint32_t* keys, int32_t key_word
     if (st == SAT_OK) st = sat_mlp_imle_select(m, m->Zc, keys, key_words, S, K, nullptr, nullptr, stream);
     if (st == SAT_OK) st = loss_grad(m, nullptr, keys, key_words, S, loss_host, s);
     if (st != SAT_OK) return st;
-    m->t++;
-    const double b1 = 0.9, b2 = 0.999;
-    const float step_size = (float)((double)lr / (1.0 - std::pow(b1, m->t)));
-    const float bc2s = (float)std::sqrt(1.0 - std::pow(b2, m->t));
-    adam_kernel<<<blocks((int64_t)m->np, 256), 256, 0, s>>>(m->P, m->G, m->M1, m->M2, m->np, lr, (float)b1, (float)b2,
-                                                            1e-8f, step_size, bc2s);
-    const int64_t nmax = std::max<int64_t>(std::max<int64_t>((int64_t)m->h * m->n_in, (int64_t)m->h * m->h),
-                                           std::max<int64_t>((int64_t)m->n_out * m->h, (int64_t)m->h * m->n_out_p));
-    refresh_kernel<<<blocks(nmax, 256), 256, 0, s>>>(view_of(m));
-    if (cudaGetLastError() != cudaSuccess) return sat::report_error(SAT_ERR_CUDA, "MLP update launch failed");
-    return SAT_OK;
+    return adam_apply(m, m->G, lr, s);
 }
 
 sat_status sat_mlp_status(const sat_mlp* m, uint32_t* status) {

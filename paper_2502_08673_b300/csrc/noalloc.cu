@@ -12,7 +12,9 @@
 // The array below is a file-scope __device__ variable of SAT_NOALLOC_SCRATCH_BYTES:
 // every GPU that loads this library holds it until the process exits.  Host
 // code must not use its name as an address (on the host it is only a stand-in);
-// the device address is looked up once per device with cudaGetSymbolAddress.
+// the device address is looked up once per device with cudaGetSymbolAddress and
+// kept for the life of the process (like every device object of the library, it
+// does not survive a cudaDeviceReset).
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -49,20 +51,40 @@ cudaError_t scratch_address(void** out) {
     return cudaSuccess;
 }
 
+sat::OptParams opt_of(const sat_opt_params* o) {
+    sat::OptParams r;
+    r.opt = o->optimizer;
+    r.lr = o->lr;
+    r.b1 = o->beta1;
+    r.b2 = o->beta2;
+    r.eps = o->eps;
+    return r;
+}
+
 }  // namespace
 
 extern "C" sat_status sat_steps_noalloc(const sat_plan* p, sat_act_dtype act_dtype, const sat_opt_params* o,
                                         float* V, float* m, float* v, int64_t ldv, float* loss, int32_t t0,
                                         int32_t n_steps, int64_t B, void* stream) {
-    if (!p) return sat::report_error(SAT_ERR_ARG, "plan is NULL");
+    // the same argument checks as sat_steps, including that the plan lives on the current
+    // device (the scratch address below is the current device's)
+    sat_status st = sat::check_plan_call(p, B, ldv);
+    if (st != SAT_OK) return st;
     const sat::DevPlan* dp = sat::plan_device(p);
     if (act_dtype < SAT_ACT_F32 || act_dtype > SAT_ACT_F16) return sat::report_error(SAT_ERR_ARG, "bad act_dtype");
-    if (!o || (o->optimizer != SAT_OPT_ADAM && o->optimizer != SAT_OPT_GD) || t0 < 1 || n_steps < 0)
+    if (!sat::opt_params_ok(o) || t0 < 1 || n_steps < 0)
         return sat::report_error(SAT_ERR_ARG, "bad optimiser parameters or steps");
-    if (B < 0 || B >= (1ll << 31) || ldv < B) return sat::report_error(SAT_ERR_ARG, "bad batch or ldv");
     if (B > 0 && dp->n_pi > 0 && (!V || (o->optimizer == SAT_OPT_ADAM && (!m || !v))))
         return sat::report_error(SAT_ERR_ARG, "NULL buffer");
-    // act and adj blocks, each rounded up to 256 bytes
+    if (sat::steps_use_resident(*dp, (int)act_dtype)) {
+        // the shared-memory resident kernel keeps activations and adjoints on chip: no scratch
+        if (B == 0 || n_steps == 0) return SAT_OK;
+        cudaError_t e = sat::launch_steps(*dp, dp->full, (int)act_dtype, opt_of(o), V, m, v, ldv, nullptr, nullptr,
+                                          loss, t0, n_steps, B, (cudaStream_t)stream);
+        if (e != cudaSuccess) return sat::report_error(SAT_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
+        return SAT_OK;
+    }
+    // the tiled kernel: act and adj blocks in the fixed array, each rounded up to 256 bytes
     const uint64_t tiles = (uint64_t)((B + SAT_TILE_SAMPLES - 1) / SAT_TILE_SAMPLES);
     const uint64_t act_elems = tiles * (uint64_t)dp->full.n_act_rows * SAT_TILE_SAMPLES;
     const uint64_t adj_elems = tiles * (uint64_t)dp->n_adj_rows * SAT_TILE_SAMPLES;
@@ -80,14 +102,8 @@ extern "C" sat_status sat_steps_noalloc(const sat_plan* p, sat_act_dtype act_dty
     if (e != cudaSuccess)
         return sat::report_error(SAT_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
     unsigned char* s = static_cast<unsigned char*>(base);
-    sat::OptParams op;
-    op.opt = o->optimizer;
-    op.lr = o->lr;
-    op.b1 = o->beta1;
-    op.b2 = o->beta2;
-    op.eps = o->eps;
-    e = sat::launch_steps(*dp, dp->full, (int)act_dtype, op, V, m, v, ldv, s, reinterpret_cast<float*>(s + act_bytes),
-                          loss, t0, n_steps, B, (cudaStream_t)stream);
+    e = sat::launch_steps(*dp, dp->full, (int)act_dtype, opt_of(o), V, m, v, ldv, s,
+                          reinterpret_cast<float*>(s + act_bytes), loss, t0, n_steps, B, (cudaStream_t)stream);
     if (e != cudaSuccess) return sat::report_error(SAT_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
     return SAT_OK;
 }

@@ -200,9 +200,12 @@ template <typename T>
 cudaError_t resident_launch(const DevPlan& p, const OptParams& o, float* V, float* m, float* v, int64_t ldv,
                             float* loss, int t0, const int32_t* age, int n_steps, int64_t B, int warps, size_t smem,
                             cudaStream_t s) {
-    // the opt-in to the dynamic shared memory, once per type (thread-safe static initialisation)
-    static const cudaError_t prepared = cudaFuncSetAttribute(
-        resident_steps_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RESIDENT_SMEM_MAX);
+    // the opt-in to the dynamic shared memory, once per type and device
+    static PerDeviceOnce once;
+    const cudaError_t prepared = once.run([] {
+        return cudaFuncSetAttribute(resident_steps_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)RESIDENT_SMEM_MAX);
+    });
     if (prepared != cudaSuccess) return prepared;
     const unsigned grid = (unsigned)((B + RES_LANES - 1) / RES_LANES);
     resident_steps_kernel<T><<<grid, warps * 32, smem, s>>>(p, o, V, m, v, ldv, loss, t0, age, n_steps, B);
@@ -222,6 +225,10 @@ bool resident_config(const DevPlan& p, int act_type, int* warps, size_t* smem) {
     if (warps) *warps = w;
     if (smem) *smem = lay.total;
     return lay.total <= RESIDENT_SMEM_MAX && p.n_cone < (1 << 27) && p.seed_row >= 0 && p.seed_row < p.n_adj_rows;
+}
+
+bool steps_use_resident(const DevPlan& p, int act_type) {
+    return p.step_kernel != STEP_KERNEL_TILED && resident_config(p, act_type, nullptr, nullptr);
 }
 
 cudaError_t launch_steps_resident(const DevPlan& p, int act_type, const OptParams& o, float* V, float* m, float* v,

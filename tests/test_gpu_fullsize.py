@@ -102,3 +102,33 @@ def test_fullsize_verification_and_dedup(gpu, setup):
     assert 0 < valid.sum() < B
     keys = ws.keys.cpu().numpy()
     assert dd.count() == len(np.unique(keys[valid], axis=0))
+
+
+def test_fullsize_sample_every_returned_assignment_passes_oracle(gpu, setup):
+    """sat_sample at the benchmarked configuration (batch 65,536, 500 Adam steps, lr 0.1, FP32,
+    one round, from host CNF and circuit objects): every returned full assignment satisfies every
+    original clause by the oracle's CNF check, the assignments are pairwise distinct, and each one
+    is the Boolean completion of its own primary-input bits by the oracle's circuit (the
+    threshold, keep-satisfiable, keep-non-redundant step at the end of Section III-A)."""
+    P, inst, plan, orc = setup
+    cnf = P.Cnf.from_dimacs(inst.dimacs())
+    circ = P.Circuit.build(cnf)
+    sols = P.sample(circ, cnf, n_wanted=10 ** 12, batch=B, steps=500, max_rounds=1, lr=0.1, seed=0)
+    n = len(sols)
+    # the workload's measured valid fraction is about one half; require a substantial set
+    assert n > B // 4, n
+    words = sols.words()
+    assert np.unique(words, axis=0).shape[0] == n
+    pis = np.array(orc.circuit.pis) - 1
+    checked = 0
+    for lo in range(0, n, 4096):
+        w = words[lo:lo + 4096]
+        bits = np.unpackbits(w.view(np.uint8), axis=1, bitorder="little")[:, : orc.n_vars]
+        assign = np.zeros((bits.shape[0], orc.n_vars + 1), np.uint8)
+        assign[:, 1:] = bits
+        ok = oracle.cnf_check(orc.n_vars, orc.clauses, assign)
+        assert ok.all(), np.nonzero(ok == 0)[0][:10] + lo
+        completed = oracle.full_assignment(orc.flat, oracle.hard_eval(orc.flat, bits[:, pis]))
+        assert np.array_equal(completed, assign)
+        checked += bits.shape[0]
+    assert checked == n

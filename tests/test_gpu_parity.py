@@ -1,9 +1,11 @@
 """GPU parity of the hot path against the FP64 oracle on the same seeded inputs.
 
-Tolerances: FP32 gate values within 1e-5 absolute; gradients within 1e-4
-relative to max(|g*|, 1e-3 max_i |g*_i|) per sample (adjoints through an XOR
-at 1/2 can be exactly 0, hence the floor); thresholded bits, Boolean node
-values, validity, hashes and unique sets bit-exact.
+Tolerances: FP32 gate values within 1e-5 absolute; every gradient element
+within 1e-4 of the sum of the absolute values of the chain-rule terms behind it
+(oracle.backward_magnitude; equal to |g*| where no node adds terms of both signs)
+plus 1e-7 of the sample's largest such sum (the forward's absolute rounding of
+probabilities near 0 or 1, which the relative term cannot express); thresholded
+bits, Boolean node values, validity, hashes and unique sets bit-exact.
 """
 import numpy as np
 import pytest
@@ -34,13 +36,15 @@ INSTANCES = {
 }
 
 
-def _grad_close(g, gref):
-    # Floor 1e-2 * max_i |g*_i| per sample: an input's adjoint sums many fan-out
-    # terms of both signs (e.g. one per 3-literal OR output), and FP32 summation
-    # error scales with the terms' magnitudes, not with the (cancelled) result.
-    floor = 1e-2 * np.abs(gref).max(axis=1, keepdims=True)
-    tol = 1e-4 * np.maximum(np.abs(gref), floor)
-    return np.abs(g - gref) <= tol + 1e-30
+def _grad_tol(gmag):
+    # An input's adjoint sums fan-out terms of both signs (e.g. one per 3-literal OR
+    # output): FP32 rounding scales with the terms' magnitudes, not with the (cancelled)
+    # result, so the bound is relative to the sum of absolute terms, element by element.
+    return 1e-4 * gmag + 1e-7 * gmag.max(axis=1, keepdims=True)
+
+
+def _grad_close(g, gref, gmag):
+    return np.abs(g - gref) <= _grad_tol(gmag) + 1e-30
 
 
 @pytest.mark.parametrize("name", sorted(INSTANCES))
@@ -58,6 +62,7 @@ def test_forward_backward_parity(gpu, name, B):
     torch.cuda.synchronize()
     vals, loss_ref = oracle.forward(orc.flat, V0.astype(np.float64))
     gref, _ = oracle.backward(orc.flat, vals)
+    gmag = oracle.backward_magnitude(orc.flat, vals)
     np.testing.assert_allclose(loss.cpu().numpy(), loss_ref, rtol=0, atol=1e-5 * max(1, plan.n_outputs))
     cone, _, neg = plan.var_nodes()
     A = P.untile(act, B).cpu().numpy()
@@ -69,8 +74,9 @@ def test_forward_backward_parity(gpu, name, B):
             gv = 1.0 - gv
         np.testing.assert_allclose(gv, vals[:, v - 1], rtol=0, atol=1e-5, err_msg=f"var {v}")
     g = gV.cpu().numpy().T
-    ok = _grad_close(g.astype(np.float64), gref)
-    assert ok.all(), (np.argwhere(~ok)[:5], g[~ok][:5], gref[~ok][:5])
+    ok = _grad_close(g.astype(np.float64), gref, gmag)
+    assert ok.all(), (np.argwhere(~ok)[:5], g[~ok][:5], gref[~ok][:5], gmag[~ok][:5])
+    print(f"{name} B={B}: max |g - g*| / tol = {float((np.abs(g - gref) / _grad_tol(gmag)).max()):.3g}")
 
 
 @pytest.mark.parametrize("name", ["planted3sat_50_200", "tseitin_small"])
@@ -94,10 +100,11 @@ def test_direct_relaxation_parity(gpu, name):
     torch.cuda.synchronize()
     vals, loss_ref = oracle.forward(orc.flat, V0.astype(np.float64))
     gref, _ = oracle.backward(orc.flat, vals)
+    gmag = oracle.backward_magnitude(orc.flat, vals)
     np.testing.assert_allclose(loss.cpu().numpy(), loss_ref, rtol=0, atol=1e-5 * max(1, plan.n_outputs))
     g = gV.cpu().numpy().T
-    ok = _grad_close(g.astype(np.float64), gref)
-    assert ok.all(), (np.argwhere(~ok)[:5], g[~ok][:5], gref[~ok][:5])
+    ok = _grad_close(g.astype(np.float64), gref, gmag)
+    assert ok.all(), (np.argwhere(~ok)[:5], g[~ok][:5], gref[~ok][:5], gmag[~ok][:5])
 
 
 @pytest.mark.parametrize("act_dtype", ["f32", "bf16", "f16"])
@@ -240,8 +247,9 @@ def test_autograd_function(gpu):
     (circuit_loss(V, plan) * w).sum().backward()
     vals, _ = oracle.forward(orc.flat, V0.astype(np.float64))
     gref, _ = oracle.backward(orc.flat, vals)
-    gref = gref * w.cpu().numpy()[:, None]
-    assert _grad_close(V.grad.cpu().numpy().T.astype(np.float64), gref).all()
+    wc = w.cpu().numpy()[:, None]
+    gref, gmag = gref * wc, oracle.backward_magnitude(orc.flat, vals) * wc
+    assert _grad_close(V.grad.cpu().numpy().T.astype(np.float64), gref, gmag).all()
 
 
 @pytest.mark.parametrize("act_dtype,bound", [("bf16", 0.06), ("f16", 0.01)])
@@ -338,13 +346,14 @@ def test_workspace_pool_kept_between_calls_and_released(gpu):
     np.testing.assert_array_equal(A, C_)
 
 
-@pytest.mark.parametrize("act_dtype,act_bound,rel_bound", [("f32", 1e-5, 1e-4), ("bf16", 0.06, 2.0),
+@pytest.mark.parametrize("act_dtype,act_bound,rel_bound", [("f32", 1e-5, 1e-4), ("bf16", 0.06, 1.0),
                                                            ("f16", 0.01, 0.5)])
 def test_per_step_error_vs_fp64(gpu, act_dtype, act_bound, rel_bound):
     """Per-step error on the 20k-gate workload against the FP64 oracle, by activation
-    storage type: activations (max abs), loss (max rel) and dL/dV (max of |g - g*| /
-    max(|g*|, 1e-2 max_i |g*_i|) per sample).  FP32 meets the parity tolerances; the
-    16-bit types are reported (printed) and loosely bounded."""
+    storage type: activations (max abs), loss (max rel) and dL/dV (max of |g - g*| over
+    the sum of the absolute chain-rule terms behind g*, element by element; also printed
+    against max(|g*|, 1e-2 max_i |g*_i|) per sample).  FP32 meets the parity tolerances;
+    the 16-bit types are reported (printed) and loosely bounded."""
     P, cnf, circ, plan, orc = _setup(INSTANCES["tseitin_2k_20k_d40"]())
     B = 256
     V0 = normal_logits(B, orc.n_pi, seed=31)
@@ -366,10 +375,13 @@ def test_per_step_error_vs_fp64(gpu, act_dtype, act_bound, rel_bound):
             a = A[cone[var]] if not neg[var] else 1.0 - A[cone[var]]
             act_err = max(act_err, float(np.abs(a - vals[:, var - 1]).max()))
     loss_err = float(np.max(np.abs(loss.cpu().numpy() - loss_ref) / np.abs(loss_ref)))
+    gmag = oracle.backward_magnitude(orc.flat, vals)
+    grad_err = float(np.max(np.abs(g - gref) / (gmag + 1e-300)))
     floor = 1e-2 * np.abs(gref).max(axis=1, keepdims=True)
-    grad_err = float(np.max(np.abs(g - gref) / (np.maximum(np.abs(gref), floor) + 1e-30)))
+    grad_err_floored = float(np.max(np.abs(g - gref) / (np.maximum(np.abs(gref), floor) + 1e-30)))
     print(f"per-step error vs FP64 [{act_dtype}]: activations {act_err:.3g} abs, loss {loss_err:.3g} rel, "
-          f"gradient {grad_err:.3g} rel (floored), |g*| max {np.abs(gref).max():.3g}")
+          f"gradient {grad_err:.3g} of sum|terms| ({grad_err_floored:.3g} rel, floored), "
+          f"|g*| max {np.abs(gref).max():.3g}")
     assert act_err < act_bound and grad_err < rel_bound
 
 

@@ -65,3 +65,35 @@ def test_param_layout():
     th = np.arange(M.n_params(2, 3, 4), dtype=float)
     W1, b1, W2, b2, W3, b3 = M.unpack(th, 2, 3, 4)
     assert W1.shape == (3, 2) and W1[0, 1] == 1 and b1[0] == 6 and W3.shape == (4, 3) and b3[-1] == th[-1]
+
+
+def test_grad_magnitude_bounds_and_equals_when_terms_are_positive():
+    """With dL/dy as seed the magnitude bounds |grad| entry by entry; with every weight, bias
+    and input positive (so every pre-activation and GELU' > 0) and every target 0 (so dL/dy > 0)
+    all terms are positive and the magnitude equals the gradient."""
+    n_in, h, n_out, S = 5, 7, 6, 4
+    rng = np.random.default_rng(5)
+    theta = M.init_params(n_in, h, n_out, 5) * 2.0
+    Z = rng.normal(size=(S, n_in))
+    T = rng.integers(0, 2, (S, n_out)).astype(np.float64)
+    g = M.grad(theta, Z, T, n_in, h, n_out)
+    gm = M.grad_magnitude(theta, Z, M.output_grad(theta, Z, T, n_in, h, n_out), n_in, h, n_out)
+    assert (gm >= np.abs(g) * (1 - 1e-12)).all() and (gm > np.abs(g) * (1 + 1e-9)).any()
+    thp, Zp, T0 = np.abs(theta), np.abs(Z), np.zeros((S, n_out))
+    g = M.grad(thp, Zp, T0, n_in, h, n_out)
+    gm = M.grad_magnitude(thp, Zp, M.output_grad(thp, Zp, T0, n_in, h, n_out), n_in, h, n_out)
+    assert (g > 0).all()
+    np.testing.assert_allclose(gm, g, rtol=1e-12)
+
+
+def test_noise_is_standard_normal_and_uses_the_stated_blocks():
+    """Moments of the Box-Muller noise, and its first entries re-derived from the pinned
+    Philox block function (counter (row, group, round, 1))."""
+    import oracle
+    z = M.noise(400, 64, 7, 3)
+    assert abs(z.mean()) < 0.02 and abs(z.std() - 1) < 0.02
+    assert abs(((z - z.mean()) ** 3).mean()) < 0.05 and abs((z ** 4).mean() - 3) < 0.15
+    o = oracle.philox4x32_10([2, 1, 3, 1], [7, 0])
+    r = math.sqrt(-2 * math.log(((o[2] >> 8) + 1) / 2 ** 24))
+    assert abs(z[2, 6] - r * math.cos(2 * math.pi * (o[3] >> 8) / 2 ** 24)) < 1e-12
+    assert np.array_equal(M.noise(5, 10, 7, 3), z[:5, :10])

@@ -318,6 +318,64 @@ def test_gradient_fd_sop_and_wide_gates():
             assert np.all(np.abs(fd - gV[:, j]) <= 1e-6 * np.abs(gV).max(axis=1) + 1e-12)
 
 
+# ------------------------------------------- magnitude of the chain rule ----
+def _gate_clauses(y, a, b, op):
+    """CNF of y = op(a, b) for literals a, b (the signatures of Eqs. 1-3)."""
+    if op == "and":
+        return [[-y, a], [-y, b], [y, -a, -b]]
+    if op == "or":
+        return [[y, -a], [y, -b], [-y, a, b]]
+    return [[-y, a, b], [-y, -a, -b], [y, -a, b], [y, a, -b]]
+
+
+# Two fan-out-free trees over inputs 1..8 that share input 1:
+# 9 = AND(1, -2), 10 = XOR(3, 4), 11 = OR(9, 10)  (tree 1, output 11)
+# 12 = OR(-1, 5), 13 = XOR(6, -7), 14 = AND(12, -13), 15 = XOR(14, 8)  (tree 2, output 15)
+_TREES = [(9, 1, -2, "and"), (10, 3, 4, "xor"), (11, 9, 10, "or"),
+          (12, -1, 5, "or"), (13, 6, -7, "xor"), (14, 12, -13, "and"), (15, 14, 8, "xor")]
+
+
+def _tree_oracle(outputs):
+    clauses = [c for g in _TREES for c in _gate_clauses(*g)] + [[o] for o in outputs]
+    return oracle.Oracle(dimacs_text(15, clauses))
+
+
+def test_gradient_magnitude_bounds_gradient():
+    """sum_terms |.| >= |dL/dV| on circuits with reconvergent fan-out and many outputs."""
+    for text in (tseitin_random_circuit(40, 200, 8, 6, seed=2).dimacs(), planted_3sat(20, 60, 3).dimacs(),
+                 fig1_example_dimacs()):
+        o = oracle.Oracle(text)
+        V = np.random.default_rng(4).normal(size=(5, o.n_pi))
+        vals, _ = oracle.forward(o.flat, V)
+        g, _ = oracle.backward(o.flat, vals)
+        gm = oracle.backward_magnitude(o.flat, vals)
+        assert (gm >= np.abs(g) * (1 - 1e-12)).all()
+        assert (gm > np.abs(g) * (1 + 1e-9)).any()  # some input sums terms of both signs
+
+
+def test_gradient_magnitude_on_trees():
+    """A single output over a fan-out-free cone has one term per adjoint: magnitude = |dL/dV|.
+    Two outputs whose trees share input 1: at input 1 the magnitude is the sum of the two
+    single-output gradients' absolute values, while the gradient is their signed sum."""
+    V = np.random.default_rng(6).normal(size=(7, 8))
+    single = {}
+    for out in (11, 15):
+        o = _tree_oracle([out])
+        assert o.circuit.pis == list(range(1, 9))
+        vals, _ = oracle.forward(o.flat, V)
+        g, _ = oracle.backward(o.flat, vals)
+        gm = oracle.backward_magnitude(o.flat, vals)
+        np.testing.assert_allclose(gm, np.abs(g), rtol=1e-13, atol=0)
+        single[out] = g
+    o = _tree_oracle([11, 15])
+    vals, _ = oracle.forward(o.flat, V)
+    g, _ = oracle.backward(o.flat, vals)
+    gm = oracle.backward_magnitude(o.flat, vals)
+    np.testing.assert_allclose(g, single[11] + single[15], rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(gm[:, 0], np.abs(single[11][:, 0]) + np.abs(single[15][:, 0]), rtol=1e-13)
+    np.testing.assert_allclose(gm[:, 1:], np.abs(g[:, 1:]), rtol=1e-13, atol=0)
+
+
 # -------------------------------------------------------------- optimisers -
 def test_adam_first_step_closed_form():
     """Adam at t=1: m_hat = g, v_hat = g^2, so V1 = V0 - lr * g / (|g| + eps)."""

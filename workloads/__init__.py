@@ -8,5 +8,5 @@ oracle may consume its output.
 from .generators import (  # noqa: F401
     TseitinInstance, PlantedSATInstance,
     tseitin_random_circuit, planted_3sat, fig1_example_dimacs,
-    dimacs_text, normal_logits,
+    dimacs_text, normal_logits, mlp_params, normal_vector,
 )

@@ -188,3 +188,21 @@ def normal_logits(n_rows: int, n_cols: int, seed: int, scale: float = 1.0) -> np
     """Seeded N(0, scale^2) float32 matrix, used as initial logits V0 [n_rows, n_cols]."""
     rng = np.random.default_rng(seed)
     return (rng.standard_normal((n_rows, n_cols)) * scale).astype(np.float32)
+
+
+def mlp_params(n_in: int, n_hidden: int, n_out: int, seed: int) -> np.ndarray:
+    """Seeded float32 parameter vector of the proposal network n_in -> n_hidden ->
+    n_hidden -> n_out (order W1, b1, W2, b2, W3, b3), every entry of a layer uniform in
+    +-1/sqrt(fan_in) (the usual dense-layer initialisation)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_out, fan_in in ((n_hidden, n_in), (n_hidden, n_hidden), (n_out, n_hidden)):
+        k = 1.0 / np.sqrt(fan_in)
+        parts.append(rng.uniform(-k, k, fan_out * fan_in))
+        parts.append(rng.uniform(-k, k, fan_out))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def normal_vector(n: int, seed: int, scale: float = 1.0) -> np.ndarray:
+    """Seeded N(0, scale^2) float32 vector (e.g. a gradient fed to an optimiser)."""
+    return (np.random.default_rng(seed).standard_normal(n) * scale).astype(np.float32)
