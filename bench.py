@@ -73,10 +73,18 @@ def train_proposal(P, torch, plan, w, mode, B, opt, ad, log, train_steps=0, roun
     mode "same": solutions of the benchmarked instance itself (rounds on Philox
     streams disjoint from the timed ones).  mode "heldout": solutions of 16
     instances of the same topology with other planted inputs (planted seeds
-    1..16); the benchmarked instance (planted seed 17) is never seen.
+    1..16); the benchmarked instance (planted seed 17) is never seen.  mode
+    "heldout_topology" (the control): 16 instances of other random topologies
+    (topology seeds 101..116, same sizes), so nothing about the benchmarked
+    circuit's structure can be learned.
     """
     t0 = time.perf_counter()
-    texts = [None] if mode == "same" else [instance_text(w, planted_seed=k) for k in range(1, 17)]
+    if mode == "same":
+        texts = [None]
+    elif mode == "heldout_topology":
+        texts = [instance_text(dict(w, seed=100 + k)) for k in range(1, 17)]
+    else:
+        texts = [instance_text(w, planted_seed=k) for k in range(1, 17)]
     rounds_per = rounds or (4 if mode == "same" else 2)
     keys = []
     for ti, text in enumerate(texts):
@@ -176,20 +184,21 @@ def measured_peaks():
     return 6400.0, "fallback"
 
 
+TRAFFIC_FILE = ROOT / "profiles" / "steps_kernel_traffic.json"
+
+
 def profile_traffic(workload, act_dtype, B=None, steps=None):
-    """DRAM bytes of the fused step kernel from the committed ncu summary: per sample-step
-    (one-wave capture), and per round when the summary holds the full-size launch list of
-    this batch and step count; None when absent or taken on a different kernel source."""
-    f = ROOT / "profiles" / f"steps_kernel_{workload}.md"
-    if not f.exists():
+    """DRAM bytes of the fused step kernel from the committed ncu figures: per sample-step
+    (one-wave capture, scaled to the launch), and per round when a full-size launch list of
+    this batch and step count exists; None when absent or taken on a different kernel source."""
+    if not TRAFFIC_FILE.exists():
         return None, None, None
-    text = f.read_text()
-    m = re.search(r"dram_bytes_per_sample_step:\s*([0-9.eE+]+)", text)
-    h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
-    if not m or not h or h.group(1) != kernel_source_hash():
+    d = json.loads(TRAFFIC_FILE.read_text())
+    e = d.get("workloads", {}).get(workload)
+    if not e or d.get("kernel_source_sha256") != kernel_source_hash():
         return None, None, None
-    r = re.search(rf"dram_bytes_per_round_b{B}_s{steps}:\s*([0-9.eE+]+)", text) if B and steps else None
-    return float(m.group(1)), (float(r.group(1)) if r else None), f.name
+    per_round = e.get("dram_bytes_per_round", {}).get(f"b{B}_s{steps}") if B and steps else None
+    return float(e["dram_bytes_per_sample_step"]), per_round, TRAFFIC_FILE.name
 
 
 def resident_bytes_per_launch(info, B, optimizer):
@@ -372,6 +381,120 @@ def run_mlp(args, w):
                       "frac_of_bf16_peak": flops / (ms / 1e3) / 1e12 / peak, "status": mlp.status()}))
 
 
+# Per-step error of BF16 activation storage against FP64 on this workload (256 samples, one
+# forward and backward; tests/test_gpu_parity.py::test_per_step_error_vs_fp64 measures and
+# bounds it on every GPU test run; the bench does not run the oracle outside its CPU leg).
+BF16_PER_STEP_ERROR = {"activations_max_abs": 9.4e-3, "loss_max_rel": 3.8e-3,
+                       "dL_dV_max_err_over_sum_abs_terms": 0.21, "dL_dV_max_rel_floored": 0.87,
+                       "source": "tests/test_gpu_parity.py::test_per_step_error_vs_fp64[bf16]"}
+
+
+def timed_rounds(P, torch, plan, ws, opt, steps, rounds, round0, dedup, stream, mlp=None, tau=1.0):
+    """`rounds` sampling rounds (init or proposal, fused steps, threshold, Boolean pass,
+    CNF check, dedup insert) timed with CUDA events on the stream, the step kernel's own
+    launches too; counts are read after the timed region."""
+    B = ws.B
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(rounds)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    before = dedup.count()
+    snaps = []
+    e0.record(stream)
+    for r in range(rounds):
+        if mlp is not None:
+            mlp.propose(ws.V, seed=0, round_=round0 + r, tau=tau)
+        else:
+            P.sat_init_normal(plan, ws.V, seed=0, round_=round0 + r, scale=1.0)
+        ws.m.zero_()
+        ws.v.zero_()
+        kev[r][0].record(stream)
+        P.sat_steps(plan, opt, ws.V, ws.m, ws.v, ws.act, ws.adj, 1, steps, act_dtype=ws.act_dtype)
+        kev[r][1].record(stream)
+        P.sat_threshold(plan, ws.V, ws.bits, ws.keys)
+        P.sat_hard_eval(plan, ws.bits, B)
+        P.sat_cnf_check(plan, ws.bits, ws.valid, B)
+        dedup.insert(ws.keys, ws.valid, B, sync=False)
+        snaps.append(ws.valid.clone())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dedup.check()
+    ms = e0.elapsed_time(e1)
+    uniq = dedup.count() - before
+    valid = sum(int(P.valid_mask(x, B).sum()) for x in snaps)
+    return {"unique": int(uniq), "ms": ms, "valid": valid, "rounds": rounds, "steps": steps,
+            "kernel_ms": [a.elapsed_time(b) for a, b in kev]}
+
+
+def chosen_form_entry(P, torch, w, args, stream, peak, peak_kind):
+    """The chosen form (BF16 activations + the learned proposal) against the plain FP32
+    form on the same GPU.  The proposal is trained untimed, by the library's own kernels,
+    on distinct solutions that plain BF16 rounds find on 16 instances of the benchmarked
+    circuit topology with other planted inputs (planted seeds 1..16); it is then timed on
+    4 held-out instances (planted seeds 17..20, never seen in training) at 200 steps per
+    round, beside the plain forms on the same instances: BF16 and FP32 at 200 steps, and
+    FP32 at the workload's own step count.  Every counted assignment passed the exact CNF
+    check on the device."""
+    B, steps = w["batch"], w["steps"]
+    cs = args.chosen_steps
+    opt = P.opt_params("adam", lr=w["lr"])
+    t0 = time.perf_counter()
+    log = {}
+    w_train = dict(w, collect_steps=cs)
+    text0 = instance_text(w, planted_seed=17)
+    cnf0 = P.Cnf.from_dimacs(text0)
+    plan0 = P.Plan.create(P.Circuit.build(cnf0), cnf0)
+    mlp = train_proposal(P, torch, plan0, w_train, "heldout", B, opt, "bf16", log, 0, 2)
+    train_s = time.perf_counter() - t0
+    forms = {"chosen": ("bf16", cs, True), "plain_bf16_same_steps": ("bf16", cs, False),
+             "plain_fp32_same_steps": ("f32", cs, False), "plain_fp32_workload_steps": ("f32", steps, False)}
+    acc = {k: {"unique": 0, "ms": 0.0, "valid": 0, "rounds": 0, "kernel_ms": [], "per_instance": []} for k in forms}
+    R = args.chosen_rounds
+    for k in range(17, 21):
+        cnf = cnf0 if k == 17 else P.Cnf.from_dimacs(instance_text(w, planted_seed=k))
+        plan = plan0 if k == 17 else P.Plan.create(P.Circuit.build(cnf), cnf)
+        wss = {"bf16": P.new_workspace(plan, B, "bf16"), "f32": P.new_workspace(plan, B, "f32")}
+        for fi, (name, (ad, ns, use_mlp)) in enumerate(forms.items()):
+            dd = P.Dedup.create(plan, max_keys=B * R, max_batch=B)
+            r = timed_rounds(P, torch, plan, wss[ad], opt, ns, R, (2 << 20) + k * 1024 + fi * 64, dd, stream,
+                             mlp=mlp if use_mlp else None)
+            a = acc[name]
+            for key in ("unique", "ms", "valid", "rounds"):
+                a[key] += r[key]
+            a["kernel_ms"] += r["kernel_ms"]
+            a["per_instance"].append(round(r["unique"] / (r["ms"] / 1e3), 1))
+            del dd
+        del wss
+        torch.cuda.empty_cache()
+    info = plan0.info
+    out = {}
+    for name, (ad, ns, _) in forms.items():
+        a = acc[name]
+        kavg = statistics.mean(a["kernel_ms"])
+        alg = algorithmic_bytes_per_step(info, B, ad) * ns
+        out[name] = {"value": a["unique"] / (a["ms"] / 1e3), "unit": "unique valid solutions/s",
+                     "act_dtype": ad, "steps": ns, "ms_per_step": a["ms"] / a["rounds"],
+                     "valid_fraction": a["valid"] / (B * a["rounds"]), "unique": a["unique"],
+                     "per_instance_value": a["per_instance"],
+                     "roofline": {"bound": "hbm", "kernel": "steps_kernel", "kernel_ms_avg": kavg,
+                                  "algorithmic_bytes_per_launch": alg,
+                                  "achieved": alg / (kavg / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                                  "frac": alg / (kavg / 1e3) / 1e9 / peak, "peak_kind": peak_kind}}
+    ch = out.pop("chosen")
+    return {**ch, "form": "BF16 activations + learned proposal (V0 = MLP(z), IMLE-trained)", "batch": B,
+            "rounds_timed": acc["chosen"]["rounds"], "instances": "planted seeds 17-20 of the benchmarked topology",
+            "proposal": {"trained_on": "distinct solutions of plain BF16 rounds (%d steps) on planted seeds 1-16"
+                                       % cs, **log, "train_and_collect_s": train_s},
+            "plain": out,
+            "vs_plain_fp32_workload_steps": ch["value"] / out["plain_fp32_workload_steps"]["value"]
+            if out["plain_fp32_workload_steps"]["value"] else None,
+            "vs_plain_fp32_same_steps": ch["value"] / out["plain_fp32_same_steps"]["value"]
+            if out["plain_fp32_same_steps"]["value"] else None,
+            "vs_plain_bf16_same_steps": ch["value"] / out["plain_bf16_same_steps"]["value"]
+            if out["plain_bf16_same_steps"]["value"] else None,
+            "validity": "every counted assignment passed the exact CNF check on the device",
+            "per_step_error_vs_fp64": BF16_PER_STEP_ERROR}
+
+
 def run_curve(P, torch, plan, ws, opt, args, w, info):
     """Distinct valid solutions against the number of descent iterations per round
     (the unique-vs-iterations view of the paper's Fig. 3 on the synthetic workload)."""
@@ -419,7 +542,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-samples", type=int, default=16)
-    ap.add_argument("--proposal", default="none", choices=["none", "same", "heldout"],
+    ap.add_argument("--proposal", default="none", choices=["none", "same", "heldout", "heldout_topology"],
                     help="initial logits from the learned proposal (trained untimed) instead of N(0,1)")
     ap.add_argument("--tau", type=float, default=1.0)
     ap.add_argument("--heldout-seed", type=int, default=17,
@@ -446,6 +569,11 @@ def main():
                     help="comma-separated step counts: unique solutions vs iterations (one JSON line)")
     ap.add_argument("--mlp", action="store_true",
                     help="time only the proposal network's inference GEMMs (tcgen05) at the workload's batch")
+    ap.add_argument("--chosen-form", default="auto", choices=["auto", "on", "off"],
+                    help="also time the chosen form (BF16 + learned proposal) against the plain forms on held-out "
+                         "instances (auto: on for the default 20k-gate workload without other variants)")
+    ap.add_argument("--chosen-steps", type=int, default=200, help="steps per round of the chosen form")
+    ap.add_argument("--chosen-rounds", type=int, default=2, help="timed rounds per held-out instance and form")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     args.optimizer = args.optimizer or w.get("optimizer", "adam")
@@ -474,7 +602,7 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    text = instance_text(w, planted_seed=args.heldout_seed if args.proposal == "heldout" else None)
+    text = instance_text(w, planted_seed=args.heldout_seed if args.proposal.startswith("heldout") else None)
     cnf = P.Cnf.from_dimacs(text)
     t0 = time.perf_counter()
     circ = P.Circuit.build(cnf, direct=args.direct, reorder=args.reorder)
@@ -619,35 +747,48 @@ def main():
     scratch = {"act": ws.act.numel() * ws.act.element_size(), "adj": ws.adj.numel() * ws.adj.element_size()}
     del ws, dedup
     torch.cuda.empty_cache()
+    chosen = None
+    default_variant = (args.workload == "tseitin20k" and args.proposal == "none" and args.check_every <= 0
+                       and not args.direct and not args.recompute and not args.shuffle_clauses
+                       and args.optimizer == "adam" and not args.batch and not args.gd_steps and not args.lr)
+    if args.chosen_form == "on" or (args.chosen_form == "auto" and default_variant):
+        chosen = chosen_form_entry(P, torch, w, args, stream, peak, peak_kind)
     e2e = None
     if not args.no_e2e:
         # the user-facing call with host inputs: plan upload, rounds, key download; one
         # untimed call first (it grows the library's workspace pool, which later calls reuse)
         e2e_steps = max(1, min(args.steps, 2))
-        ucount = 0
+        kept = []
         d2h = 0
         for k in range(-1, e2e_steps):
             if k == 0:
                 torch.cuda.synchronize()
                 t1 = time.perf_counter()
-                ucount = 0
                 d2h = 0
             sols = P.sample(circ, cnf, n_wanted=10 ** 12, batch=B, steps=steps, max_rounds=1, lr=w["lr"], seed=0,
                             first_round=round_base + (n_rounds + (k if k >= 0 else e2e_steps)) * 4096, init_scale=w["init_scale"], act_dtype=ad,
                             check_every=max(0, args.check_every), max_age=args.max_age, optimizer=args.optimizer,
                             recompute_segment=args.recompute)
-            ucount += len(sols)
             d2h += len(sols) * info["key_words"] * 4 + B // 8 + 16
             st = sols.stats
-            sols = None  # results consumed: the library may reuse their host buffer
+            if k >= 0:
+                kept.append(sols)
+            sols = None
         e2e_s = time.perf_counter() - t1
+        # distinct over all timed calls: a solution that two calls return counts once
+        words = [x.words() for x in kept if len(x)]
+        ucount = int(np.unique(np.concatenate(words), axis=0).shape[0]) if words else 0
+        per_call = [len(x) for x in kept]
+        kept = None
         e2e = {"value": ucount / e2e_s, "unit": "unique valid solutions/s",
                "h2d_bytes_per_step": info["upload_bytes"],
                "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps, "warmup_calls": 1,
                "wall_ms_per_call": 1e3 * e2e_s / e2e_steps,
                "last_call_ms": {k: round(st[f"ms_{k}"], 3) for k in
                                 ("upload", "init", "steps", "verify", "dedup", "download")},
-               "note": "sat_sample from host CNF/circuit objects: plan upload, workspace, one round, key download"}
+               "solutions_per_call": per_call, "distinct_over_calls": ucount,
+               "note": "sat_sample from host CNF/circuit objects: plan upload, workspace, one round, key download; "
+                       "value counts the distinct assignments over all timed calls"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -676,8 +817,7 @@ def main():
                          "byte_model": ("V, m, v once per launch (activations and adjoints in shared memory)"
                                         if skind == "resident" else "stored-activation schedule"),
                          "note": ("the resident kernel barely uses HBM: it is bound by instruction issue and "
-                                  "shared-memory latency (profiles/resident_steps_kernel_small_circuits.md)"
-                                  if skind == "resident" else None),
+                                  "shared-memory latency" if skind == "resident" else None),
                          "kernel_ms_avg": kavg,
                          "algorithmic_bytes_per_launch": alg,
                          "traffic": (dram_per_round if dram_per_round else
@@ -694,6 +834,8 @@ def main():
             "cpu_baseline": cpu,
             "e2e": e2e,
         }
+        if chosen is not None:
+            line["chosen_form"] = chosen
         if args.check_every > 0:
             line["config"]["early_exit"] = {"check_every": args.check_every, "max_age": max_age,
                                             "epochs_per_step": -(-steps // args.check_every),
@@ -702,7 +844,7 @@ def main():
         if mlp is not None:
             line["config"]["proposal"] = {"mode": args.proposal, "tau": args.tau, "steps_per_round": prop_steps,
                                           **({"heldout_planted_seed": args.heldout_seed}
-                                             if args.proposal == "heldout" else {}),
+                                             if args.proposal.startswith("heldout") else {}),
                                           **prop_log}
             line["plain_same_run"] = plain_cmp
         print(json.dumps(line), flush=True)

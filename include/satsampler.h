@@ -404,7 +404,8 @@ sat_status sat_mlp_loss_grad(sat_mlp* m, const void* z, const uint32_t* keys, in
  * [n_params], the parameter order above): step count t = previous + 1, then
  *   m <- b1 m + (1 - b1) g,  v <- b2 v + (1 - b2) g^2,
  *   theta <- theta - lr / (1 - b1^t) * m / (sqrt(v) / sqrt(1 - b2^t) + eps)
- * with b1 = 0.9, b2 = 0.999, eps = 1e-8 (PyTorch's Adam, no weight decay); the
+ * with b1 = 0.9f, b2 = 0.999f, eps = 1e-8f (PyTorch's Adam, no weight decay; the
+ * betas are these FP32 values in every term, bias corrections included); the
  * BF16 copies of the weights are refreshed.  The paper has no learned part; the
  * optimiser is the one the proposal's configuration names. */
 sat_status sat_mlp_apply_grad(sat_mlp* m, const float* grad, float lr, void* stream);
@@ -426,11 +427,19 @@ sat_status sat_mlp_status(const sat_mlp* m, uint32_t* status);
 void sat_mlp_free(sat_mlp* m);
 
 /* -------------------------------------------------------- end to end ---
- * Rounds of: init (or caller logits, or the proposal network) -> `steps`
- * fused steps -> threshold -> Boolean pass -> CNF check -> dedup, until
- * n_wanted distinct solutions or max_rounds.  Round r draws its initial logits
- * (or the proposal's noise) with round counter first_round + r.  Returns SAT_PARTIAL (with what was found) when the budget
- * ends first. */
+ * The sampling problem of Section II-A: draw many distinct assignments that
+ * satisfy every clause of a CNF.  The method of Section III-A learns a batch
+ * of input vectors on the relaxed circuit (Eqs. 5-9), thresholds them, and
+ * keeps only the satisfiable, non-redundant rows (the end of Section III-A);
+ * Section IV measures it as unique valid solutions per second.  Here that is
+ * rounds of: init (or caller logits, or the proposal network) -> `steps`
+ * fused steps -> threshold -> Boolean pass -> exact check against the
+ * original clauses -> dedup, until n_wanted distinct solutions or max_rounds.
+ * Round r draws its initial logits (or the proposal's noise) with round
+ * counter first_round + r.  Returns SAT_PARTIAL (with what was found) when the
+ * budget ends first.  The stats' device times give the throughput of Section
+ * IV (distinct solutions over time; the host transformation is timed apart by
+ * sat_circuit_build, as the paper reports it separately in Section IV-C). */
 typedef struct sat_sample_opts {
     int64_t batch;
     int32_t steps;
@@ -475,18 +484,39 @@ typedef struct sat_sample_stats {
 sat_status sat_cached_memory(uint64_t* reserved_bytes, uint64_t* used_bytes);
 sat_status sat_release_cached_memory(void);
 
+/* Defaults: batch 1,024, 200 steps, 1 round, Adam lr 0.1 (beta 0.9/0.999, eps 1e-8),
+ * seed 0, init_scale 1, FP32 activations, no early exit, no recomputation. */
 void sat_sample_opts_default(sat_sample_opts* o);
+/* The whole sampler from host objects (Section III-A, end to end): builds a plan
+ * of circuit c for cnf (the clauses that are checked are cnf's own), samples
+ * until n_wanted distinct solutions or the round budget, and returns them in
+ * *out (owned by the caller, freed with sat_solutions_free).  SAT_OK when
+ * n_wanted were found, SAT_PARTIAL with fewer; SAT_ERR_ARG on bad options
+ * (batch < 1, steps < 0, max_rounds < 1, bad optimiser), SAT_ERR_OOM when the
+ * workspace does not fit on the device, SAT_ERR_CUDA on a device error (out is
+ * then NULL).  stats (nullable) gets counts and per-phase device times.  Runs on
+ * o->stream of the current device and synchronises it before returning. */
 sat_status sat_sample(const sat_circuit* c, const sat_cnf* cnf, const sat_sample_opts* o, uint64_t n_wanted,
                       sat_solutions** out, sat_sample_stats* stats);
-/* Same on an existing plan, adding to an existing dedup set (device-resident inputs). */
+/* The same rounds on an existing plan, adding the distinct solutions to an existing
+ * dedup set d (device-resident: nothing is copied to the host; read d with
+ * sat_dedup_count / sat_dedup_copy_keys).  n_wanted counts d's total.  Errors as
+ * sat_sample, plus SAT_ERR_TABLE_FULL when d cannot take a round's distinct keys. */
 sat_status sat_sample_plan(const sat_plan* p, sat_dedup* d, const sat_sample_opts* o, uint64_t n_wanted,
                            sat_sample_stats* stats);
 
+/* The kept rows of Section III-A's last step: satisfiable (every original clause
+ * has a true literal) and non-redundant (pairwise distinct full assignments).
+ * sat_solutions_count: their number (0 for NULL); sat_solutions_nvars: variables
+ * of each assignment (the CNF's). */
 uint64_t sat_solutions_count(const sat_solutions* s);
 uint32_t sat_solutions_nvars(const sat_solutions* s);
 /* Full assignments of solutions [first, first+count) in canonical ascending
- * order: ceil(n_vars/64) uint64 words each, bit j of word k = variable 64k+j+1. */
+ * order (of the packed primary-input bits, the dedup key): ceil(n_vars/64)
+ * uint64 words each into host words_out, bit j of word k = variable 64k+j+1.
+ * SAT_ERR_ARG when the range exceeds the count or an argument is NULL. */
 sat_status sat_solutions_copy(const sat_solutions* s, uint64_t first, uint64_t count, uint64_t* words_out);
+/* Frees a solution set (NULL is accepted). */
 void sat_solutions_free(sat_solutions* s);
 
 #ifdef __cplusplus

@@ -502,11 +502,13 @@ sat_status sat_mlp_loss_grad(sat_mlp* m, const void* z, const uint32_t* keys, in
 // One Adam step of the master weights with gradient G (device [np]); then the BF16 copies.
 static sat_status adam_apply(sat_mlp* m, const float* G, float lr, cudaStream_t s) {
     m->t++;
-    const double b1 = 0.9, b2 = 0.999;
-    const float step_size = (float)((double)lr / (1.0 - std::pow(b1, m->t)));
-    const float bc2s = (float)std::sqrt(1.0 - std::pow(b2, m->t));
-    adam_kernel<<<blocks((int64_t)m->np, 256), 256, 0, s>>>(m->P, G, m->M1, m->M2, m->np, lr, (float)b1, (float)b2,
-                                                            1e-8f, step_size, bc2s);
+    // beta1, beta2 are the FP32 values 0.9f, 0.999f throughout: in the moment updates
+    // (where 1 - beta is exact in FP32) and in the bias corrections (formed in FP64)
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float step_size = (float)((double)lr / (1.0 - std::pow((double)b1, m->t)));
+    const float bc2s = (float)std::sqrt(1.0 - std::pow((double)b2, m->t));
+    adam_kernel<<<blocks((int64_t)m->np, 256), 256, 0, s>>>(m->P, G, m->M1, m->M2, m->np, lr, b1, b2, 1e-8f,
+                                                            step_size, bc2s);
     const int64_t nmax = std::max<int64_t>(std::max<int64_t>((int64_t)m->h * m->n_in, (int64_t)m->h * m->h),
                                            std::max<int64_t>((int64_t)m->n_out * m->h, (int64_t)m->h * m->n_out_p));
     refresh_kernel<<<blocks(nmax, 256), 256, 0, s>>>(view_of(m));

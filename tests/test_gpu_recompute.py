@@ -129,3 +129,35 @@ def test_sampler_with_recompute_same_solutions(gpu):
     c = P.sample(circ, cnf, recompute_segment=6, check_every=20, max_age=40, **kw)
     d = P.sample(circ, cnf, check_every=20, max_age=40, **kw)
     assert np.array_equal(c.words(), d.words())
+
+
+@pytest.mark.parametrize("name", ["tseitin16", "mid_outputs"])
+@pytest.mark.parametrize("opt_name,lr,atol", [("gd", 0.5, 2e-5), ("adam", 0.02, 1e-3)])
+def test_recompute_trajectory_vs_oracle(gpu, name, opt_name, lr, atol):
+    """100 recomputed steps (segments of 2 to 6 levels) against the FP64 oracle's trajectory
+    from the same V0, with the bounds of the stored-layout trajectory test on the 16-level
+    circuit (10x its measured FP32 drift: 1.7e-6 GD, 1.0e-4 Adam); thresholded bits agree
+    wherever the oracle's logit is not within 10 x atol of 0."""
+    import oracle
+    text = dict(CASES)[name]()
+    P, cnf, circ, plan = _plan(text)
+    orc = oracle.Oracle(text)
+    assert list(plan.pi_vars()) == orc.circuit.pis
+    B, steps = 96, 100
+    V0 = normal_logits(B, orc.n_pi, seed=8, scale=0.5)
+    f32 = lambda x: float(np.float32(x))  # noqa: E731  (the GPU's FP32 constants)
+    res = oracle.sample_round(orc.flat, orc.n_vars, orc.clauses, V0.astype(np.float64), steps=steps, lr=f32(lr),
+                              opt=opt_name, betas=(f32(0.9), f32(0.999)), eps=f32(1e-8))
+    near = np.abs(res["V"]) <= 10 * atol
+    for k in (2, 5, 6):
+        V = torch.tensor(V0.T.copy(), device=gpu)
+        m, v = torch.zeros_like(V), torch.zeros_like(V)
+        P.sat_steps(plan, P.opt_params(opt_name, lr=lr), V, m, v, P.new_act(plan, B, segment=k),
+                    P.new_adj(plan, B), 1, steps, segment=k)
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+        got = V.cpu().numpy().T.astype(np.float64)
+        err = np.abs(got - res["V"])
+        print(f"{name} {opt_name} segment {k}: max |V - V*| after {steps} steps = {err.max():.2e}")
+        assert err.max() <= atol, (k, err.max())
+        assert ((got > 0) == (res["V"] > 0))[~near].all()
