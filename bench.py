@@ -437,6 +437,8 @@ def chosen_form_entry(P, torch, w, args, stream, peak, peak_kind):
     B, steps = w["batch"], w["steps"]
     cs = args.chosen_steps
     opt = P.opt_params("adam", lr=w["lr"])
+    # the step size of the short-budget forms (the chosen form and the plain forms at its step count)
+    opt_cs = P.opt_params("adam", lr=args.chosen_lr or w["lr"])
     t0 = time.perf_counter()
     log = {}
     w_train = dict(w, collect_steps=cs)
@@ -445,18 +447,26 @@ def chosen_form_entry(P, torch, w, args, stream, peak, peak_kind):
     plan0 = P.Plan.create(P.Circuit.build(cnf0), cnf0)
     mlp = train_proposal(P, torch, plan0, w_train, "heldout", B, opt, "bf16", log, 0, 2)
     train_s = time.perf_counter() - t0
-    forms = {"chosen": ("bf16", cs, True), "plain_bf16_same_steps": ("bf16", cs, False),
-             "plain_fp32_same_steps": ("f32", cs, False), "plain_fp32_workload_steps": ("f32", steps, False)}
+    # form: (activation type, steps, proposal: None = plain Philox init)
+    forms = {"chosen": ("bf16", cs, mlp), "plain_bf16_same_steps": ("bf16", cs, None),
+             "plain_fp32_same_steps": ("f32", cs, None), "plain_fp32_workload_steps": ("f32", steps, None)}
+    ctrl_log = {}
+    if args.chosen_control:
+        # the control reading: a proposal trained on 16 instances of other topologies, and
+        # both proposals with FP32 activations
+        ctrl = train_proposal(P, torch, plan0, w_train, "heldout_topology", B, opt, "bf16", ctrl_log, 0, 2)
+        forms.update({"control_bf16": ("bf16", cs, ctrl), "proposal_fp32": ("f32", cs, mlp),
+                      "control_fp32": ("f32", cs, ctrl)})
     acc = {k: {"unique": 0, "ms": 0.0, "valid": 0, "rounds": 0, "kernel_ms": [], "per_instance": []} for k in forms}
     R = args.chosen_rounds
     for k in range(17, 21):
         cnf = cnf0 if k == 17 else P.Cnf.from_dimacs(instance_text(w, planted_seed=k))
         plan = plan0 if k == 17 else P.Plan.create(P.Circuit.build(cnf), cnf)
         wss = {"bf16": P.new_workspace(plan, B, "bf16"), "f32": P.new_workspace(plan, B, "f32")}
-        for fi, (name, (ad, ns, use_mlp)) in enumerate(forms.items()):
+        for fi, (name, (ad, ns, net)) in enumerate(forms.items()):
             dd = P.Dedup.create(plan, max_keys=B * R, max_batch=B)
-            r = timed_rounds(P, torch, plan, wss[ad], opt, ns, R, (2 << 20) + k * 1024 + fi * 64, dd, stream,
-                             mlp=mlp if use_mlp else None)
+            r = timed_rounds(P, torch, plan, wss[ad], opt_cs if ns == cs else opt, ns, R,
+                             (2 << 20) + k * 1024 + fi * 64, dd, stream, mlp=net)
             a = acc[name]
             for key in ("unique", "ms", "valid", "rounds"):
                 a[key] += r[key]
@@ -472,7 +482,8 @@ def chosen_form_entry(P, torch, w, args, stream, peak, peak_kind):
         kavg = statistics.mean(a["kernel_ms"])
         alg = algorithmic_bytes_per_step(info, B, ad) * ns
         out[name] = {"value": a["unique"] / (a["ms"] / 1e3), "unit": "unique valid solutions/s",
-                     "act_dtype": ad, "steps": ns, "ms_per_step": a["ms"] / a["rounds"],
+                     "act_dtype": ad, "steps": ns, "lr": (opt_cs if ns == cs else opt).lr,
+                     "ms_per_step": a["ms"] / a["rounds"],
                      "valid_fraction": a["valid"] / (B * a["rounds"]), "unique": a["unique"],
                      "per_instance_value": a["per_instance"],
                      "roofline": {"bound": "hbm", "kernel": "steps_kernel", "kernel_ms_avg": kavg,
@@ -492,7 +503,9 @@ def chosen_form_entry(P, torch, w, args, stream, peak, peak_kind):
             "vs_plain_bf16_same_steps": ch["value"] / out["plain_bf16_same_steps"]["value"]
             if out["plain_bf16_same_steps"]["value"] else None,
             "validity": "every counted assignment passed the exact CNF check on the device",
-            "per_step_error_vs_fp64": BF16_PER_STEP_ERROR}
+            "per_step_error_vs_fp64": BF16_PER_STEP_ERROR,
+            **({"control": {"trained_on": "plain BF16 rounds on 16 instances of other topologies (seeds 101-116)",
+                            **ctrl_log}} if ctrl_log else {})}
 
 
 def run_curve(P, torch, plan, ws, opt, args, w, info):
@@ -574,6 +587,11 @@ def main():
                          "instances (auto: on for the default 20k-gate workload without other variants)")
     ap.add_argument("--chosen-steps", type=int, default=200, help="steps per round of the chosen form")
     ap.add_argument("--chosen-rounds", type=int, default=2, help="timed rounds per held-out instance and form")
+    ap.add_argument("--chosen-lr", type=float, default=0.0,
+                    help="Adam step size of the forms at the chosen step count (default: the workload's)")
+    ap.add_argument("--chosen-control", action="store_true",
+                    help="with the chosen form: also a proposal trained on other topologies (the control reading) "
+                         "and both proposals with FP32 activations")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     args.optimizer = args.optimizer or w.get("optimizer", "adam")
