@@ -478,6 +478,42 @@ def chosen_form_entry(P, torch, w, args, stream, peak, peak_kind):
             del dd
         del wss
         torch.cuda.empty_cache()
+    # early exit (verify every ee_k steps, harvest, restart from the proposal or Philox), the
+    # batch carried from an untimed warm call into the timed one
+    ee = {}
+    if args.chosen_early_exit:
+        ee_k, ee_age, ee_budget = 40, 160, 360
+        for name, net in (("proposal", mlp), ("plain", None)):
+            u = ms = 0.0
+            kms, per = [], []
+            for k in range(17, 21):
+                cnf = P.Cnf.from_dimacs(instance_text(w, planted_seed=k))
+                plan = P.Plan.create(P.Circuit.build(cnf), cnf)
+                ws = P.new_workspace(plan, B, "bf16")
+                dd = P.Dedup.create(plan, max_keys=B * (2 * ee_budget // ee_k + 4), max_batch=B)
+                r0 = (6 << 20) + k * 65536 + (0 if net is not None else 32768)
+                P.run_epochs(plan, ws, opt_cs, ee_budget, ee_k, ee_age, seed=0, round_=r0, dedup=dd, proposal=net)
+                torch.cuda.synchronize()
+                before = dd.count()
+                evs = []
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                P.run_epochs(plan, ws, opt_cs, ee_budget, ee_k, ee_age, seed=0, round_=r0 + 8192, dedup=dd,
+                             proposal=net, fresh=False, events=evs)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                t = e0.elapsed_time(e1)
+                n = dd.count() - before
+                u, ms = u + n, ms + t
+                per.append(round(n / (t / 1e3), 1))
+                kms += [a.elapsed_time(b) for _, (a, b) in evs]
+                del ws, dd
+            ee[name] = {"value": u / (ms / 1e3), "per_instance_value": per, "kernel_ms_avg": statistics.mean(kms)}
+        ee["config"] = {"check_every": ee_k, "max_age": ee_age, "steps_per_timed_call": ee_budget,
+                        "lr": opt_cs.lr, "act_dtype": "bf16",
+                        "note": "batch carried over from an untimed warm call; valid samples harvested and "
+                                "restarted every check_every steps (from the proposal, or from Philox)"}
+        torch.cuda.empty_cache()
     info = plan0.info
     out = {}
     for name, (ad, ns, _) in forms.items():
@@ -510,7 +546,8 @@ def chosen_form_entry(P, torch, w, args, stream, peak, peak_kind):
             "validity": "every counted assignment passed the exact CNF check on the device",
             "per_step_error_vs_fp64": BF16_PER_STEP_ERROR,
             **({"control": {"trained_on": "plain BF16 rounds on 16 instances of other topologies (seeds 101-116)",
-                            **ctrl_log}} if ctrl_log else {})}
+                            **ctrl_log}} if ctrl_log else {}),
+            **({"early_exit": ee} if ee else {})}
 
 
 def run_curve(P, torch, plan, ws, opt, args, w, info):
@@ -594,6 +631,8 @@ def main():
     ap.add_argument("--chosen-rounds", type=int, default=2, help="timed rounds per held-out instance and form")
     ap.add_argument("--chosen-lr", type=float, default=0.3,
                     help="Adam step size of the forms at the chosen step count (0: the workload's)")
+    ap.add_argument("--chosen-early-exit", type=int, default=1,
+                    help="with the chosen form: also time it (and plain BF16) under early exit (0: off)")
     ap.add_argument("--chosen-control", action="store_true",
                     help="with the chosen form: also a proposal trained on other topologies (the control reading) "
                          "and both proposals with FP32 activations")

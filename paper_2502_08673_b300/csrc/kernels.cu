@@ -483,8 +483,16 @@ __device__ void forward_levels(const DevPlan& p, const DevAct& L, T* act, Stage&
                     const VF x = ActIO<T>::ld(reinterpret_cast<const T*>(sb + j * ROWB) + c.lane * VEC);
                     const VF y = ActIO<T>::ld(reinterpret_cast<const T*>(sb + (CHUNK + j) * ROWB) + c.lane * VEC);
                     VF z;
+                    // gate_apply on two samples per instruction (the same IEEE fma per element)
+                    const float2 kw = make_float2(k.w, k.w), kz = make_float2(k.z, k.z);
+                    const float2 ky = make_float2(k.y, k.y), kx = make_float2(k.x, k.x);
 #pragma unroll
-                    for (int q = 0; q < VEC; q++) z.v[q] = gate_apply(k, x.v[q], y.v[q]);
+                    for (int q = 0; q < VEC; q += 2) {
+                        const float2 a = make_float2(x.v[q], x.v[q + 1]), b = make_float2(y.v[q], y.v[q + 1]);
+                        const float2 r = __ffma2_rn(__ffma2_rn(kw, a, kz), b, __ffma2_rn(ky, a, kx));
+                        z.v[q] = r.x;
+                        z.v[q + 1] = r.y;
+                    }
                     ActIO<T>::st(out_ch + j * TILE, z);
                 };
                 if ((ch + 1) * CHUNK <= cnt) {  // a full chunk
@@ -644,8 +652,15 @@ __device__ void level_adjoint(const DevPlan& p, const DevAct& L, const AdjRun& r
                     const float2 cc = reinterpret_cast<const float2*>(st.coef)[ch * CHUNK + j];
                     const VF ga = ActIO<float>::ld(reinterpret_cast<const float*>(sb + j * ROWF) + c.lane * VEC);
                     const VF sv = ActIO<T>::ld(reinterpret_cast<const T*>(sb + CHUNK * ROWF + j * ROWB) + c.lane * VEC);
+                    const float2 c1 = make_float2(cc.y, cc.y), c0 = make_float2(cc.x, cc.x);
 #pragma unroll
-                    for (int q = 0; q < VEC; q++) acc.v[q] = fmaf(ga.v[q], fmaf(cc.y, sv.v[q], cc.x), acc.v[q]);
+                    for (int q = 0; q < VEC; q += 2) {
+                        const float2 d = __ffma2_rn(c1, make_float2(sv.v[q], sv.v[q + 1]), c0);
+                        const float2 r = __ffma2_rn(make_float2(ga.v[q], ga.v[q + 1]), d,
+                                                    make_float2(acc.v[q], acc.v[q + 1]));
+                        acc.v[q] = r.x;
+                        acc.v[q + 1] = r.y;
+                    }
                     if ((chunk_last >> j) & 1u) {
                         st_row_hint(node_row, acc, keep_policy);
                         node_row += TILE;

@@ -28,6 +28,8 @@ __device__ __forceinline__ float4 gate_coeffs(uint32_t gop) {
     }
 }
 
+// (The tiled step kernel evaluates the same three fmas on two samples at a time with the
+// packed FP32 fma, which rounds each element exactly as fmaf does.)
 __device__ __forceinline__ float gate_apply(const float4& k, float a, float b) {
     return fmaf(fmaf(k.w, a, k.z), b, fmaf(k.y, a, k.x));
 }
