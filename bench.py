@@ -781,7 +781,9 @@ def main():
         dram_per_sample_step, dram_per_round, prof = None, None, None
     else:
         alg = algorithmic_bytes_per_step(info, B, ad, args.recompute) * (launch_steps or run_steps)
-        dram_per_sample_step, dram_per_round, prof = profile_traffic(args.workload, ad, B, launch_steps or run_steps)
+        # figures are per workload and layout: a recomputation run matches only its own capture
+        prof_key = args.workload + (f"_recompute{args.recompute}" if args.recompute else "")
+        dram_per_sample_step, dram_per_round, prof = profile_traffic(prof_key, ad, B, launch_steps or run_steps)
     kavg = statistics.mean(kernel_ms)
     achieved = alg / (kavg / 1e3) / 1e9
 
