@@ -41,6 +41,10 @@ def test_null_objects_are_rejected():
     _err(L.sat_plan_step_kernel(None, 0, C.byref(k)))
     _err(L.sat_cached_memory(None, None))
     assert L.sat_solutions_count(None) == 0
+    # the allocation-free steps and the proposal's optimiser step
+    _err(L.sat_steps_noalloc(None, 0, C.byref(opt), None, None, None, 0, None, 1, 1, 0, None))
+    _err(L.sat_mlp_apply_grad(None, None, 1e-3, None))
+    _err(L.sat_mlp_train_step(None, None, 1, 1, 1, 1e-3, 0, 0, None, None))
 
 
 def test_bad_sizes_and_options():
