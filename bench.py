@@ -717,8 +717,9 @@ def main():
             mlp.propose(ws.V, seed=0, round_=round_base + k, tau=args.tau)
         else:
             P.sat_init_normal(plan, ws.V, seed=0, round_=round_base + k, scale=w["init_scale"])
-        ws.m.zero_()
-        ws.v.zero_()
+        if args.optimizer == "adam":  # GD neither reads nor writes m, v
+            ws.m.zero_()
+            ws.v.zero_()
         if ev is not None:
             ev[0].record(stream)
         P.sat_steps(plan, opt, ws.V, ws.m, ws.v, ws.act, ws.adj, 1,

@@ -1330,8 +1330,10 @@ sat_status sat_sample_plan(const sat_plan* p, sat_dedup* d, const sat_sample_opt
         } else {
             CK(sat::launch_init_normal(dp, o->seed, o->first_round + (uint32_t)r, o->init_scale, w.V, B, B, str));
         }
-        CK(cudaMemsetAsync(w.m, 0, npi * B * 4, str));
-        CK(cudaMemsetAsync(w.v, 0, npi * B * 4, str));
+        if (o->opt.optimizer == SAT_OPT_ADAM) {  // GD neither reads nor writes m, v
+            CK(cudaMemsetAsync(w.m, 0, npi * B * 4, str));
+            CK(cudaMemsetAsync(w.v, 0, npi * B * 4, str));
+        }
         CK(cudaEventRecord(ev[1], str));
         ph.next("sat.steps");
         for (int t0 = 1; t0 <= o->steps; t0 += spl)

@@ -976,22 +976,35 @@ __global__ void restart_kernel(int32_t n_pi, const uint32_t* restart, uint64_t s
 }
 
 // ---------------------------------------------------- verification -------
-// Threshold (bit = V > 0) of a 32 x 32 (sample x input) tile: ballots give the
-// bitsliced input rows; a shared-memory transpose gives per-sample keys.
-__global__ void threshold_kernel(const float* V, int64_t ldv, int32_t n_pi, uint32_t* bits, int64_t ldw,
-                                 uint32_t* keys, int32_t kw, int64_t B) {
-    __shared__ float tile[32][33];
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int64_t b0 = (int64_t)blockIdx.x * 32, pi0 = (int64_t)blockIdx.y * 32;
-    const int64_t pi = pi0 + ty, b = b0 + tx;
-    const float val = (pi < n_pi && b < B) ? V[pi * ldv + b] : 0.0f;
-    tile[ty][tx] = val;
-    const unsigned wb = __ballot_sync(0xffffffffu, val > 0.0f);
-    if (tx == 0 && pi < n_pi) bits[pi * ldw + blockIdx.x] = wb;
-    __syncthreads();
-    const float u = tile[tx][ty];
-    const unsigned wk = __ballot_sync(0xffffffffu, u > 0.0f);
-    if (tx == 0 && b0 + ty < B) keys[(b0 + ty) * kw + blockIdx.y] = wk;
+// Threshold (bit = V > 0), one warp per block of 32 samples x 32 inputs (grid-stride over
+// the blocks, consecutive warps on consecutive sample blocks of one input block).  Lane j
+// loads V[pi][b0 + j] for the block's 32 inputs (coalesced 128-byte rows, 32 loads in
+// flight per warp); the ballot of each input row is its bitsliced word (lane r stores row
+// r's), and lane j's own bits over the 32 inputs are its sample's key word.
+__global__ void __launch_bounds__(256) threshold_kernel(const float* V, int64_t ldv, int32_t n_pi, uint32_t* bits,
+                                                        int64_t ldw, uint32_t* keys, int32_t kw, int64_t B) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nb = (B + 31) / 32, ng = (n_pi + 31) / 32;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nb * ng; t += nwarps) {
+        const int64_t g = t / nb, sb = t - g * nb;
+        const int64_t b = sb * 32 + lane;
+        const int pi0 = (int)(g * 32);
+        const int nrows = min(32, n_pi - pi0);
+        float x[32];
+#pragma unroll
+        for (int r = 0; r < 32; r++) x[r] = (r < nrows && b < B) ? V[(int64_t)(pi0 + r) * ldv + b] : 0.0f;
+        uint32_t key = 0, row = 0;
+#pragma unroll
+        for (int r = 0; r < 32; r++) {
+            const bool bit = x[r] > 0.0f;
+            key |= (uint32_t)bit << r;
+            const unsigned wb = __ballot_sync(FULL, bit);
+            if (lane == r) row = wb;
+        }
+        if (lane < nrows) bits[(int64_t)(pi0 + lane) * ldw + sb] = row;
+        if (b < B) keys[b * kw + g] = key;
+    }
 }
 
 // Boolean pass over every gate (constrained or not), 32 samples per word.
@@ -1320,8 +1333,9 @@ cudaError_t launch_restart(const DevPlan& p, const uint32_t* restart, uint64_t s
 cudaError_t launch_threshold(const DevPlan& p, const float* V, int64_t ldv, uint32_t* node_bits, int64_t ldw,
                              uint32_t* keys, int64_t B, cudaStream_t s) {
     if (B == 0 || p.n_pi == 0) return cudaSuccess;
-    dim3 grid((unsigned)((B + 31) / 32), (unsigned)((p.n_pi + 31) / 32));
-    threshold_kernel<<<grid, dim3(32, 32), 0, s>>>(V, ldv, p.n_pi, node_bits, ldw, keys, p.key_words, B);
+    const int64_t blocks = ((B + 31) / 32) * ((p.n_pi + 31) / 32);  // 32 x 32 blocks, one per warp
+    const unsigned grid = (unsigned)std::min<int64_t>((blocks + 7) / 8, 148 * 8);
+    threshold_kernel<<<grid, 256, 0, s>>>(V, ldv, p.n_pi, node_bits, ldw, keys, p.key_words, B);
     return cudaGetLastError();
 }
 
