@@ -440,12 +440,14 @@ def chosen_form_entry(P, torch, w, args, stream, peak, peak_kind):
     opt = P.opt_params("adam", lr=w["lr"])
     # the step size of the short-budget forms (the chosen form and the plain forms at its step count)
     opt_cs = P.opt_params("adam", lr=args.chosen_lr or w["lr"])
+    info0 = None
     t0 = time.perf_counter()
     log = {}
     w_train = dict(w, collect_steps=200)
     text0 = instance_text(w, planted_seed=17)
     cnf0 = P.Cnf.from_dimacs(text0)
     plan0 = P.Plan.create(P.Circuit.build(cnf0), cnf0)
+    info0 = plan0.info
     # training data: plain BF16 rounds of 200 steps at the workload's lr (a setting that finds
     # many distinct solutions per round; it need not be the timed operating point)
     mlp = train_proposal(P, torch, plan0, w_train, "heldout", B, opt, "bf16", log, 0, 2)
@@ -469,7 +471,7 @@ def chosen_form_entry(P, torch, w, args, stream, peak, peak_kind):
         for fi, (name, (ad, ns, net)) in enumerate(forms.items()):
             dd = P.Dedup.create(plan, max_keys=B * R, max_batch=B)
             r = timed_rounds(P, torch, plan, wss[ad], opt_cs if ns == cs else opt, ns, R,
-                             (2 << 20) + k * 1024 + fi * 64, dd, stream, mlp=net)
+                             (2 << 20) + k * 1024 + fi * 64, dd, stream, mlp=net, tau=args.chosen_tau)
             a = acc[name]
             for key in ("unique", "ms", "valid", "rounds"):
                 a[key] += r[key]
@@ -492,14 +494,15 @@ def chosen_form_entry(P, torch, w, args, stream, peak, peak_kind):
                 ws = P.new_workspace(plan, B, "bf16")
                 dd = P.Dedup.create(plan, max_keys=B * (2 * ee_budget // ee_k + 4), max_batch=B)
                 r0 = (6 << 20) + k * 65536 + (0 if net is not None else 32768)
-                P.run_epochs(plan, ws, opt_cs, ee_budget, ee_k, ee_age, seed=0, round_=r0, dedup=dd, proposal=net)
+                P.run_epochs(plan, ws, opt_cs, ee_budget, ee_k, ee_age, seed=0, round_=r0, dedup=dd, proposal=net,
+                             tau=args.chosen_tau)
                 torch.cuda.synchronize()
                 before = dd.count()
                 evs = []
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
                 P.run_epochs(plan, ws, opt_cs, ee_budget, ee_k, ee_age, seed=0, round_=r0 + 8192, dedup=dd,
-                             proposal=net, fresh=False, events=evs)
+                             proposal=net, tau=args.chosen_tau, fresh=False, events=evs)
                 e1.record(stream)
                 torch.cuda.synchronize()
                 t = e0.elapsed_time(e1)
@@ -514,6 +517,35 @@ def chosen_form_entry(P, torch, w, args, stream, peak, peak_kind):
                         "note": "batch carried over from an untimed warm call; valid samples harvested and "
                                 "restarted every check_every steps (from the proposal, or from Philox)"}
         torch.cuda.empty_cache()
+    # end to end through sat_sample (host CNF and circuit objects, the proposal as V0, BF16),
+    # one untimed call per instance, then timed calls; distinct solutions over the timed calls
+    e2e = None
+    if args.chosen_e2e > 0:
+        t_sum, u_sum, calls, h2d, d2h = 0.0, 0, 0, 0, 0
+        for k in range(17, 21):
+            cnf = P.Cnf.from_dimacs(instance_text(w, planted_seed=k))
+            circ = P.Circuit.build(cnf)
+            kept = []
+            for c in range(-1, args.chosen_e2e):
+                if c == 0:
+                    torch.cuda.synchronize()
+                    t1 = time.perf_counter()
+                sols = P.sample(circ, cnf, n_wanted=10 ** 12, batch=B, steps=cs, max_rounds=1, lr=opt_cs.lr,
+                                seed=0, first_round=(7 << 20) + k * 64 + c + 1, act_dtype="bf16", proposal=mlp,
+                                tau=args.chosen_tau)
+                if c >= 0:
+                    kept.append(sols)
+                    calls += 1
+                    d2h += len(sols) * info0["key_words"] * 4 + B // 8 + 16
+                    h2d += info0["upload_bytes"]
+            t_sum += time.perf_counter() - t1
+            words = [x.words() for x in kept if len(x)]
+            u_sum += int(np.unique(np.concatenate(words), axis=0).shape[0]) if words else 0
+        e2e = {"value": u_sum / t_sum, "unit": "unique valid solutions/s", "calls": calls,
+               "wall_ms_per_call": 1e3 * t_sum / calls, "h2d_bytes_per_step": h2d // calls,
+               "d2h_bytes_per_step": d2h // calls,
+               "note": "sat_sample from host CNF/circuit objects with the proposal network and BF16 activations: "
+                       "plan upload, proposal, one round, key download; distinct over the timed calls of an instance"}
     info = plan0.info
     out = {}
     for name, (ad, ns, _) in forms.items():
@@ -532,7 +564,8 @@ def chosen_form_entry(P, torch, w, args, stream, peak, peak_kind):
                                   "frac": alg / (kavg / 1e3) / 1e9 / peak, "peak_kind": peak_kind,
                                   "traffic": per_ss * B * ns if per_ss else None, "traffic_source": src}}
     ch = out.pop("chosen")
-    return {**ch, "form": "BF16 activations + learned proposal (V0 = MLP(z), IMLE-trained)", "batch": B,
+    return {**ch, "form": "BF16 activations + learned proposal (V0 = tau MLP(z), IMLE-trained)", "batch": B,
+            "tau": args.chosen_tau,
             "rounds_timed": acc["chosen"]["rounds"], "instances": "planted seeds 17-20 of the benchmarked topology",
             "proposal": {"trained_on": "distinct solutions of plain BF16 rounds (200 steps) on planted seeds 1-16",
                          **log, "train_and_collect_s": train_s},
@@ -547,7 +580,8 @@ def chosen_form_entry(P, torch, w, args, stream, peak, peak_kind):
             "per_step_error_vs_fp64": BF16_PER_STEP_ERROR,
             **({"control": {"trained_on": "plain BF16 rounds on 16 instances of other topologies (seeds 101-116)",
                             **ctrl_log}} if ctrl_log else {}),
-            **({"early_exit": ee} if ee else {})}
+            **({"early_exit": ee} if ee else {}),
+            **({"e2e": e2e} if e2e else {})}
 
 
 def run_curve(P, torch, plan, ws, opt, args, w, info):
@@ -633,6 +667,10 @@ def main():
                     help="Adam step size of the forms at the chosen step count (0: the workload's)")
     ap.add_argument("--chosen-early-exit", type=int, default=1,
                     help="with the chosen form: also time it (and plain BF16) under early exit (0: off)")
+    ap.add_argument("--chosen-tau", type=float, default=2.0,
+                    help="scale of the proposal's logits in the chosen form (V0 = tau MLP(z))")
+    ap.add_argument("--chosen-e2e", type=int, default=2,
+                    help="with the chosen form: timed sat_sample calls per held-out instance (0: none)")
     ap.add_argument("--chosen-control", action="store_true",
                     help="with the chosen form: also a proposal trained on other topologies (the control reading) "
                          "and both proposals with FP32 activations")
