@@ -854,7 +854,8 @@ def main():
     default_variant = (args.workload == "tseitin20k" and args.proposal == "none" and args.check_every <= 0
                        and not args.direct and not args.recompute and not args.shuffle_clauses
                        and args.optimizer == "adam" and not args.batch and not args.gd_steps and not args.lr)
-    if args.chosen_form == "on" or (args.chosen_form == "auto" and default_variant):
+    # the chosen-form comparison belongs to the single-GPU line (a scaling run times the plain form)
+    if args.chosen_form == "on" or (args.chosen_form == "auto" and default_variant and world == 1):
         chosen = chosen_form_entry(P, torch, w, args, stream, peak, peak_kind)
     e2e = None
     if not args.no_e2e:
