@@ -244,6 +244,7 @@ sat_status report_error(sat_status s, const std::string& msg) { return fail(s, m
 const DevPlan* plan_device(const sat_plan* p) { return &p->dp; }
 sat_status check_plan_call(const sat_plan* p, int64_t B, int64_t ldv) { return check_layout(p, B, ldv); }
 bool opt_params_ok(const sat_opt_params* o) { return opt_ok(o); }
+OptParams opt_params_of(const sat_opt_params* o) { return opt_of(o); }
 }  // namespace sat
 
 extern "C" {

@@ -132,4 +132,7 @@ const DevPlan* plan_device(const sat_plan* p);
 sat_status check_plan_call(const sat_plan* p, int64_t B, int64_t ldv);
 // Optimiser parameters the kernels accept (Adam with beta1, beta2 in [0, 1), or GD).
 bool opt_params_ok(const sat_opt_params* o);
+// The kernels' copy of checked optimiser parameters.
+struct OptParams;
+OptParams opt_params_of(const sat_opt_params* o);
 }  // namespace sat

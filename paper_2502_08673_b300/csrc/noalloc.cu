@@ -51,16 +51,6 @@ cudaError_t scratch_address(void** out) {
     return cudaSuccess;
 }
 
-sat::OptParams opt_of(const sat_opt_params* o) {
-    sat::OptParams r;
-    r.opt = o->optimizer;
-    r.lr = o->lr;
-    r.b1 = o->beta1;
-    r.b2 = o->beta2;
-    r.eps = o->eps;
-    return r;
-}
-
 }  // namespace
 
 extern "C" sat_status sat_steps_noalloc(const sat_plan* p, sat_act_dtype act_dtype, const sat_opt_params* o,
@@ -79,7 +69,7 @@ extern "C" sat_status sat_steps_noalloc(const sat_plan* p, sat_act_dtype act_dty
     if (sat::steps_use_resident(*dp, (int)act_dtype)) {
         // the shared-memory resident kernel keeps activations and adjoints on chip: no scratch
         if (B == 0 || n_steps == 0) return SAT_OK;
-        cudaError_t e = sat::launch_steps(*dp, dp->full, (int)act_dtype, opt_of(o), V, m, v, ldv, nullptr, nullptr,
+        cudaError_t e = sat::launch_steps(*dp, dp->full, (int)act_dtype, sat::opt_params_of(o), V, m, v, ldv, nullptr, nullptr,
                                           loss, t0, n_steps, B, (cudaStream_t)stream);
         if (e != cudaSuccess) return sat::report_error(SAT_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
         return SAT_OK;
@@ -102,7 +92,7 @@ extern "C" sat_status sat_steps_noalloc(const sat_plan* p, sat_act_dtype act_dty
     if (e != cudaSuccess)
         return sat::report_error(SAT_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
     unsigned char* s = static_cast<unsigned char*>(base);
-    e = sat::launch_steps(*dp, dp->full, (int)act_dtype, opt_of(o), V, m, v, ldv, s,
+    e = sat::launch_steps(*dp, dp->full, (int)act_dtype, sat::opt_params_of(o), V, m, v, ldv, s,
                           reinterpret_cast<float*>(s + act_bytes), loss, t0, n_steps, B, (cudaStream_t)stream);
     if (e != cudaSuccess) return sat::report_error(SAT_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
     return SAT_OK;
