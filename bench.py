@@ -431,10 +431,11 @@ def chosen_form_entry(P, torch, w, args, stream, peak, peak_kind):
     on distinct solutions that plain BF16 rounds find on 16 instances of the benchmarked
     circuit topology with other planted inputs (planted seeds 1..16); it is then timed on
     4 held-out instances (planted seeds 17..20, never seen in training) at its operating
-    point (120 steps per round, lr 0.3: the best of a sweep of the short-budget forms),
-    beside the plain forms on the same instances: BF16 and FP32 at the same steps and lr,
-    and FP32 at the workload's own step count and lr.  Every counted assignment passed the
-    exact CNF check on the device."""
+    point (120 steps per round, lr 0.3, V0 = 2 MLP(z): the best of sweeps of the short-budget
+    forms and of the logit scale), beside the plain forms on the same instances: BF16 and
+    FP32 at the same steps and lr, and FP32 at the workload's own step count and lr; also
+    under early exit and end to end through sat_sample.  Every counted assignment passed
+    the exact CNF check on the device."""
     B, steps = w["batch"], w["steps"]
     cs = args.chosen_steps
     opt = P.opt_params("adam", lr=w["lr"])
