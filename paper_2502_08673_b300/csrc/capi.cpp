@@ -445,6 +445,42 @@ sat_status sat_plan_create(const sat_circuit* c, const sat_cnf* cnf, sat_plan** 
             fe[e] = make_int4(P.fo_g[e] < 0 ? d.seed_row : adj_row[P.fo_g[e]], P.fo_sib[e], i0, i1);
         }
     }
+    // Dead adjoint rows per backward level (ring only): a gate's adjoint row is read by the
+    // fan-out edges of its inputs, the last time at the level of its lowest input; it is
+    // dropped from L2 after that level unless the very next level reuses its slot (its level
+    // is then exactly max_span above, and the slot's new rows are written right after the
+    // barrier).
+    std::vector<int32_t> dead_off(d.n_clev + 2, 0), dead_row;
+    if (d.adj_slots > 0) {
+        auto level_of = [&](int64_t x) {
+            if (x < (int64_t)P.n_cone_pi) return 0;
+            return (int32_t)(std::upper_bound(P.c_level_off.begin() + 1, P.c_level_off.end(), (int32_t)x) -
+                             P.c_level_off.begin()) - 1;
+        };
+        std::vector<int32_t> last(P.n_cone, -1);  // lowest level among each consumer's inputs
+        for (size_t n = 0; n + 1 < P.fo_off.size(); n++) {
+            const int32_t ln = level_of((int64_t)n);
+            for (uint64_t e = P.fo_off[n]; e < P.fo_off[n + 1]; e++) {
+                const int64_t g = P.fo_g[e];
+                if (g >= 0 && (last[g] < 0 || ln < last[g])) last[g] = ln;
+            }
+        }
+        std::vector<std::vector<int32_t>> per(d.n_clev + 1);
+        for (int32_t L = 1; L <= d.n_clev; L++)
+            for (int32_t x = P.c_level_off[L]; x < P.c_level_off[L + 1]; x++) {
+                const int32_t l = last[x];
+                if (l >= 0 && l < L && L - l <= d.max_span - 1)
+                    per[l].push_back((int32_t)(sat::adj_level_row(d, L, P.c_level_off[L]) + (x - P.c_level_off[L])));
+            }
+        for (int32_t l = 0; l <= d.n_clev; l++) {
+            dead_off[l] = (int32_t)dead_row.size();
+            dead_row.insert(dead_row.end(), per[l].begin(), per[l].end());
+        }
+        dead_off[d.n_clev + 1] = (int32_t)dead_row.size();
+        for (int32_t r : dead_row)
+            if (r < (int32_t)P.n_cone_pi || r >= d.seed_row)
+                return bail(fail(SAT_ERR_ARG, "internal error: dead adjoint row outside the ring"));
+    }
     // bit 31 of the sibling field marks the last edge of each node's range
     for (size_t n = 0; n + 1 < P.fo_off.size(); n++)
         if (P.fo_off[n + 1] > P.fo_off[n]) fe[(size_t)P.fo_off[n + 1] - 1].y |= (int32_t)0x80000000u;
@@ -465,6 +501,10 @@ sat_status sat_plan_create(const sat_circuit* c, const sat_cnf* cnf, sat_plan** 
     if ((st = upload(p, fg, &d.f_gate)) != SAT_OK) return bail(st);
     if ((st = upload(p, P.cl_off, &d.cl_off)) != SAT_OK) return bail(st);
     if ((st = upload(p, cl_lit, &d.cl_lit)) != SAT_OK) return bail(st);
+    if (!dead_row.empty()) {
+        if ((st = upload(p, dead_off, &d.dead_off)) != SAT_OK) return bail(st);
+        if ((st = upload(p, dead_row, &d.dead_row)) != SAT_OK) return bail(st);
+    }
     d.full.k = 0;
     d.full.n_act_rows = (int64_t)P.n_cone;
     d.full.act_off = d.c_level_off;

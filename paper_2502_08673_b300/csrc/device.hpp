@@ -59,6 +59,11 @@ struct DevPlan {
     const int32_t* cl_lit = nullptr;    // node << 1 | negation
     int32_t key_words = 0;              // ceil(n_pi / 32)
     unsigned int* status = nullptr;     // device status word (bit 2: an async-copy wait expired)
+    // Adjoint ring rows that no backward level below l reads (their consumer's inputs all lie
+    // at levels >= l) and whose slot the next level does not reuse: rows
+    // dead_row[dead_off[l] .. dead_off[l + 1]) are dropped from L2 after level l (ring only).
+    const int32_t* dead_off = nullptr;  // [n_clev + 2]
+    const int32_t* dead_row = nullptr;
     DevAct full;                        // the full act layout (row = node)
     int32_t step_kernel = 0;            // fused steps: STEP_KERNEL_AUTO / _TILED / _RESIDENT
     // host mirrors of the level offsets (launch loops need them)

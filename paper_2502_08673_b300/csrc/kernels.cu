@@ -704,6 +704,20 @@ __device__ __forceinline__ void discard_adj_rows(const DevPlan& p, int l, const 
         discard_l2_line(b + (size_t)row * TILE * 4 + (size_t)i * 128);
 }
 
+// Discard, from L2, the ring rows whose last reader was level l (their dirty lines are
+// then never written back); the whole CTA (both CTAs of a split tile) shares the lines.
+__device__ __forceinline__ void discard_dead_rows(const DevPlan& p, int l, const float* adj, const TileCtx& c) {
+    const int lo = __ldg(&p.dead_off[l]), hi = __ldg(&p.dead_off[l + 1]);
+    const char* b = reinterpret_cast<const char*>(adj);
+    constexpr int LINES_PER_ROW = TILE * 4 / 128;
+    const int n = (hi - lo) * LINES_PER_ROW;
+    const int stride = (c.split ? 2 : 1) * (int)blockDim.x;
+    for (int i = c.rank * (int)blockDim.x + (int)threadIdx.x; i < n; i += stride) {
+        const int row = __ldg(&p.dead_row[lo + i / LINES_PER_ROW]);
+        discard_l2_line(b + (size_t)row * TILE * 4 + (size_t)(i % LINES_PER_ROW) * 128);
+    }
+}
+
 // Discard the whole adjoint scratch of this tile (after the input level has been read).
 __device__ __forceinline__ void discard_adj_all(const DevPlan& p, const float* adj, const TileCtx& c) {
     const char* b = reinterpret_cast<const char*>(adj);
@@ -750,6 +764,7 @@ __device__ void tile_backward(const DevPlan& p, const DevAct& L, const OptParams
         // slot is level l - 1's, written right after this barrier: a discard there would
         // race with those stores, so ring slots are only discarded at the end.)
         if (p.adj_slots == 0 && l + p.max_span <= p.n_clev) discard_adj_rows(p, l + p.max_span, adj, c);
+        if (p.adj_slots > 0 && p.dead_off) discard_dead_rows(p, l, adj, c);
     }
     const bool adam = UPDATE && o.opt == 0;
     for (int i0 = c.vw * UBATCH; i0 < p.n_cone_pi; i0 += c.nvw * UBATCH) {
