@@ -230,7 +230,10 @@ sat_status sat_opt_update(const sat_plan* p, const sat_opt_params* o, float* V, 
 
 /* The fused hot loop: n_steps x (forward, loss, adjoint, update) at steps
  * t0 .. t0 + n_steps - 1, one kernel launch.  loss (nullable) receives the
- * per-sample loss of the last step's forward pass. */
+ * per-sample loss of the last step's forward pass.  act and adj are scratch
+ * (sat_plan_scratch_elems / sat_plan_layout_elems elements, 16-byte aligned):
+ * their contents are undefined after the call (rows are dropped from L2 once
+ * their last reader has run). */
 sat_status sat_steps(const sat_plan* p, sat_act_dtype act_dtype, const sat_opt_params* o, float* V, float* m,
                      float* v, int64_t ldv, void* act, float* adj, float* loss, int32_t t0, int32_t n_steps,
                      int64_t B, void* stream);
