@@ -106,3 +106,22 @@ def test_sampler_same_solutions_on_both_kernels(gpu):
         b = P.sample(circ, cnf, step_kernel="resident", **kw, **extra)
         assert len(a) > 0
         assert np.array_equal(a.words(), b.words())
+
+
+@pytest.mark.parametrize("act_dtype", ["f32", "bf16", "f16"])
+def test_resident_two_samples_per_lane_bit_identical_to_tiled(gpu, act_dtype):
+    """Batches of at least 148 x 64 x 8 samples run the resident kernel with two samples per
+    lane (64 per CTA, pairs through the packed FP32 fma) on narrow circuits: the same values
+    as the tiled kernel, bit for bit, with a ragged last CTA, Adam with ages and GD."""
+    P, plan = _plan(SMALL["tseitin_50_50_d5"]())
+    assert plan.step_kernel(act_dtype) == "resident"
+    B = 148 * 64 * 8 + 77
+    V0 = torch.tensor(normal_logits(B, plan.n_pi, seed=4).T.copy(), device=gpu)
+    for optname, aged in (("adam", True), ("gd", False)):
+        age = torch.randint(0, 50, (B,), dtype=torch.int32, device=gpu) if aged else None
+        opt = P.opt_params(optname, lr=0.05)
+        a = _run(P, plan, "tiled", V0, opt, act_dtype, 3, 6, age)
+        b = _run(P, plan, "resident", V0, opt, act_dtype, 3, 6, age)
+        for x, y, what in zip(a, b, ("V", "m", "v", "loss")):
+            assert torch.equal(x, y), (act_dtype, optname, what, (x - y).abs().max().item())
+    plan.set_step_kernel("auto")
