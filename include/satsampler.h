@@ -197,10 +197,12 @@ void sat_plan_free(sat_plan* p);
 /* ------------------------------------------- hot-path kernels (device) ---
  * All buffers are caller-owned device memory; B >= 0 samples. */
 
-/* V[r][b] = scale * z, z standard normal from Box-Muller on the first two
- * words of Philox4x32-10 (Salmon et al., SC'11) at counter (b, r, round, 0)
- * with key (seed low, seed high).  Initial distribution: the paper does not
- * state one; this is the library's choice. */
+/* V[r][b] = scale * z_k, k = b mod 4: the Philox4x32-10 block (Salmon et al.,
+ * SC'11) at counter (b / 4, r, round, 0) with key (seed low, seed high) gives
+ * four standard normals z_0 .. z_3 as two Box-Muller pairs (cos, sin) of its
+ * words (x, y) and (z, w), u1 = ((first >> 8) + 1) / 2^24, u2 = (second >> 8) /
+ * 2^24.  Initial distribution: the paper does not state one; this is the
+ * library's choice. */
 sat_status sat_init_normal(const sat_plan* p, uint64_t seed, uint32_t round, float scale, float* V, int64_t ldv,
                            int64_t B, void* stream);
 

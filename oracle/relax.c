@@ -16,7 +16,7 @@
  *
  * Also here: Boolean evaluation of the same circuit, the CNF check against
  * the original clauses, and Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
- * with a Box-Muller transform for the initial logits.
+ * with a Box-Muller transform (four normals per block) for the initial logits.
  */
 #include <math.h>
 #include <stdint.h>
@@ -237,16 +237,20 @@ void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint3
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* Initial logits V0[s][j] = scale * z, z from Box-Muller on the first two
- * Philox words of counter (s, j, round, 0) under key (seed lo, seed hi). */
+/* Initial logits V0[s][j] = scale * z_k, k = s mod 4: the Philox block of counter
+ * (s / 4, j, round, 0) under key (seed lo, seed hi) gives four normals, the Box-Muller
+ * pairs (cos, sin) of its words (0, 1) and (2, 3). */
 void orc_init_normal(int S, int n_pi, uint64_t seed, uint32_t round, double scale, double *V) {
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     for (int s = 0; s < S; s++)
         for (int j = 0; j < n_pi; j++) {
-            uint32_t ctr[4] = {(uint32_t)s, (uint32_t)j, round, 0u}, o[4];
+            uint32_t ctr[4] = {(uint32_t)(s / 4), (uint32_t)j, round, 0u}, o[4];
             orc_philox4x32_10(ctr, key, o);
-            double u1 = (double)((o[0] >> 8) + 1u) * (1.0 / 16777216.0);
-            double u2 = (double)(o[1] >> 8) * (1.0 / 16777216.0);
-            V[(size_t)s * n_pi + j] = scale * sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+            int k = s % 4;
+            uint32_t a = o[k < 2 ? 0 : 2], b = o[k < 2 ? 1 : 3];
+            double u1 = (double)((a >> 8) + 1u) * (1.0 / 16777216.0);
+            double u2 = (double)(b >> 8) * (1.0 / 16777216.0);
+            double rad = sqrt(-2.0 * log(u1));
+            V[(size_t)s * n_pi + j] = scale * rad * ((k % 2 == 0) ? cos(2.0 * M_PI * u2) : sin(2.0 * M_PI * u2));
         }
 }

@@ -940,17 +940,52 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 ctr, uint2 key) {
     return ctr;
 }
 
-// V[r][b] = scale * sqrt(-2 ln u1) cos(2 pi u2), (u1, u2) from counter (b, r, round, 0).
-// Samples on x (coalesced within a row), rows on y, both grid-stride.
+// Four standard normals of input row r for samples 4c .. 4c + 3: the Philox4x32-10 block at
+// counter (c, r, round, 0) gives two Box-Muller pairs, (cos, sin) of words (x, y) and of
+// words (z, w), with u1 = ((first >> 8) + 1) / 2^24 and u2 = (second >> 8) / 2^24.
+__device__ __forceinline__ float4 normal4(uint32_t c, uint32_t r, uint32_t round, uint2 key) {
+    const uint4 o = philox4x32_10(make_uint4(c, r, round, 0u), key);
+    float4 z;
+    {
+        const float u1 = (float)((o.x >> 8) + 1u) * (1.0f / 16777216.0f);
+        const float u2 = (float)(o.y >> 8) * (1.0f / 16777216.0f);
+        const float rad = sqrtf(-2.0f * logf(u1));
+        float sn, cs;
+        sincospif(2.0f * u2, &sn, &cs);
+        z.x = rad * cs;
+        z.y = rad * sn;
+    }
+    {
+        const float u1 = (float)((o.z >> 8) + 1u) * (1.0f / 16777216.0f);
+        const float u2 = (float)(o.w >> 8) * (1.0f / 16777216.0f);
+        const float rad = sqrtf(-2.0f * logf(u1));
+        float sn, cs;
+        sincospif(2.0f * u2, &sn, &cs);
+        z.z = rad * cs;
+        z.w = rad * sn;
+    }
+    return z;
+}
+
+// V[r][b] = scale * z, z the (b mod 4)-th normal of group c = b / 4 of row r (normal4).
+// One thread per group of four samples (coalesced within a row), rows on y, both
+// grid-stride; 16-byte stores where the group is whole and aligned.
 __global__ void init_normal_kernel(int32_t n_pi, uint64_t seed, uint32_t round, float scale, float* V, int64_t ldv,
                                    int64_t B) {
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    const int64_t groups = (B + 3) / 4;
     for (int64_t r = blockIdx.y; r < n_pi; r += gridDim.y)
-        for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < B; b += (int64_t)gridDim.x * blockDim.x) {
-            const uint4 o = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)r, round, 0u), key);
-            const float u1 = (float)((o.x >> 8) + 1u) * (1.0f / 16777216.0f);
-            const float u2 = (float)(o.y >> 8) * (1.0f / 16777216.0f);
-            V[r * ldv + b] = scale * sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+        for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < groups;
+             c += (int64_t)gridDim.x * blockDim.x) {
+            const float4 z = normal4((uint32_t)c, (uint32_t)r, round, key);
+            float* out = V + r * ldv + 4 * c;
+            const float4 x = make_float4(scale * z.x, scale * z.y, scale * z.z, scale * z.w);
+            if (4 * c + 3 < B && ((uintptr_t)out & 15u) == 0) {
+                *reinterpret_cast<float4*>(out) = x;
+            } else {
+                const float xs[4] = {x.x, x.y, x.z, x.w};
+                for (int k = 0; k < 4 && 4 * c + k < B; k++) out[k] = xs[k];
+            }
         }
 }
 
@@ -979,10 +1014,9 @@ __global__ void restart_kernel(int32_t n_pi, const uint32_t* restart, uint64_t s
         if (src) {
             x = src[r * lds + b];
         } else {
-            const uint4 o = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)r, round, 0u), key);
-            const float u1 = (float)((o.x >> 8) + 1u) * (1.0f / 16777216.0f);
-            const float u2 = (float)(o.y >> 8) * (1.0f / 16777216.0f);
-            x = scale * sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+            const float4 z = normal4((uint32_t)(b >> 2), (uint32_t)r, round, key);  // what init draws for b
+            const int k = (int)(b & 3);
+            x = scale * (k == 0 ? z.x : k == 1 ? z.y : k == 2 ? z.z : z.w);
         }
         V[r * ldv + b] = x;
         m[r * ldv + b] = 0.0f;
@@ -1276,7 +1310,9 @@ cudaError_t launch_init_normal(const DevPlan& p, uint64_t seed, uint32_t round, 
                                int64_t B, cudaStream_t s) {
     const int64_t n = (int64_t)p.n_pi * B;
     if (n == 0) return cudaSuccess;
-    const dim3 grid((unsigned)std::min<int64_t>((B + 255) / 256, 1024), (unsigned)std::min<int64_t>(p.n_pi, 65535));
+    const int64_t groups = (B + 3) / 4;
+    const dim3 grid((unsigned)std::min<int64_t>((groups + 255) / 256, 1024),
+                    (unsigned)std::min<int64_t>(p.n_pi, 65535));
     init_normal_kernel<<<grid, 256, 0, s>>>(p.n_pi, seed, round, scale, V, ldv, B);
     return cudaGetLastError();
 }

@@ -442,6 +442,25 @@ def test_philox_known_answers():
         [0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1]
 
 
+def test_init_normal_uses_the_stated_blocks():
+    """V0[s][j] = scale z_(s mod 4) from the Philox block of counter (s // 4, j, round, 0): entries
+    re-derived from the pinned block function, and the pair structure of Box-Muller (the two
+    normals of a pair are uncorrelated; z0^2 + z1^2 is exponential with mean 2)."""
+    V = oracle.init_normal(4001, 7, seed=0x1234_5678_9ABC, rnd=3, scale=1.5)
+    key = [0x5678_9ABC, 0x1234]
+    for s, j in ((0, 0), (5, 3), (10, 6), (4000, 2)):
+        o = oracle.philox4x32_10([s // 4, j, 3, 0], key)
+        k = s % 4
+        a, b = (o[0], o[1]) if k < 2 else (o[2], o[3])
+        r = math.sqrt(-2 * math.log(((a >> 8) + 1) / 2 ** 24))
+        t = 2 * math.pi * (b >> 8) / 2 ** 24
+        assert abs(V[s, j] - 1.5 * r * (math.cos(t) if k % 2 == 0 else math.sin(t))) < 1e-12
+    Z = oracle.init_normal(40000, 4, seed=9, rnd=0, scale=1.0)
+    z0, z1 = Z[0::4].ravel(), Z[1::4].ravel()
+    assert abs(np.corrcoef(z0, z1)[0, 1]) < 0.02
+    assert abs((z0 ** 2 + z1 ** 2).mean() - 2.0) < 0.05 and abs(np.median(z0 ** 2 + z1 ** 2) - 2 * math.log(2)) < 0.05
+
+
 def test_init_normal_moments():
     V = oracle.init_normal(4000, 16, seed=5, rnd=0, scale=2.0)
     assert abs(V.mean()) < 0.05 and abs(V.std() - 2.0) < 0.05
