@@ -1191,13 +1191,21 @@ __global__ void dedup_insert_kernel(DevDedup d, const uint32_t* keys, const uint
     slot_of[s] = where;
 }
 
-// Move this batch's new keys into the pool and point their slots at it.
+// Move this batch's new keys into the pool and point their slots at it.  Pool indices are
+// taken one atomic add per warp (the warp's new keys, in lane order).
 __global__ void dedup_commit_kernel(DevDedup d, const uint32_t* keys, int64_t B, const unsigned long long* slot_of) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= B) return;
-    const unsigned long long pos = slot_of[s];
-    if (pos == EMPTY_SLOT) return;
-    const unsigned long long idx = atomicAdd(d.count, 1ull);
+    const unsigned long long pos = s < B ? slot_of[s] : EMPTY_SLOT;
+    const bool mine = pos != EMPTY_SLOT;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned ballot = __ballot_sync(0xffffffffu, mine);
+    if (ballot == 0u) return;
+    const int leader = __ffs(ballot) - 1;
+    unsigned long long base = 0;
+    if ((int)lane == leader) base = atomicAdd(d.count, (unsigned long long)__popc(ballot));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (!mine) return;
+    const unsigned long long idx = base + (unsigned long long)__popc(ballot & ((1u << lane) - 1u));
     if (idx >= d.pool_capacity) {  // cannot happen when the host checked capacity first
         atomicOr(d.status, 2u);
         d.slots[pos] = EMPTY_SLOT;
