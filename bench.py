@@ -929,8 +929,10 @@ def main():
                                      (dram_per_sample_step * B * (launch_steps or run_steps))
                                      if dram_per_sample_step else None),
                          "traffic_source": prof},
-            "gpu_launches": ((7 + step_kernel_launches(B, torch, skind)) * args.steps if args.check_every <= 0
-                             else (8 + step_kernel_launches(B, torch, skind)) * len(ee_events)),
+            # per round: init, threshold (bits, keys), Boolean pass, valid init, CNF check, dedup
+            # insert and commit, plus the step kernel's launches (early exit: retire, restart too)
+            "gpu_launches": ((8 + step_kernel_launches(B, torch, skind)) * args.steps if args.check_every <= 0
+                             else (9 + step_kernel_launches(B, torch, skind)) * len(ee_events)),
             "transform_s": transform_s,
             "plan": {k: info[k] for k in ("n_pi", "n_cone_pi", "n_cone_gates", "n_gates", "n_clauses",
                                           "n_cone_levels", "max_span")},

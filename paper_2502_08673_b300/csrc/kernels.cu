@@ -1025,33 +1025,51 @@ __global__ void restart_kernel(int32_t n_pi, const uint32_t* restart, uint64_t s
 }
 
 // ---------------------------------------------------- verification -------
-// Threshold (bit = V > 0), one warp per block of 32 samples x 32 inputs (grid-stride over
-// the blocks, consecutive warps on consecutive sample blocks of one input block).  Lane j
-// loads V[pi][b0 + j] for the block's 32 inputs (coalesced 128-byte rows, 32 loads in
-// flight per warp); the ballot of each input row is its bitsliced word (lane r stores row
-// r's), and lane j's own bits over the 32 inputs are its sample's key word.
-__global__ void __launch_bounds__(256) threshold_kernel(const float* V, int64_t ldv, int32_t n_pi, uint32_t* bits,
-                                                        int64_t ldw, uint32_t* keys, int32_t kw, int64_t B) {
+// Threshold (bit = V > 0) in two passes.  Bits: one warp per (input row, segment of 32
+// words = 1,024 samples); lane j loads V[r][b0 + 32k + j] for k = 0..31 (32 coalesced
+// 128-byte loads in flight, 4 KB contiguous per row), the ballot of load k is word k of the
+// row, and lane k stores it (one coalesced store of the segment's words).
+__global__ void __launch_bounds__(256) threshold_bits_kernel(const float* V, int64_t ldv, int32_t n_pi, uint32_t* bits,
+                                                             int64_t ldw, int64_t B) {
     const int lane = threadIdx.x & 31;
-    const int64_t nb = (B + 31) / 32, ng = (n_pi + 31) / 32;
+    const int64_t W = (B + 31) / 32, nseg = (W + 31) / 32;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nb * ng; t += nwarps) {
-        const int64_t g = t / nb, sb = t - g * nb;
-        const int64_t b = sb * 32 + lane;
-        const int pi0 = (int)(g * 32);
-        const int nrows = min(32, n_pi - pi0);
+    for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nseg * n_pi; t += nwarps) {
+        const int64_t r = t / nseg, seg = t - r * nseg;
+        const float* row = V + r * ldv;
+        const int64_t b0 = seg * 1024 + lane;
         float x[32];
 #pragma unroll
-        for (int r = 0; r < 32; r++) x[r] = (r < nrows && b < B) ? V[(int64_t)(pi0 + r) * ldv + b] : 0.0f;
-        uint32_t key = 0, row = 0;
+        for (int k = 0; k < 32; k++) x[k] = b0 + 32 * k < B ? row[b0 + 32 * k] : 0.0f;
+        uint32_t mine = 0;
 #pragma unroll
-        for (int r = 0; r < 32; r++) {
-            const bool bit = x[r] > 0.0f;
-            key |= (uint32_t)bit << r;
-            const unsigned wb = __ballot_sync(FULL, bit);
-            if (lane == r) row = wb;
+        for (int k = 0; k < 32; k++) {
+            const unsigned wb = __ballot_sync(FULL, x[k] > 0.0f);
+            if (lane == k) mine = wb;
         }
-        if (lane < nrows) bits[(int64_t)(pi0 + lane) * ldw + sb] = row;
+        if (seg * 32 + lane < W) bits[r * ldw + seg * 32 + lane] = mine;
+    }
+}
+
+// Keys: one warp per (word w, block g of 32 inputs); lane i holds word w of input row
+// 32g + i, and the ballot of bit j over the lanes is sample 32w + j's key word g (a 32 x 32
+// bit transpose), kept by lane j.
+__global__ void __launch_bounds__(256) threshold_keys_kernel(const uint32_t* bits, int64_t ldw, int32_t n_pi,
+                                                             uint32_t* keys, int32_t kw, int64_t B) {
+    const int lane = threadIdx.x & 31;
+    const int64_t W = (B + 31) / 32, ng = (n_pi + 31) / 32;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < W * ng; t += nwarps) {
+        const int64_t g = t / W, w = t - g * W;
+        const int64_t r = g * 32 + lane;
+        const uint32_t word = r < n_pi ? bits[r * ldw + w] : 0u;
+        uint32_t key = 0;
+#pragma unroll
+        for (int j = 0; j < 32; j++) {
+            const unsigned kb = __ballot_sync(FULL, (word >> j) & 1u);
+            if (lane == j) key = kb;
+        }
+        const int64_t b = w * 32 + lane;
         if (b < B) keys[b * kw + g] = key;
     }
 }
@@ -1392,9 +1410,12 @@ cudaError_t launch_restart(const DevPlan& p, const uint32_t* restart, uint64_t s
 cudaError_t launch_threshold(const DevPlan& p, const float* V, int64_t ldv, uint32_t* node_bits, int64_t ldw,
                              uint32_t* keys, int64_t B, cudaStream_t s) {
     if (B == 0 || p.n_pi == 0) return cudaSuccess;
-    const int64_t blocks = ((B + 31) / 32) * ((p.n_pi + 31) / 32);  // 32 x 32 blocks, one per warp
-    const unsigned grid = (unsigned)std::min<int64_t>((blocks + 7) / 8, 148 * 8);
-    threshold_kernel<<<grid, 256, 0, s>>>(V, ldv, p.n_pi, node_bits, ldw, keys, p.key_words, B);
+    const int64_t W = (B + 31) / 32;
+    const int64_t bit_tasks = ((W + 31) / 32) * p.n_pi, key_tasks = W * ((p.n_pi + 31) / 32);  // one per warp
+    threshold_bits_kernel<<<(unsigned)std::min<int64_t>((bit_tasks + 7) / 8, 148 * 16), 256, 0, s>>>(
+        V, ldv, p.n_pi, node_bits, ldw, B);
+    threshold_keys_kernel<<<(unsigned)std::min<int64_t>((key_tasks + 7) / 8, 148 * 16), 256, 0, s>>>(
+        node_bits, ldw, p.n_pi, keys, p.key_words, B);
     return cudaGetLastError();
 }
 
