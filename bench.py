@@ -272,7 +272,7 @@ def distinct_keys_across_ranks(keys, device="cuda"):
     return int(np.unique(rows).shape[0])
 
 
-STEP_KERNEL_SOURCES = ("kernels.cu", "relax.cuh", "device.hpp", "tmap.hpp")
+STEP_KERNEL_SOURCES = ("steps.cu", "relax.cuh", "device.hpp", "tmap.hpp")
 
 
 def kernel_source_hash(text=None):
@@ -423,6 +423,62 @@ def timed_rounds(P, torch, plan, ws, opt, steps, rounds, round0, dedup, stream, 
     valid = sum(int(P.valid_mask(x, B).sum()) for x in snaps)
     return {"unique": int(uniq), "ms": ms, "valid": valid, "rounds": rounds, "steps": steps,
             "kernel_ms": [a.elapsed_time(b) for a, b in kev]}
+
+
+def paper_setting_entry(P, torch, stream, rounds=20, warmup=3):
+    """The paper's own sampling setting (Section IV: plain GD, lr 10, 5 iterations, a batch
+    of a million) on the synthetic stand-in of its smallest instances (50 inputs, 50 gates,
+    4 outputs), timed on the same GPU as the main line: whole rounds (init, the fused GD
+    steps, threshold, Boolean pass, CNF check, dedup) with CUDA events, the step kernel's
+    own launches too; distinct solutions over the timed rounds."""
+    w = dict(WORKLOADS["tseitin100_paper"])
+    cnf = P.Cnf.from_dimacs(instance_text(w))
+    plan = P.Plan.create(P.Circuit.build(cnf), cnf)
+    B, steps = w["batch"], w["steps"]
+    opt = P.opt_params("gd", lr=w["lr"])
+    ws = P.new_workspace(plan, B, w["act_dtype"])
+    dedup = P.Dedup.create(plan, max_keys=B * (rounds + warmup), max_batch=B)
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(rounds)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def one(k, ev=None):
+        P.sat_init_normal(plan, ws.V, seed=0, round_=(5 << 24) + k, scale=w["init_scale"])
+        if ev is not None:
+            ev[0].record(stream)
+        P.sat_steps(plan, opt, ws.V, ws.m, ws.v, ws.act, ws.adj, 1, steps, act_dtype=w["act_dtype"])
+        if ev is not None:
+            ev[1].record(stream)
+        P.sat_threshold(plan, ws.V, ws.bits, ws.keys)
+        P.sat_hard_eval(plan, ws.bits, B)
+        P.sat_cnf_check(plan, ws.bits, ws.valid, B)
+        dedup.insert(ws.keys, ws.valid, B, sync=False)
+
+    for k in range(warmup):
+        one(k)
+    torch.cuda.synchronize()
+    before = dedup.count()
+    snaps = []
+    e0.record(stream)
+    for k in range(rounds):
+        one(warmup + k, kev[k])
+        snaps.append(ws.valid.clone())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dedup.check()
+    ms = e0.elapsed_time(e1)
+    uniq = dedup.count() - before
+    valid = sum(int(P.valid_mask(x, B).sum()) for x in snaps)
+    kind = plan.step_kernel(w["act_dtype"])
+    out = {"workload": "tseitin100_paper", "value": uniq / (ms / 1e3), "unit": "unique valid solutions/s",
+           "ms_per_round": ms / rounds, "rounds": rounds, "warmup": warmup, "batch": B, "steps": steps,
+           "optimizer": "gd", "lr": w["lr"], "valid_fraction": valid / (B * rounds), "unique": int(uniq),
+           "step_kernel": kind + "_steps_kernel" if kind == "resident" else "steps_kernel",
+           "step_kernel_ms_avg": statistics.mean(a.elapsed_time(b) for a, b in kev),
+           "gpu_launches": (8 + step_kernel_launches(B, torch, kind)) * rounds,
+           "plan": {k: plan.info[k] for k in ("n_pi", "n_cone_gates", "n_clauses", "n_cone_levels")}}
+    del ws, dedup
+    torch.cuda.empty_cache()
+    return out
 
 
 def chosen_form_entry(P, torch, w, args, stream, peak, peak_kind):
@@ -675,6 +731,9 @@ def main():
     ap.add_argument("--chosen-control", action="store_true",
                     help="with the chosen form: also a proposal trained on other topologies (the control reading) "
                          "and both proposals with FP32 activations")
+    ap.add_argument("--paper-setting", default="auto", choices=["auto", "on", "off"],
+                    help="also time the paper's own setting (GD lr 10, 5 iterations, batch 1M, 50-input "
+                         "instance) on the same GPU (auto: on for the default 20k-gate workload)")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     args.optimizer = args.optimizer or w.get("optimizer", "adam")
@@ -858,6 +917,9 @@ def main():
     # the chosen-form comparison belongs to the single-GPU line (a scaling run times the plain form)
     if args.chosen_form == "on" or (args.chosen_form == "auto" and default_variant and world == 1):
         chosen = chosen_form_entry(P, torch, w, args, stream, peak, peak_kind)
+    paper = None
+    if args.paper_setting == "on" or (args.paper_setting == "auto" and default_variant and world == 1):
+        paper = paper_setting_entry(P, torch, stream)
     e2e = None
     if not args.no_e2e:
         # the user-facing call with host inputs: plan upload, rounds, key download; one
@@ -943,6 +1005,8 @@ def main():
         }
         if chosen is not None:
             line["chosen_form"] = chosen
+        if paper is not None:
+            line["paper_setting"] = paper
         if args.check_every > 0:
             line["config"]["early_exit"] = {"check_every": args.check_every, "max_age": max_age,
                                             "epochs_per_step": -(-steps // args.check_every),

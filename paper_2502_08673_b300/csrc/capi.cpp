@@ -1,6 +1,6 @@
 // extern "C" boundary of the sampler library: argument checks, object
 // lifetimes, device uploads and the end-to-end round loop.  Every step of the
-// path runs in the kernels of kernels.cu.
+// path runs in the kernels of steps.cu, resident.cu and sample.cu.
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
