@@ -428,55 +428,80 @@ def timed_rounds(P, torch, plan, ws, opt, steps, rounds, round0, dedup, stream, 
 def paper_setting_entry(P, torch, stream, rounds=20, warmup=3):
     """The paper's own sampling setting (Section IV: plain GD, lr 10, 5 iterations, a batch
     of a million) on the synthetic stand-in of its smallest instances (50 inputs, 50 gates,
-    4 outputs), timed on the same GPU as the main line: whole rounds (init, the fused GD
-    steps, threshold, Boolean pass, CNF check, dedup) with CUDA events, the step kernel's
-    own launches too; distinct solutions over the timed rounds."""
+    4 outputs), timed on the same GPU as the main line, whole rounds with CUDA events:
+    the instance-compiled round kernel (init, the GD steps, threshold, Boolean pass and
+    clause check in one launch) plus the dedup insert, and beside it the same rounds
+    through the separate kernels (init, fused steps, threshold, Boolean pass, CNF check,
+    dedup).  Distinct solutions over each mode's timed rounds (fresh Philox rounds)."""
     w = dict(WORKLOADS["tseitin100_paper"])
     cnf = P.Cnf.from_dimacs(instance_text(w))
     plan = P.Plan.create(P.Circuit.build(cnf), cnf)
     B, steps = w["batch"], w["steps"]
     opt = P.opt_params("gd", lr=w["lr"])
     ws = P.new_workspace(plan, B, w["act_dtype"])
-    dedup = P.Dedup.create(plan, max_keys=B * (rounds + warmup), max_batch=B)
-    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(rounds)]
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rinfo = plan.round_info(compile=True)
+    kind = plan.step_kernel(w["act_dtype"])
 
-    def one(k, ev=None):
-        P.sat_init_normal(plan, ws.V, seed=0, round_=(5 << 24) + k, scale=w["init_scale"])
-        if ev is not None:
-            ev[0].record(stream)
-        P.sat_steps(plan, opt, ws.V, ws.m, ws.v, ws.act, ws.adj, 1, steps, act_dtype=w["act_dtype"])
-        if ev is not None:
-            ev[1].record(stream)
-        P.sat_threshold(plan, ws.V, ws.bits, ws.keys)
-        P.sat_hard_eval(plan, ws.bits, B)
-        P.sat_cnf_check(plan, ws.bits, ws.valid, B)
+    def one(mode, k, ev=None):
+        rnd = (5 << 24) + (0 if mode == "compiled" else 1 << 20) + k
+        if mode == "compiled":
+            if ev is not None:
+                ev[0].record(stream)
+            P.sat_round_gd(plan, ws.keys, ws.valid, B, w["lr"], steps, seed=0, round_=rnd, scale=w["init_scale"])
+            if ev is not None:
+                ev[1].record(stream)
+        else:
+            P.sat_init_normal(plan, ws.V, seed=0, round_=rnd, scale=w["init_scale"])
+            if ev is not None:
+                ev[0].record(stream)
+            P.sat_steps(plan, opt, ws.V, ws.m, ws.v, ws.act, ws.adj, 1, steps, act_dtype=w["act_dtype"])
+            if ev is not None:
+                ev[1].record(stream)
+            P.sat_threshold(plan, ws.V, ws.bits, ws.keys)
+            P.sat_hard_eval(plan, ws.bits, B)
+            P.sat_cnf_check(plan, ws.bits, ws.valid, B)
         dedup.insert(ws.keys, ws.valid, B, sync=False)
 
-    for k in range(warmup):
-        one(k)
-    torch.cuda.synchronize()
-    before = dedup.count()
-    snaps = []
-    e0.record(stream)
-    for k in range(rounds):
-        one(warmup + k, kev[k])
-        snaps.append(ws.valid.clone())
-    e1.record(stream)
-    torch.cuda.synchronize()
-    dedup.check()
-    ms = e0.elapsed_time(e1)
-    uniq = dedup.count() - before
-    valid = sum(int(P.valid_mask(x, B).sum()) for x in snaps)
-    kind = plan.step_kernel(w["act_dtype"])
-    out = {"workload": "tseitin100_paper", "value": uniq / (ms / 1e3), "unit": "unique valid solutions/s",
-           "ms_per_round": ms / rounds, "rounds": rounds, "warmup": warmup, "batch": B, "steps": steps,
-           "optimizer": "gd", "lr": w["lr"], "valid_fraction": valid / (B * rounds), "unique": int(uniq),
-           "step_kernel": kind + "_steps_kernel" if kind == "resident" else "steps_kernel",
-           "step_kernel_ms_avg": statistics.mean(a.elapsed_time(b) for a, b in kev),
-           "gpu_launches": (8 + step_kernel_launches(B, torch, kind)) * rounds,
-           "plan": {k: plan.info[k] for k in ("n_pi", "n_cone_gates", "n_clauses", "n_cone_levels")}}
-    del ws, dedup
+    res = {}
+    for mode in ("compiled", "separate"):
+        dedup = P.Dedup.create(plan, max_keys=B * (rounds + warmup), max_batch=B)
+        for k in range(warmup):
+            one(mode, k)
+        torch.cuda.synchronize()
+        before = dedup.count()
+        kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(rounds)]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        snaps = []
+        e0.record(stream)
+        for k in range(rounds):
+            one(mode, warmup + k, kev[k])
+            snaps.append(ws.valid.clone())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dedup.check()
+        ms = e0.elapsed_time(e1)
+        uniq = dedup.count() - before
+        res[mode] = {"value": uniq / (ms / 1e3), "ms_per_round": ms / rounds, "unique": int(uniq),
+                     "valid_fraction": sum(int(P.valid_mask(x, B).sum()) for x in snaps) / (B * rounds),
+                     "kernel_ms_avg": statistics.mean(a.elapsed_time(b) for a, b in kev)}
+        del dedup
+    out = {"workload": "tseitin100_paper", "value": res["compiled"]["value"], "unit": "unique valid solutions/s",
+           "ms_per_round": res["compiled"]["ms_per_round"], "rounds": rounds, "warmup": warmup, "batch": B,
+           "steps": steps, "optimizer": "gd", "lr": w["lr"], "unique": res["compiled"]["unique"],
+           "valid_fraction": res["compiled"]["valid_fraction"],
+           "round_kernel": {"name": "sat_round_gd_kernel (instance-compiled: init, steps, threshold, Boolean pass, "
+                                    "clause check)", "ms_avg": res["compiled"]["kernel_ms_avg"],
+                            **{k: rinfo[k] for k in ("registers", "spill_bytes", "compile_ms")}},
+           # per round: the round kernel, dedup insert and commit
+           "gpu_launches": 3 * rounds,
+           "separate_kernels": {"value": res["separate"]["value"], "ms_per_round": res["separate"]["ms_per_round"],
+                                "valid_fraction": res["separate"]["valid_fraction"],
+                                "step_kernel": kind + "_steps_kernel" if kind == "resident" else "steps_kernel",
+                                "step_kernel_ms_avg": res["separate"]["kernel_ms_avg"],
+                                "gpu_launches": (8 + step_kernel_launches(B, torch, kind)) * rounds},
+           "plan": {k: plan.info[k] for k in ("n_pi", "n_cone_pi", "n_cone_gates", "n_gates", "n_clauses",
+                                              "n_cone_levels")}}
+    del ws
     torch.cuda.empty_cache()
     return out
 

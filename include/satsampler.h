@@ -324,6 +324,54 @@ sat_status sat_hard_eval(const sat_plan* p, uint32_t* node_bits, int64_t ldw, in
 sat_status sat_cnf_check(const sat_plan* p, const uint32_t* node_bits, int64_t ldw, uint32_t* valid, int64_t B,
                          void* stream);
 
+/* ------------------------------------ instance-compiled round (plain GD) ---
+ * One sampling round of the paper's own setting (Section IV: plain gradient descent on V,
+ * Eq. 9, for a few iterations) in ONE kernel launch, for small circuits.  The plan's
+ * circuit is generated into the kernel's code (one thread per sample, every logit,
+ * activation and adjoint in registers; indices as immediates) and compiled at run time
+ * with NVRTC for sm_103a on first use.  It computes, with the same device functions in
+ * the same order:
+ *   sat_init_normal(seed, round, init_scale) ; sat_steps(FP32 activations, GD lr, n_steps) ;
+ *   sat_threshold ; sat_hard_eval ; sat_cnf_check
+ * so keys, valid and (when V != NULL) the final logits are bit-identical to those calls
+ * run one after another.  Keys: [B][key_words] uint32 (bit j of word k = input 32k + j);
+ * valid: [ceil(B/32)] words, overwritten (padding bits 0); V: nullable [n_pi][ldv],
+ * ldv >= B, receives every input's final logit.  Nothing else is read or written.
+ *
+ * A plan has the kernel when its circuit is within the generator's limits: at most 256
+ * primary inputs, cone inputs + cone nodes <= 224, at most 4,096 gates and 16,384
+ * clause literals (sat_plan_round_info: available).  Errors: SAT_ERR_ARG for a plan
+ * without it, NULL keys / valid, n_steps < 0, a non-finite lr or init_scale, or the
+ * checks of every per-step call; SAT_ERR_CUDA when NVRTC or the module load fails (the
+ * message holds the compiler log) or the launch fails.  The first call compiles (tens to
+ * hundreds of ms, synchronous); make it before any stream capture.  Compiled programs are
+ * cached per process by their text (the 32 most recently used): plans of the same circuit,
+ * such as those sat_sample builds per call, compile once; sat_release_cached_memory drops
+ * the cache (a plan keeps its own program loaded until it is freed).
+ *
+ * sat_sample_plan runs its rounds through this kernel when the plan has it, it compiled
+ * without register spills, the plan's step kernel is AUTO, and the options ask for plain
+ * GD on FP32 activations without a proposal, initial logits or early exit; its stats
+ * then count the whole round as ms_steps. */
+typedef struct sat_round_info {
+    int32_t available;     /* 1: the plan's circuit is within the limits and has a round kernel */
+    int32_t compiled;      /* 1: compiled and loaded (after a call with compile != 0 or a round) */
+    int32_t registers;     /* registers per thread of the compiled kernel */
+    int32_t spill_bytes;   /* local-memory bytes per thread (0: everything stays in registers) */
+    double compile_ms;     /* NVRTC compilation and module load */
+} sat_round_info;
+/* Host only (no device needed): compile == 0 writes the generated CUDA C++ program of the
+ * circuit's round kernel; compile != 0 compiles it with NVRTC for sm_103a and writes the
+ * compiler's log instead (with ptxas's register and spill report); SAT_ERR_CUDA when the
+ * compilation fails, SAT_ERR_ARG for a circuit beyond the limits.  At most cap bytes are
+ * written (NUL-terminated when they fit); *len = full length. */
+sat_status sat_circuit_round_program(const sat_circuit* c, int32_t compile, char* buf, size_t cap, size_t* len);
+/* compile != 0: compile and load now if not done yet (SAT_ERR_CUDA if that fails). */
+sat_status sat_plan_round_info(const sat_plan* p, int32_t compile, sat_round_info* info);
+sat_status sat_round_gd(const sat_plan* p, float lr, int32_t n_steps, uint64_t seed, uint32_t round,
+                        float init_scale, float* V, int64_t ldv, uint32_t* keys, uint32_t* valid, int64_t B,
+                        void* stream);
+
 /* ----------------------------------------------------- deduplication ---
  * Device hash set of distinct solutions ("non-redundant", end of Section
  * III-A), keyed by the packed primary-input bits (the full assignment is a
@@ -485,7 +533,8 @@ typedef struct sat_sample_stats {
  * allocation (or queued work) still uses to the device, and frees the host buffers kept
  * between calls: the pinned buffer that solutions are downloaded through and the key
  * buffers of up to two freed solution sets (1 MiB-256 MiB each), which the next
- * sat_sample reuses.  Proposal networks are allocated separately (cudaMalloc). */
+ * sat_sample reuses; it also drops the cache of compiled round programs (sat_round_gd).
+ * Proposal networks are allocated separately (cudaMalloc). */
 sat_status sat_cached_memory(uint64_t* reserved_bytes, uint64_t* used_bytes);
 sat_status sat_release_cached_memory(void);
 

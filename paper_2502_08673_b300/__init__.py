@@ -10,5 +10,5 @@ from .api import (  # noqa: F401
     run_epochs, sample, valid_mask, round32, untile, sat_retire, sat_restart, save_checkpoint, load_checkpoint,
     sat_init_normal, sat_forward, sat_backward, sat_opt_update, sat_steps, sat_steps_noalloc, sat_threshold,
     sat_hard_eval, sat_gemm_bf16,
-    sat_cnf_check, cached_memory, release_cached_memory,
+    sat_cnf_check, sat_round_gd, cached_memory, release_cached_memory,
 )

@@ -66,6 +66,11 @@ class SampleStats(C.Structure):
                 ("ms_download", C.c_double)]
 
 
+class RoundInfo(C.Structure):
+    _fields_ = [("available", C.c_int32), ("compiled", C.c_int32), ("registers", C.c_int32),
+                ("spill_bytes", C.c_int32), ("compile_ms", C.c_double)]
+
+
 P, I32, I64, U32, U64, F32, SZ = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_uint64, C.c_float, C.c_size_t
 PP = C.POINTER(C.c_void_p)
 
@@ -106,6 +111,9 @@ PROTOTYPES = {
     "sat_threshold": (I32, [P, P, I64, P, I64, P, I64, P]),
     "sat_hard_eval": (I32, [P, P, I64, I64, P]),
     "sat_cnf_check": (I32, [P, P, I64, P, I64, P]),
+    "sat_circuit_round_program": (I32, [P, I32, C.c_char_p, SZ, C.POINTER(SZ)]),
+    "sat_plan_round_info": (I32, [P, I32, C.POINTER(RoundInfo)]),
+    "sat_round_gd": (I32, [P, F32, I32, U64, U32, F32, P, I64, P, P, I64, P]),
     "sat_dedup_create": (I32, [P, U64, I64, PP]),
     "sat_dedup_insert": (I32, [P, P, P, I64, P, P, P]),
     "sat_dedup_insert_async": (I32, [P, P, P, I64, P]),

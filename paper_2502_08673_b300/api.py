@@ -105,6 +105,16 @@ class Circuit(_Handle):
         check(lib().sat_circuit_dump(self._h, buf, n.value + 1, C.byref(n)))
         return buf.value.decode()
 
+    def round_program(self, compile: bool = False) -> str:
+        """The generated CUDA program of the circuit's instance-compiled round kernel, or with
+        compile the NVRTC log of compiling it for sm_103a (host only; raises for a circuit
+        beyond the kernel's limits or a failed compilation)."""
+        n = C.c_size_t()
+        check(lib().sat_circuit_round_program(self._h, int(compile), None, 0, C.byref(n)))
+        buf = C.create_string_buffer(n.value + 1)
+        check(lib().sat_circuit_round_program(self._h, int(compile), buf, n.value + 1, C.byref(n)))
+        return buf.value.decode()
+
 
 class Plan(_Handle):
     _free = "sat_plan_free"
@@ -144,6 +154,13 @@ class Plan(_Handle):
         k = C.c_int32()
         check(lib().sat_plan_step_kernel(self._h, self.ACT_CODES[act_dtype], C.byref(k)))
         return {1: "tiled", 2: "resident"}[k.value]
+
+    def round_info(self, compile: bool = False) -> dict:
+        """The plan's instance-compiled round kernel: available, compiled, registers,
+        spill_bytes, compile_ms (compile: compile and load it now)."""
+        r = N.RoundInfo()
+        check(lib().sat_plan_round_info(self._h, int(compile), C.byref(r)))
+        return {k: getattr(r, k) for k, _ in r._fields_}
 
     def scratch_elems(self, B: int) -> int:
         n = C.c_uint64()
@@ -421,6 +438,15 @@ def sat_hard_eval(plan: Plan, node_bits, B: int, stream=None):
 
 def sat_cnf_check(plan: Plan, node_bits, valid, B: int, stream=None):
     check(lib().sat_cnf_check(plan.handle, _ptr(node_bits), node_bits.stride(0), _ptr(valid), B, _stream(stream)))
+
+
+def sat_round_gd(plan: Plan, keys, valid, B: int, lr: float, steps: int, seed: int = 0, round_: int = 0,
+                 scale: float = 1.0, V=None, stream=None):
+    """One plain-GD sampling round in the plan's instance-compiled kernel: init, steps,
+    threshold, Boolean pass and clause check (keys [B][key_words] int32, valid
+    [ceil(B/32)] int32; V, if given, [n_pi][ldv] receives the final logits)."""
+    check(lib().sat_round_gd(plan.handle, lr, steps, seed, round_, scale, _ptr(V), V.stride(0) if V is not None else 0,
+                             _ptr(keys), _ptr(valid), B, _stream(stream)))
 
 
 def sat_gemm_bf16(A, B, bias=None, epilogue=0, pre=None, alpha=1.0, out_f32=None, out_bf16=None, out_t_bf16=None,

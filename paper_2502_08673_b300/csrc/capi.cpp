@@ -7,10 +7,12 @@
 #include <algorithm>
 #include <cstdint>
 #include <chrono>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <fstream>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <sstream>
@@ -19,6 +21,7 @@
 #include <vector>
 
 #include "../../include/satsampler.h"
+#include "compiled.hpp"
 #include "device.hpp"
 #include "host.hpp"
 
@@ -59,6 +62,8 @@ struct sat_plan {
     std::vector<int32_t> f_in0, f_in1;
     std::vector<uint8_t> f_gop;
     sat_plan_info info{};
+    // the instance-compiled round kernel (circuits within its limits), compiled on first use
+    std::unique_ptr<sat::CompiledRound> round;
 };
 
 struct sat_dedup {
@@ -354,6 +359,24 @@ sat_status sat_circuit_dump(const sat_circuit* c, char* buf, size_t cap, size_t*
     return SAT_OK;
 }
 
+sat_status sat_circuit_round_program(const sat_circuit* c, int32_t compile, char* buf, size_t cap, size_t* len) {
+    if (!c) return fail(SAT_ERR_ARG, "NULL circuit");
+    std::string why;
+    if (!sat::round_kernel_fits(c->plan, &why)) return fail(SAT_ERR_ARG, "no compiled round kernel: " + why);
+    std::string text = sat::round_kernel_source(c->plan);
+    bool ok = true;
+    if (compile) {
+        std::vector<char> cubin;
+        ok = sat::compile_round_cubin(text, true, cubin, text);
+    }
+    if (len) *len = text.size();
+    if (buf && cap) {
+        size_t n = std::min(cap, text.size() + 1);
+        std::memcpy(buf, text.c_str(), n);
+    }
+    return ok ? SAT_OK : fail(SAT_ERR_CUDA, text);
+}
+
 void sat_circuit_free(sat_circuit* c) { delete c; }
 
 // ---------------------------------------------------------------- plan --
@@ -566,7 +589,47 @@ sat_status sat_plan_create(const sat_circuit* c, const sat_cnf* cnf, sat_plan** 
     I.n_gates = P.in0.size();
     I.n_clauses = (uint64_t)d.n_clauses;
     I.n_fanout_edges = P.fo_g.size();
+    if (sat::round_kernel_fits(P, nullptr)) {
+        p->round.reset(new sat::CompiledRound());
+        p->round->source = sat::round_kernel_source(P);
+    }
     *out = p;
+    return SAT_OK;
+}
+
+sat_status sat_plan_round_info(const sat_plan* p, int32_t compile, sat_round_info* info) {
+    if (!p || !info) return fail(SAT_ERR_ARG, "NULL argument");
+    *info = sat_round_info{};
+    if (!p->round) return SAT_OK;
+    info->available = 1;
+    if (compile) {
+        sat_status s = check_device(p->device);
+        if (s != SAT_OK) return s;
+        std::string err;
+        if (p->round->ensure(err) != cudaSuccess) return fail(SAT_ERR_CUDA, err);
+    }
+    std::lock_guard<std::mutex> g(p->round->mu);
+    if (p->round->mod) {
+        info->compiled = 1;
+        info->registers = p->round->mod->registers;
+        info->spill_bytes = p->round->mod->spill_bytes;
+        info->compile_ms = p->round->mod->compile_ms;
+    }
+    return SAT_OK;
+}
+
+sat_status sat_round_gd(const sat_plan* p, float lr, int32_t n_steps, uint64_t seed, uint32_t round,
+                        float init_scale, float* V, int64_t ldv, uint32_t* keys, uint32_t* valid, int64_t B,
+                        void* stream) {
+    sat_status s = sat::check_plan_call(p, B, V ? ldv : -1);
+    if (s != SAT_OK) return s;
+    if (!keys || !valid) return fail(SAT_ERR_ARG, "NULL keys or valid");
+    if (n_steps < 0 || !std::isfinite(lr) || !std::isfinite(init_scale))
+        return fail(SAT_ERR_ARG, "n_steps must be >= 0, lr and init_scale finite");
+    if (!p->round) return fail(SAT_ERR_ARG, "the plan's circuit exceeds the compiled round kernel's limits");
+    std::string err;
+    if (p->round->ensure(err) != cudaSuccess) return fail(SAT_ERR_CUDA, err);
+    CK(p->round->launch(seed, round, init_scale, lr, n_steps, V, ldv, keys, valid, B, S(stream)));
     return SAT_OK;
 }
 
@@ -1197,6 +1260,7 @@ sat_status sat_release_cached_memory(void) {
         std::lock_guard<std::mutex> lk(g_keys.mu);
         g_keys.bufs.clear();
     }
+    sat::round_cache_clear();
     cudaMemPool_t pool = nullptr;
     cudaError_t e = library_pool(&pool);
     if (e == cudaSuccess) e = cudaMemPoolTrimTo(pool, 0);
@@ -1355,37 +1419,58 @@ sat_status sat_sample_plan(const sat_plan* p, sat_dedup* d, const sat_sample_opt
     sat_sample_stats acc{};
     const sat::OptParams op = opt_of(&o->opt);
     const int spl = o->steps_per_launch > 0 ? o->steps_per_launch : std::max(1, o->steps);
+    // Plain GD on FP32 activations: the whole round (init, steps, threshold, Boolean pass,
+    // clause check) in the plan's instance-compiled kernel when it keeps every value in
+    // registers.
+    bool use_round = false;
+    if (p->round && p->dp.step_kernel == SAT_STEP_KERNEL_AUTO && o->opt.optimizer == SAT_OPT_GD &&
+        o->act_dtype == SAT_ACT_F32 && !o->proposal && !o->init_logits) {
+        std::string err;
+        if (p->round->ensure(err) != cudaSuccess) return fail(SAT_ERR_CUDA, err);
+        use_round = p->round->mod->spill_bytes == 0;
+    }
     std::vector<uint32_t> hvalid(w.ldw);
     uint64_t have = 0;
     sat_status result = SAT_PARTIAL;
     for (int r = 0; r < o->max_rounds; r++) {
         NvtxPhases ph("sat.round");
-        ph.next("sat.init");
-        CK(cudaEventRecord(ev[0], str));
-        if (r == 0 && o->init_logits) {
-            CK(cudaMemcpy2DAsync(w.V, B * 4, o->init_logits, o->init_ld * 4, B * 4, npi, cudaMemcpyDeviceToDevice, str));
-        } else if (o->proposal) {
-            if ((s = sat_mlp_propose(o->proposal, o->seed, o->first_round + (uint32_t)r, o->proposal_tau, w.V, B, B,
-                                     o->stream)) != SAT_OK)
-                return s;
+        if (use_round) {
+            ph.next("sat.round_kernel");
+            CK(cudaEventRecord(ev[0], str));
+            CK(cudaEventRecord(ev[1], str));
+            CK(p->round->launch(o->seed, o->first_round + (uint32_t)r, o->init_scale, op.lr, o->steps, nullptr, 0,
+                                w.keys, w.valid, B, str));
+            CK(cudaEventRecord(ev[2], str));
+            CK(cudaEventRecord(ev[3], str));
         } else {
-            CK(sat::launch_init_normal(dp, o->seed, o->first_round + (uint32_t)r, o->init_scale, w.V, B, B, str));
+            ph.next("sat.init");
+            CK(cudaEventRecord(ev[0], str));
+            if (r == 0 && o->init_logits) {
+                CK(cudaMemcpy2DAsync(w.V, B * 4, o->init_logits, o->init_ld * 4, B * 4, npi, cudaMemcpyDeviceToDevice,
+                                     str));
+            } else if (o->proposal) {
+                if ((s = sat_mlp_propose(o->proposal, o->seed, o->first_round + (uint32_t)r, o->proposal_tau, w.V, B, B,
+                                         o->stream)) != SAT_OK)
+                    return s;
+            } else {
+                CK(sat::launch_init_normal(dp, o->seed, o->first_round + (uint32_t)r, o->init_scale, w.V, B, B, str));
+            }
+            if (o->opt.optimizer == SAT_OPT_ADAM) {  // GD neither reads nor writes m, v
+                CK(cudaMemsetAsync(w.m, 0, npi * B * 4, str));
+                CK(cudaMemsetAsync(w.v, 0, npi * B * 4, str));
+            }
+            CK(cudaEventRecord(ev[1], str));
+            ph.next("sat.steps");
+            for (int t0 = 1; t0 <= o->steps; t0 += spl)
+                CK(sat::launch_steps(dp, *w.lay, o->act_dtype, op, w.V, w.m, w.v, B, w.act, w.adj, nullptr, t0,
+                                     std::min(spl, o->steps - t0 + 1), B, str));
+            CK(cudaEventRecord(ev[2], str));
+            ph.next("sat.verify");
+            CK(sat::launch_threshold(dp, w.V, B, w.bits, w.ldw, w.keys, B, str));
+            CK(sat::launch_hard_eval(dp, w.bits, w.ldw, B, str));
+            CK(sat::launch_cnf_check(dp, w.bits, w.ldw, w.valid, B, str));
+            CK(cudaEventRecord(ev[3], str));
         }
-        if (o->opt.optimizer == SAT_OPT_ADAM) {  // GD neither reads nor writes m, v
-            CK(cudaMemsetAsync(w.m, 0, npi * B * 4, str));
-            CK(cudaMemsetAsync(w.v, 0, npi * B * 4, str));
-        }
-        CK(cudaEventRecord(ev[1], str));
-        ph.next("sat.steps");
-        for (int t0 = 1; t0 <= o->steps; t0 += spl)
-            CK(sat::launch_steps(dp, *w.lay, o->act_dtype, op, w.V, w.m, w.v, B, w.act, w.adj, nullptr, t0,
-                                 std::min(spl, o->steps - t0 + 1), B, str));
-        CK(cudaEventRecord(ev[2], str));
-        ph.next("sat.verify");
-        CK(sat::launch_threshold(dp, w.V, B, w.bits, w.ldw, w.keys, B, str));
-        CK(sat::launch_hard_eval(dp, w.bits, w.ldw, B, str));
-        CK(sat::launch_cnf_check(dp, w.bits, w.ldw, w.valid, B, str));
-        CK(cudaEventRecord(ev[3], str));
         ph.next("sat.dedup");
         uint64_t n = 0;
         if ((s = sat_dedup_count(d, &n, str)) != SAT_OK) return s;
