@@ -491,7 +491,7 @@ def paper_setting_entry(P, torch, stream, rounds=20, warmup=3):
            "valid_fraction": res["compiled"]["valid_fraction"],
            "round_kernel": {"name": "sat_round_gd_kernel (instance-compiled: init, steps, threshold, Boolean pass, "
                                     "clause check)", "ms_avg": res["compiled"]["kernel_ms_avg"],
-                            **{k: rinfo[k] for k in ("registers", "spill_bytes", "compile_ms")}},
+                            **{k: rinfo[k] for k in ("registers", "spill_bytes", "min_blocks", "compile_ms")}},
            # per round: the round kernel, dedup insert and commit
            "gpu_launches": 3 * rounds,
            "separate_kernels": {"value": res["separate"]["value"], "ms_per_round": res["separate"]["ms_per_round"],

@@ -358,7 +358,10 @@ typedef struct sat_round_info {
     int32_t compiled;      /* 1: compiled and loaded (after a call with compile != 0 or a round) */
     int32_t registers;     /* registers per thread of the compiled kernel */
     int32_t spill_bytes;   /* local-memory bytes per thread (0: everything stays in registers) */
-    double compile_ms;     /* NVRTC compilation and module load */
+    int32_t min_blocks;    /* resident blocks of 128 threads per SM the kernel was compiled for: after
+                              the first compilation, ptxas is asked for one block more (twice at most)
+                              as long as that leaves no spills */
+    double compile_ms;     /* NVRTC compilation(s) and module load */
 } sat_round_info;
 /* Host only (no device needed): compile == 0 writes the generated CUDA C++ program of the
  * circuit's round kernel; compile != 0 compiles it with NVRTC for sm_103a and writes the

@@ -68,7 +68,7 @@ class SampleStats(C.Structure):
 
 class RoundInfo(C.Structure):
     _fields_ = [("available", C.c_int32), ("compiled", C.c_int32), ("registers", C.c_int32),
-                ("spill_bytes", C.c_int32), ("compile_ms", C.c_double)]
+                ("spill_bytes", C.c_int32), ("min_blocks", C.c_int32), ("compile_ms", C.c_double)]
 
 
 P, I32, I64, U32, U64, F32, SZ = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_uint64, C.c_float, C.c_size_t

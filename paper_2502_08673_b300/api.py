@@ -157,7 +157,7 @@ class Plan(_Handle):
 
     def round_info(self, compile: bool = False) -> dict:
         """The plan's instance-compiled round kernel: available, compiled, registers,
-        spill_bytes, compile_ms (compile: compile and load it now)."""
+        spill_bytes, min_blocks, compile_ms (compile: compile and load it now)."""
         r = N.RoundInfo()
         check(lib().sat_plan_round_info(self._h, int(compile), C.byref(r)))
         return {k: getattr(r, k) for k, _ in r._fields_}

@@ -613,6 +613,7 @@ sat_status sat_plan_round_info(const sat_plan* p, int32_t compile, sat_round_inf
         info->compiled = 1;
         info->registers = p->round->mod->registers;
         info->spill_bytes = p->round->mod->spill_bytes;
+        info->min_blocks = p->round->mod->min_blocks;
         info->compile_ms = p->round->mod->compile_ms;
     }
     return SAT_OK;

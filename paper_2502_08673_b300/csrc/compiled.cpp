@@ -83,7 +83,9 @@ std::string round_kernel_source(const Plan& P) {
     for (uint32_t i = 0; i < ncpi; i++) cone_of_pi[P.cone_pi_row[i]] = i;
 
     s << "#include \"relax.cuh\"\n#include \"philox.cuh\"\n\n"
-      << "extern \"C\" __global__ void __launch_bounds__(" << ROUND_THREADS << ", 1) " << ROUND_KERNEL_NAME << "(\n"
+      << "#ifndef SAT_MIN_BLOCKS\n#define SAT_MIN_BLOCKS 1\n#endif\n"
+      << "extern \"C\" __global__ void __launch_bounds__(" << ROUND_THREADS << ", SAT_MIN_BLOCKS) "
+      << ROUND_KERNEL_NAME << "(\n"
       << "    unsigned long long seed, unsigned round, float scale, float lr, int n_steps, float* __restrict__ V,\n"
       << "    long long ldv, unsigned* __restrict__ keys, unsigned* __restrict__ valid, long long B) {\n"
       << "  const long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;\n"
@@ -187,7 +189,8 @@ RoundModule::~RoundModule() {
     if (lib) cudaLibraryUnload(lib);
 }
 
-bool compile_round_cubin(const std::string& source, bool verbose, std::vector<char>& cubin, std::string& log) {
+bool compile_round_cubin(const std::string& source, bool verbose, std::vector<char>& cubin, std::string& log,
+                         int min_blocks) {
     nvrtcProgram prog = nullptr;
     const char* headers[] = {kRelaxCuh, kPhiloxCuh, kStubCudaRuntime, kStubCstdint, kStubDevice};
     const char* names[] = {"relax.cuh", "philox.cuh", "cuda_runtime.h", "cstdint", "device.hpp"};
@@ -197,9 +200,10 @@ bool compile_round_cubin(const std::string& source, bool verbose, std::vector<ch
     }
     // IEEE division and square root, fma contraction on, no flush to zero: nvcc's defaults,
     // which the separate kernels are built with
+    const std::string mb = "-DSAT_MIN_BLOCKS=" + std::to_string(min_blocks);
     const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "--fmad=true", "--prec-div=true",
-                          "--prec-sqrt=true", "--ftz=false", "--ptxas-options=-v"};
-    const nvrtcResult rc = nvrtcCompileProgram(prog, verbose ? 7 : 6, opts);
+                          "--prec-sqrt=true", "--ftz=false", mb.c_str(), "--ptxas-options=-v"};
+    const nvrtcResult rc = nvrtcCompileProgram(prog, verbose ? 8 : 7, opts);
     size_t log_size = 0;
     nvrtcGetProgramLogSize(prog, &log_size);
     log.assign(log_size, '\0');
@@ -240,6 +244,39 @@ void round_cache_clear() {
     g_cache.clear();
 }
 
+namespace {
+// Compiles and loads the program with the given minimum of resident blocks per SM
+// (__launch_bounds__), or returns null with err set.
+std::shared_ptr<RoundModule> build_module(const std::string& source, int min_blocks, std::string& err) {
+    std::vector<char> cubin;
+    std::string log;
+    if (!compile_round_cubin(source, false, cubin, log, min_blocks)) {
+        err = log;
+        return nullptr;
+    }
+    auto m = std::make_shared<RoundModule>();
+    cudaError_t e = cudaLibraryLoadData(&m->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    if (e == cudaSuccess) e = cudaLibraryGetKernel(&m->kern, m->lib, ROUND_KERNEL_NAME);
+    cudaFuncAttributes fa{};
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(m->kern));
+    if (e != cudaSuccess) {
+        err = std::string("loading the compiled round kernel failed: ") + cudaGetErrorString(e);
+        return nullptr;
+    }
+    m->registers = fa.numRegs;
+    m->spill_bytes = (int)fa.localSizeBytes;
+    m->min_blocks = min_blocks;
+    return m;
+}
+
+// Blocks of ROUND_THREADS threads that the register file holds (registers are allocated
+// per warp in units of 256, i.e. 8 per thread).
+int blocks_per_sm(int registers) {
+    const int per_thread = (std::max(registers, 1) + 7) / 8 * 8;
+    return std::min(65536 / (per_thread * ROUND_THREADS), 2048 / ROUND_THREADS);
+}
+}  // namespace
+
 cudaError_t CompiledRound::ensure(std::string& err) {
     std::lock_guard<std::mutex> g(mu);
     if (tried) {
@@ -254,23 +291,23 @@ cudaError_t CompiledRound::ensure(std::string& err) {
         return cudaSuccess;
     }
     const auto t0 = std::chrono::steady_clock::now();
-    std::vector<char> cubin;
-    std::string log;
-    if (!compile_round_cubin(source, false, cubin, log)) {
-        error = err = log;
+    std::shared_ptr<RoundModule> m = build_module(source, 1, error);
+    if (!m) {
+        err = error;
         return cudaErrorInvalidValue;
     }
-    auto m = std::make_shared<RoundModule>();
-    cudaError_t e = cudaLibraryLoadData(&m->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
-    if (e == cudaSuccess) e = cudaLibraryGetKernel(&m->kern, m->lib, ROUND_KERNEL_NAME);
-    cudaFuncAttributes fa{};
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(m->kern));
-    if (e != cudaSuccess) {
-        error = err = std::string("loading the compiled round kernel failed: ") + cudaGetErrorString(e);
-        return e;
+    // More resident warps hide more of the kernel's dependency latency (paper setting: 79
+    // registers and 6 blocks per SM, 0.244 ms, against 89 and 5 blocks, 0.258 ms): ask
+    // ptxas for one more block per SM while that keeps every value in registers (at most
+    // two more compilations).
+    for (int tries = 0; tries < 2 && m->spill_bytes == 0; tries++) {
+        const int want = blocks_per_sm(m->registers) + 1;
+        if (want > 2048 / ROUND_THREADS) break;
+        std::string e2;
+        std::shared_ptr<RoundModule> t = build_module(source, want, e2);
+        if (!t || t->spill_bytes != 0 || blocks_per_sm(t->registers) < want) break;
+        m = t;
     }
-    m->registers = fa.numRegs;
-    m->spill_bytes = (int)fa.localSizeBytes;
     m->compile_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     mod = m;
     g_cache.emplace_back(source, m);

@@ -29,14 +29,16 @@ std::string round_kernel_source(const Plan& P);
 
 // NVRTC compilation of a round kernel's source to an sm_103a cubin; log = the compiler's
 // messages (with verbose, ptxas's register and spill report).  False on failure.
-bool compile_round_cubin(const std::string& source, bool verbose, std::vector<char>& cubin, std::string& log);
+// min_blocks: the minimum of resident blocks per SM asked of ptxas (__launch_bounds__).
+bool compile_round_cubin(const std::string& source, bool verbose, std::vector<char>& cubin, std::string& log,
+                         int min_blocks = 1);
 
 // A compiled and loaded round kernel.  Libraries loaded with cudaLibraryLoadData are
 // context-independent: one module serves every device of the process.
 struct RoundModule {
     cudaLibrary_t lib = nullptr;
     cudaKernel_t kern = nullptr;
-    int registers = 0, spill_bytes = 0;
+    int registers = 0, spill_bytes = 0, min_blocks = 1;
     double compile_ms = 0.0;
     ~RoundModule();
 };

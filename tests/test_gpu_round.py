@@ -60,6 +60,9 @@ def test_round_equals_separate_kernels(gpu, name):
     P, cnf, circ, plan, = _plan(INSTANCES[name]())
     info = plan.round_info(compile=True)
     assert info["available"] == 1 and info["compiled"] == 1 and info["spill_bytes"] == 0, info
+    # compiled for as many resident blocks as its registers allow
+    per_thread = (info["registers"] + 7) // 8 * 8
+    assert 1 <= info["min_blocks"] <= min(65536 // (per_thread * 128), 16), info
     for B, lr, steps, scale in [(1, 10.0, 5, 1.0), (37, 10.0, 5, 1.0), (1000, 10.0, 0, 1.5), (4173, 10.0, 1, 1.0),
                                 (4173, 0.5, 30, 0.7)]:
         seed, rnd = 0x9E37_79B9_7F4A + B, 3 + steps
