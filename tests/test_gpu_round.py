@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import oracle
-from workloads import tseitin_random_circuit, planted_3sat, fig1_example_dimacs
+from workloads import tseitin_random_circuit, planted_3sat, fig1_example_dimacs, dimacs_text
 
 pytestmark = pytest.mark.gpu
 
@@ -25,13 +25,20 @@ INSTANCES = {
     "planted3sat_20_60": lambda: planted_3sat(20, 60, 2).dimacs(),
     "tseitin_40_120_d6": lambda: tseitin_random_circuit(40, 120, 6, 3, seed=5).dimacs(),
     "tseitin_100_200_d8": lambda: tseitin_random_circuit(100, 200, 8, 6, seed=7).dimacs(),
+    # edge cases: outputs that are bare inputs (unit clauses; no gate in the cone), the
+    # direct-CNF relaxation (every variable an input, 3-input ORs lowered to gates), a CNF
+    # with no clauses (no cone at all; every sample valid)
+    "units_100": lambda: dimacs_text(100, [[v if (v * 7919) % 3 else -v] for v in range(65, 101)]),
+    "direct_planted3sat_20_60": lambda: planted_3sat(20, 60, 2).dimacs(),
+    "no_clauses_8": lambda: dimacs_text(8, []),
 }
+DIRECT = {"direct_planted3sat_20_60"}
 
 
-def _plan(text):
+def _plan(text, direct=False):
     import paper_2502_08673_b300 as P
     cnf = P.Cnf.from_dimacs(text)
-    circ = P.Circuit.build(cnf)
+    circ = P.Circuit.build(cnf, direct=direct)
     return P, cnf, circ, P.Plan.create(circ, cnf)
 
 
@@ -57,7 +64,7 @@ def _compiled(P, plan, B, lr, steps, seed, rnd, scale, with_V=True):
 
 @pytest.mark.parametrize("name", sorted(INSTANCES))
 def test_round_equals_separate_kernels(gpu, name):
-    P, cnf, circ, plan, = _plan(INSTANCES[name]())
+    P, cnf, circ, plan = _plan(INSTANCES[name](), direct=name in DIRECT)
     info = plan.round_info(compile=True)
     assert info["available"] == 1 and info["compiled"] == 1 and info["spill_bytes"] == 0, info
     # compiled for as many resident blocks as its registers allow

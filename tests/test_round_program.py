@@ -5,7 +5,7 @@ import re
 
 import pytest
 
-from workloads import tseitin_random_circuit, planted_3sat, fig1_example_dimacs
+from workloads import tseitin_random_circuit, planted_3sat, fig1_example_dimacs, dimacs_text
 
 
 def _circuit(text):
@@ -15,7 +15,8 @@ def _circuit(text):
 
 
 @pytest.mark.parametrize("text", [fig1_example_dimacs(), tseitin_random_circuit(50, 50, 5, 4, seed=1).dimacs(),
-                                  planted_3sat(20, 60, 2).dimacs()], ids=["fig1", "paper_50_50_d5", "planted3sat_20_60"])
+                                  planted_3sat(20, 60, 2).dimacs(), dimacs_text(8, [])],
+                         ids=["fig1", "paper_50_50_d5", "planted3sat_20_60", "no_clauses_8"])
 def test_round_program_compiles_without_spills(text):
     P, circ = _circuit(text)
     src = circ.round_program()
