@@ -74,6 +74,31 @@ def test_forward_matches_oracle(gpu, n_out):
     assert (np.abs(got - y) <= 4 * 2 ** -8 * mag + 1e-6).all(), float(np.abs(got - y).max())
 
 
+def test_forward_at_the_1m_gate_workload_size(gpu):
+    """The proposal of the 1M-gate workload (50,000 inputs) at its batch of 8,192 rows, as the
+    sampler runs it (noise drawn on the device, tau = 2, FP32 logits written into V [n][B]):
+    sampled rows (both ends of every 128-row tile boundary case, and random ones) against the
+    FP64 oracle on the same BF16 noise and weights, within the forward bound above."""
+    n_in, h, n_out, R, tau = 64, 256, 50000, 8192, 2.0
+    mlp, theta = _mlp(n_in, h, n_out, R, seed=13)
+    z = mlp.draw_noise(R, seed=4, round_=1)
+    V = torch.empty((n_out, R), dtype=torch.float32, device=gpu)
+    mlp.forward(z, tau=tau, V=V)
+    torch.cuda.synchronize()
+    assert mlp.status() == 0
+    idx = np.array(sorted(set([0, 1, 127, 128, 4095, 4096, R - 1] + list(np.random.default_rng(0).integers(0, R, 17)))))
+    zr = z[torch.tensor(idx, device=gpu)].double().cpu().numpy()
+    th = _rounded_theta(theta, n_in, h, n_out)
+    y, (_, _, _, _, h2) = M.forward(th, zr, n_in, h, n_out)
+    W3 = M.unpack(th, n_in, h, n_out)[4]
+    mag = np.abs(h2) @ np.abs(W3).T + np.abs(theta[-n_out:])
+    got = V[:, torch.tensor(idx, device=gpu)].cpu().double().numpy().T / tau
+    err = np.abs(got - y)
+    print(f"proposal at 50,000 outputs: max |y - y*| / bound = {float((err / (4 * 2 ** -8 * mag + 1e-6)).max()):.3g}")
+    assert (err <= 4 * 2 ** -8 * mag + 1e-6).all(), float(err.max())
+    assert torch.isfinite(V).all()
+
+
 def test_noise_matches_oracle(gpu):
     """sat_mlp_draw_noise = the oracle's Philox4x32-10 + Box-Muller noise, rounded to BF16
     (the GPU's FP32 log/sincos may land on the other side of a BF16 rounding boundary:
