@@ -132,3 +132,33 @@ def test_fullsize_sample_every_returned_assignment_passes_oracle(gpu, setup):
         assert np.array_equal(completed, assign)
         checked += bits.shape[0]
     assert checked == n
+
+
+def test_fullsize_chosen_form_every_returned_assignment_passes_oracle(gpu, setup):
+    """sat_sample in the chosen form's configuration (BF16 activations, initial logits from the
+    proposal network with tau = 2, 120 Adam steps at lr 0.3, early exit every 40 steps with
+    restarts after 160; batch 65,536): every returned assignment satisfies every original clause
+    by the oracle's CNF check, is distinct, and is the Boolean completion of its own input bits.
+    The network keeps its seeded initial weights: what is checked is that lower-precision storage
+    and proposed starts never let an invalid assignment through."""
+    P, inst, plan, orc = setup
+    cnf = P.Cnf.from_dimacs(inst.dimacs())
+    circ = P.Circuit.build(cnf)
+    mlp = P.Mlp.create(64, 256, plan.info["n_pi"], max_rows=B, seed=3)
+    sols = P.sample(circ, cnf, n_wanted=10 ** 12, batch=B, steps=120, max_rounds=1, lr=0.3, seed=1,
+                    act_dtype="bf16", proposal=mlp, tau=2.0, check_every=40, max_age=160)
+    n = len(sols)
+    assert n > 1000, n
+    words = sols.words()
+    assert np.unique(words, axis=0).shape[0] == n
+    pis = np.array(orc.circuit.pis) - 1
+    for lo in range(0, n, 4096):
+        w = words[lo:lo + 4096]
+        bits = np.unpackbits(w.view(np.uint8), axis=1, bitorder="little")[:, : orc.n_vars]
+        assign = np.zeros((bits.shape[0], orc.n_vars + 1), np.uint8)
+        assign[:, 1:] = bits
+        ok = oracle.cnf_check(orc.n_vars, orc.clauses, assign)
+        assert ok.all(), np.nonzero(ok == 0)[0][:10] + lo
+        completed = oracle.full_assignment(orc.flat, oracle.hard_eval(orc.flat, bits[:, pis]))
+        assert np.array_equal(completed, assign)
+    print(f"chosen-form configuration: {n} distinct assignments, all valid")
