@@ -504,6 +504,35 @@ sat_status sat_plan_create(const sat_circuit* c, const sat_cnf* cnf, sat_plan** 
             if (r < (int32_t)P.n_cone_pi || r >= d.seed_row)
                 return bail(fail(SAT_ERR_ARG, "internal error: dead adjoint row outside the ring"));
     }
+    // Adjoint node runs balanced by fan-out edges, one table per warp count of the step
+    // kernels: warp w of W starts at the first node of the level whose edges begin at or
+    // after w / W of the level's edges.
+    std::vector<int32_t> adj_run;
+    {
+        int32_t counts[sat::DevPlan::ADJ_RUN_SETS];
+        sat::step_warp_counts(counts);
+        for (int k = 0; k < sat::DevPlan::ADJ_RUN_SETS; k++) {
+            const int32_t W = counts[k];
+            d.adj_run_w[k] = W;
+            d.adj_run_base[k] = (int64_t)adj_run.size();
+            for (int32_t l = 0; l <= d.n_clev; l++) {
+                const int64_t lo = l == 0 ? 0 : P.c_level_off[l];
+                const int64_t hi = l == 0 ? (int64_t)P.n_cone_pi : P.c_level_off[l + 1];
+                const int64_t e0 = (int64_t)P.fo_off[lo], E = (int64_t)P.fo_off[hi] - e0;
+                int64_t prev = lo;
+                for (int32_t w = 0; w <= W; w++) {
+                    int64_t u = hi;
+                    if (w < W) {
+                        const int64_t target = e0 + E * w / W;
+                        u = std::lower_bound(P.fo_off.begin() + lo, P.fo_off.begin() + hi, target) - P.fo_off.begin();
+                    }
+                    u = std::max(u, prev);
+                    adj_run.push_back((int32_t)u);
+                    prev = u;
+                }
+            }
+        }
+    }
     // bit 31 of the sibling field marks the last edge of each node's range
     for (size_t n = 0; n + 1 < P.fo_off.size(); n++)
         if (P.fo_off[n + 1] > P.fo_off[n]) fe[(size_t)P.fo_off[n + 1] - 1].y |= (int32_t)0x80000000u;
@@ -524,6 +553,7 @@ sat_status sat_plan_create(const sat_circuit* c, const sat_cnf* cnf, sat_plan** 
     if ((st = upload(p, fg, &d.f_gate)) != SAT_OK) return bail(st);
     if ((st = upload(p, P.cl_off, &d.cl_off)) != SAT_OK) return bail(st);
     if ((st = upload(p, cl_lit, &d.cl_lit)) != SAT_OK) return bail(st);
+    if ((st = upload(p, adj_run, &d.adj_run)) != SAT_OK) return bail(st);
     if (!dead_row.empty()) {
         if ((st = upload(p, dead_off, &d.dead_off)) != SAT_OK) return bail(st);
         if ((st = upload(p, dead_row, &d.dead_row)) != SAT_OK) return bail(st);

@@ -64,6 +64,15 @@ struct DevPlan {
     // dead_row[dead_off[l] .. dead_off[l + 1]) are dropped from L2 after level l (ring only).
     const int32_t* dead_off = nullptr;  // [n_clev + 2]
     const int32_t* dead_row = nullptr;
+    // Node runs of the adjoint balanced by fan-out edges (a warp's adjoint work is its edges,
+    // and fan-outs vary from node to node): for the k-th warp count W = adj_run_w[k] of the
+    // step kernels (warps serving one tile), adj_run[adj_run_base[k] + l * (W + 1) + w] is
+    // the first cone node of warp w's run at level l (w = W: the level's end).  A warp count
+    // without a table splits each level's nodes evenly.
+    static constexpr int ADJ_RUN_SETS = 4;
+    int32_t adj_run_w[ADJ_RUN_SETS] = {};
+    int64_t adj_run_base[ADJ_RUN_SETS] = {};
+    const int32_t* adj_run = nullptr;
     DevAct full;                        // the full act layout (row = node)
     int32_t step_kernel = 0;            // fused steps: STEP_KERNEL_AUTO / _TILED / _RESIDENT
     // host mirrors of the level offsets (launch loops need them)
@@ -78,6 +87,10 @@ inline __host__ __device__ int64_t adj_level_row(const DevPlan& p, int l, int32_
 }
 
 enum ActType { ACT_F32 = 0, ACT_BF16 = 1, ACT_F16 = 2 };
+
+// Warps that serve one tile in the tiled step kernels (FP32 and 16-bit activations, one CTA
+// and 2-CTA clusters): the warp counts DevPlan::adj_run is built for.
+void step_warp_counts(int32_t out[DevPlan::ADJ_RUN_SETS]);
 
 // A set-up step that must run once on every device: attributes set with
 // cudaFuncSetAttribute (the dynamic shared-memory opt-in) hold for the device that was

@@ -565,10 +565,20 @@ struct AdjRun {
 __device__ __forceinline__ AdjRun adj_run(const DevPlan& p, const DevAct& L, int l, const TileCtx& c) {
     const int lo = l == 0 ? 0 : __ldg(&p.c_level_off[l]);
     const int hi = l == 0 ? p.n_cone_pi : __ldg(&p.c_level_off[l + 1]);
-    const int per = (hi - lo + c.nvw - 1) / c.nvw;
     AdjRun r;
-    r.u0 = lo + c.vw * per;
-    r.u1 = min(r.u0 + per, hi);
+    int set = -1;
+#pragma unroll
+    for (int k = 0; k < DevPlan::ADJ_RUN_SETS; k++)
+        if (p.adj_run_w[k] == c.nvw) set = k;
+    if (p.adj_run != nullptr && set >= 0) {  // runs of about equal fan-out edge counts
+        const int32_t* t = p.adj_run + p.adj_run_base[set] + (int64_t)l * (c.nvw + 1) + c.vw;
+        r.u0 = __ldg(t);
+        r.u1 = __ldg(t + 1);
+    } else {  // equal node counts
+        const int per = (hi - lo + c.nvw - 1) / c.nvw;
+        r.u0 = min(lo + c.vw * per, hi);
+        r.u1 = min(r.u0 + per, hi);
+    }
     r.arow = (int)((l == 0 ? (int64_t)lo : adj_level_row(p, l, lo)) + (r.u0 - lo));
     r.off = 0;
     r.first = make_int4(-1, 0, 0, 0);
@@ -1021,6 +1031,13 @@ cudaError_t steps_launch(const DevPlan& p, const DevAct& L, const OptParams& o, 
 }
 
 }  // namespace
+
+void step_warp_counts(int32_t out[DevPlan::ADJ_RUN_SETS]) {
+    out[0] = step_threads<float>() / 32;
+    out[1] = 2 * out[0];
+    out[2] = step_threads<__half>() / 32;
+    out[3] = 2 * out[2];
+}
 
 // ------------------------------------------------------------ launchers --
 cudaError_t launch_forward(const DevPlan& p, int act_type, const float* V, int64_t ldv, void* act, float* loss,
