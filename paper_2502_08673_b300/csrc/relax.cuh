@@ -45,30 +45,36 @@ __device__ __forceinline__ void adam_bias(const OptParams& o, int t, float& step
 }
 
 // dL/dV = Pbar * P (1 - P) for one sample with P = sigmoid(vv) given, then GD (Eq. 9) or
-// Adam (PyTorch's formulation, no weight decay) on V, m, v at element r.
+// Adam (PyTorch's formulation, no weight decay) on V, m, v at element r.  Returns the new
+// V (vv when only the gradient is stored).
 template <bool UPDATE>
-__device__ __forceinline__ void input_update_p(const OptParams& o, float* V, float* m, float* v, float* gV, int64_t r,
-                                               float vv, float P, float pbar, float mm, float ss, float step_size,
-                                               float bc2s) {
+__device__ __forceinline__ float input_update_p(const OptParams& o, float* V, float* m, float* v, float* gV, int64_t r,
+                                                float vv, float P, float pbar, float mm, float ss, float step_size,
+                                                float bc2s) {
     const float g = pbar * P * (1.0f - P);
     if (!UPDATE) {
         gV[r] = g;
+        return vv;
     } else if (o.opt == 1) {
-        V[r] = fmaf(-o.lr, g, vv);
+        const float nv = fmaf(-o.lr, g, vv);
+        V[r] = nv;
+        return nv;
     } else {
         const float m1 = fmaf(1.0f - o.b1, g - mm, mm);
         const float v1 = fmaf(o.b2, ss, (1.0f - o.b2) * g * g);
         m[r] = m1;
         v[r] = v1;
-        V[r] = vv - step_size * (m1 / (sqrtf(v1) / bc2s + o.eps));
+        const float nv = vv - step_size * (m1 / (sqrtf(v1) / bc2s + o.eps));
+        V[r] = nv;
+        return nv;
     }
 }
 
 // The same with P computed here.
 template <bool UPDATE>
-__device__ __forceinline__ void input_update(const OptParams& o, float* V, float* m, float* v, float* gV, int64_t r,
-                                             float vv, float pbar, float mm, float ss, float step_size, float bc2s) {
-    input_update_p<UPDATE>(o, V, m, v, gV, r, vv, sigmoidf_(vv), pbar, mm, ss, step_size, bc2s);
+__device__ __forceinline__ float input_update(const OptParams& o, float* V, float* m, float* v, float* gV, int64_t r,
+                                              float vv, float pbar, float mm, float ss, float step_size, float bc2s) {
+    return input_update_p<UPDATE>(o, V, m, v, gV, r, vv, sigmoidf_(vv), pbar, mm, ss, step_size, bc2s);
 }
 
 // Partial sums of the per-sample loss: outputs j = w, w + n, w + 2n, ... go to partial w

@@ -514,10 +514,12 @@ __device__ void forward_levels(const DevPlan& p, const DevAct& L, T* act, Stage&
     }
 }
 
+// inputs_ready: the previous step's update has written the inputs' act rows already.
 template <typename T>
 __device__ void tile_forward(const DevPlan& p, const DevAct& L, const float* __restrict__ V, int64_t ldv, T* act,
-                             Stage& st, const float4* gcoef, const RowMaps& rm, const TileCtx& c) {
-    tile_inputs<T>(p, V, ldv, act, c);
+                             Stage& st, const float4* gcoef, const RowMaps& rm, const TileCtx& c,
+                             bool inputs_ready = false) {
+    if (!inputs_ready) tile_inputs<T>(p, V, ldv, act, c);
     forward_levels<T>(p, L, act, st, gcoef, rm, c, 1, p.n_clev, false);
 }
 
@@ -748,7 +750,7 @@ template <typename T, bool UPDATE>
 __device__ void tile_backward(const DevPlan& p, const DevAct& L, const OptParams& o, float* V, float* m, float* v,
                               float* gV, int64_t ldv, T* act, float* adj, const float* grad_loss,
                               const AdamCorr& ac, Stage& st, const float4* gcoef, const RowMaps& rm,
-                              const TileCtx& c) {
+                              const TileCtx& c, bool next_inputs = false) {
     // the seed row: each sample's weight of its loss (1, or grad_loss), read by the seed edges
     if (c.warp == 0 && c.rank == 0) {
         VF seed_scale = vf_fill(1.0f);
@@ -776,6 +778,10 @@ __device__ void tile_backward(const DevPlan& p, const DevAct& L, const OptParams
         if (p.adj_slots == 0 && l + p.max_span <= p.n_clev) discard_adj_rows(p, l + p.max_span, adj, c);
         if (p.adj_slots > 0 && p.dead_off) discard_dead_rows(p, l, adj, c);
     }
+    // The input level's adjoints become dL/dV and the update; with next_inputs the update
+    // also writes P = sigmoid(V) of the new logits into the inputs' act rows, where the next
+    // step's forward pass starts (after the barrier above: until then the level-0 edges may
+    // still gather those rows as siblings).
     const bool adam = UPDATE && o.opt == 0;
     for (int i0 = c.vw * UBATCH; i0 < p.n_cone_pi; i0 += c.nvw * UBATCH) {
         VF vv[UBATCH], pb[UBATCH], mm[UBATCH], ss[UBATCH];
@@ -803,13 +809,19 @@ __device__ void tile_backward(const DevPlan& p, const DevAct& L, const OptParams
 #pragma unroll
         for (int u = 0; u < UBATCH; u++) {
             if (i0 + u >= p.n_cone_pi) continue;
+            VF y;
 #pragma unroll
-            for (int q = 0; q < VEC; q++)
+            for (int q = 0; q < VEC; q++) {
+                float nv = 0.0f;  // samples past B: sigmoid(0), as the input pass writes them
                 if (q < c.nvalid)
-                    input_update<UPDATE>(o, V, m, v, gV, r[u] + q, vv[u].v[q], pb[u].v[q], mm[u].v[q], ss[u].v[q],
-                                         ac.step[q], ac.bc2s[q]);
+                    nv = input_update<UPDATE>(o, V, m, v, gV, r[u] + q, vv[u].v[q], pb[u].v[q], mm[u].v[q],
+                                              ss[u].v[q], ac.step[q], ac.bc2s[q]);
+                y.v[q] = sigmoidf_(nv);
+            }
+            if (next_inputs) ActIO<T>::st(act + at(i0 + u, c), y);
         }
     }
+    fence_async_global();  // the inputs' act rows are gathered by the next forward pass
     level_sync(c);
     if (p.adj_slots == 0)
         for (int l = 0; l < p.max_span && l <= p.n_clev; l++) discard_adj_rows(p, l, adj, c);
@@ -885,9 +897,10 @@ __global__ void __launch_bounds__(step_threads<T>(), 1) steps_kernel(DevPlan p, 
     for (int s = 0; s < n_steps; s++) {
         AdamCorr ac;
         if (o.opt == 0) ac = adam_corr(o, age, t0 + s, c);
-        tile_forward<T>(p, L, V, ldv, a, st, gcoef, rm, c);
+        tile_forward<T>(p, L, V, ldv, a, st, gcoef, rm, c, s > 0);
         if (loss && s == n_steps - 1 && c.rank == 0) tile_loss<T>(p, L, a, loss, c);
-        tile_backward<T, true>(p, L, o, V, m, v, nullptr, ldv, a, g, nullptr, ac, st, gcoef, rm, c);
+        tile_backward<T, true>(p, L, o, V, m, v, nullptr, ldv, a, g, nullptr, ac, st, gcoef, rm, c,
+                               s + 1 < n_steps);
     }
 }
 
