@@ -19,31 +19,66 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 ctr, uint2 key) {
     return ctr;
 }
 
+// Box-Muller from two Philox words: u1 = ((first >> 8) + 1) / 2^24 in (0, 1] gives the
+// radius sqrt(-2 ln u1), u2 = (second >> 8) / 2^24 the angle 2 pi u2 (sine and cosine).
+__device__ __forceinline__ float bm_radius(uint32_t first) {
+    const float u1 = (float)((first >> 8) + 1u) * (1.0f / 16777216.0f);
+    return sqrtf(-2.0f * logf(u1));
+}
+__device__ __forceinline__ void bm_angle(uint32_t second, float* sn, float* cs) {
+    const float u2 = (float)(second >> 8) * (1.0f / 16777216.0f);
+    sincospif(2.0f * u2, sn, cs);
+}
+
 // Four standard normals of input row r for samples 4c .. 4c + 3: the Philox4x32-10 block at
 // counter (c, r, round, 0) gives two Box-Muller pairs, (cos, sin) of words (x, y) and of
-// words (z, w), with u1 = ((first >> 8) + 1) / 2^24 and u2 = (second >> 8) / 2^24.
+// words (z, w).
 __device__ __forceinline__ float4 normal4(uint32_t c, uint32_t r, uint32_t round, uint2 key) {
     const uint4 o = philox4x32_10(make_uint4(c, r, round, 0u), key);
     float4 z;
     {
-        const float u1 = (float)((o.x >> 8) + 1u) * (1.0f / 16777216.0f);
-        const float u2 = (float)(o.y >> 8) * (1.0f / 16777216.0f);
-        const float rad = sqrtf(-2.0f * logf(u1));
+        const float rad = bm_radius(o.x);
         float sn, cs;
-        sincospif(2.0f * u2, &sn, &cs);
+        bm_angle(o.y, &sn, &cs);
         z.x = rad * cs;
         z.y = rad * sn;
     }
     {
-        const float u1 = (float)((o.z >> 8) + 1u) * (1.0f / 16777216.0f);
-        const float u2 = (float)(o.w >> 8) * (1.0f / 16777216.0f);
-        const float rad = sqrtf(-2.0f * logf(u1));
+        const float rad = bm_radius(o.z);
         float sn, cs;
-        sincospif(2.0f * u2, &sn, &cs);
+        bm_angle(o.w, &sn, &cs);
         z.z = rad * cs;
         z.w = rad * sn;
     }
     return z;
+}
+
+// The threshold bits [scale * z_k > 0] of the same four normals without forming them: the
+// radius is 0 exactly when u1 = 1 (first >> 8 = 2^24 - 1; then z_k = +-0) and positive
+// otherwise, so the sign of scale * z_k is that of scale times the sine or cosine.  Valid for
+// |scale| >= 2^-60, where scale * radius * (sine or cosine) cannot underflow to 0 (radius >=
+// 3.4e-4 and a nonzero sine or cosine of the angle grid >= 3.7e-7).  Bit k of the result is
+// the bit of sample 4c + k.
+__device__ __forceinline__ uint32_t normal4_bits(uint32_t c, uint32_t r, uint32_t round, uint2 key, bool positive) {
+    const uint4 o = philox4x32_10(make_uint4(c, r, round, 0u), key);
+    uint32_t bits = 0u;
+    {
+        float sn, cs;
+        bm_angle(o.y, &sn, &cs);
+        if ((o.x >> 8) != 0xFFFFFFu) {
+            bits |= (positive ? cs > 0.0f : cs < 0.0f) ? 1u : 0u;
+            bits |= (positive ? sn > 0.0f : sn < 0.0f) ? 2u : 0u;
+        }
+    }
+    {
+        float sn, cs;
+        bm_angle(o.w, &sn, &cs);
+        if ((o.z >> 8) != 0xFFFFFFu) {
+            bits |= (positive ? cs > 0.0f : cs < 0.0f) ? 4u : 0u;
+            bits |= (positive ? sn > 0.0f : sn < 0.0f) ? 8u : 0u;
+        }
+    }
+    return bits;
 }
 
 }  // namespace sat

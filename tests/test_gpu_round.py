@@ -70,8 +70,10 @@ def test_round_equals_separate_kernels(gpu, name):
     # compiled for as many resident blocks as its registers allow
     per_thread = (info["registers"] + 7) // 8 * 8
     assert 1 <= info["min_blocks"] <= min(65536 // (per_thread * 128), 16), info
+    # scales: negative (bits of the inputs outside the cone flip with the sign), and below the
+    # threshold under which the kernel forms every normal even without V
     for B, lr, steps, scale in [(1, 10.0, 5, 1.0), (37, 10.0, 5, 1.0), (1000, 10.0, 0, 1.5), (4173, 10.0, 1, 1.0),
-                                (4173, 0.5, 30, 0.7)]:
+                                (4173, 0.5, 30, 0.7), (515, 10.0, 5, -0.8), (300, 10.0, 2, 1e-20)]:
         seed, rnd = 0x9E37_79B9_7F4A + B, 3 + steps
         Vs, ks, vs = _separate(P, plan, B, lr, steps, seed, rnd, scale)
         Vc, kc, vc = _compiled(P, plan, B, lr, steps, seed, rnd, scale)
@@ -79,6 +81,11 @@ def test_round_equals_separate_kernels(gpu, name):
         assert torch.equal(Vc, Vs), (name, B, steps)
         assert torch.equal(kc, ks), (name, B, steps)
         assert torch.equal(vc, vs), (name, B, steps)
+        # without V the inputs outside the cone get their bits from the signs alone
+        _, kn, vn = _compiled(P, plan, B, lr, steps, seed, rnd, scale, with_V=False)
+        torch.cuda.synchronize()
+        assert torch.equal(kn, ks), (name, B, steps, scale)
+        assert torch.equal(vn, vs), (name, B, steps, scale)
     # the step kernel the separate path uses does not matter (tiled = resident, bit for bit)
     plan.set_step_kernel("tiled")
     Vs, ks, vs = _separate(P, plan, 515, 10.0, 5, 11, 12, 1.0)
