@@ -326,7 +326,8 @@ sat_status sat_cnf_check(const sat_plan* p, const uint32_t* node_bits, int64_t l
 
 /* ------------------------------------ instance-compiled round (plain GD) ---
  * One sampling round of the paper's own setting (Section IV: plain gradient descent on V,
- * Eq. 9, for a few iterations) in ONE kernel launch, for small circuits.  The plan's
+ * Eq. 9, for a few iterations) in ONE kernel launch (two when V is requested: the init
+ * kernel writes every input's initial logit first), for small circuits.  The plan's
  * circuit is generated into the kernel's code (one thread per sample, every logit,
  * activation and adjoint in registers; indices as immediates) and compiled at run time
  * with NVRTC for sm_103a on first use.  It computes, with the same device functions in

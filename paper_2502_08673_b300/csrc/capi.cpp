@@ -660,6 +660,9 @@ sat_status sat_round_gd(const sat_plan* p, float lr, int32_t n_steps, uint64_t s
     if (!p->round) return fail(SAT_ERR_ARG, "the plan's circuit exceeds the compiled round kernel's limits");
     std::string err;
     if (p->round->ensure(err) != cudaSuccess) return fail(SAT_ERR_CUDA, err);
+    // the round kernel writes the cone inputs' final logits; every other input keeps its
+    // initial one, which the init kernel writes first
+    if (V) CK(sat::launch_init_normal(p->dp, seed, round, init_scale, V, ldv, B, S(stream)));
     CK(p->round->launch(seed, round, init_scale, lr, n_steps, V, ldv, keys, valid, B, S(stream)));
     return SAT_OK;
 }

@@ -96,11 +96,12 @@ std::string round_kernel_source(const Plan& P) {
     for (int g = 0; g < kw; g++) s << "  unsigned k" << g << " = 0u;\n";
     for (uint32_t i = 0; i < ncpi; i++) s << "  float v" << i << ";\n";
 
-    // Without V to write (and a scale far from 0), the inputs outside every output's cone need
-    // only their threshold bits: the cone inputs are drawn four rows at a time (lane q of each
-    // quad draws the Philox block of the group's q-th row for the quad's four samples, and the
-    // quad exchanges the normals), the others four rows at a time as sign bits (normal4_bits:
-    // no logarithm or square root), exchanged the same way.
+    // Initialisation, four input rows at a time: lane q of each quad draws the Philox block of
+    // the group's q-th row for the quad's four samples (group b / 4), and the quad exchanges
+    // the results so that every lane holds its own sample's value of the group's rows.  The
+    // inputs outside every output's cone need only their threshold bits
+    // (normal4_bits), after the cone inputs' initial logits (normal4).  When V is requested,
+    // the host writes every input's initial logit with the init kernel before this launch.
     std::vector<uint32_t> cone_rows, free_rows;
     for (uint32_t r = 0; r < npi; r++) (cone_of_pi[r] >= 0 ? cone_rows : free_rows).push_back(r);
     auto row_select = [&](const std::vector<uint32_t>& rows, size_t g0) {
@@ -110,57 +111,42 @@ std::string round_kernel_source(const Plan& P) {
           << "u";
         return o.str();
     };
-    s << "  if (V == nullptr && fabsf(scale) >= 1e-18f) {\n"
-      << "    const bool pos = scale > 0.0f;\n";
-    for (size_t g0 = 0; g0 < cone_rows.size(); g0 += 4) {
-        s << "    {\n      const float4 z = sat::normal4(grp, " << row_select(cone_rows, g0) << ", round, key);\n";
-        for (size_t j = 0; j < 4 && g0 + j < cone_rows.size(); j++)
-            s << "      {\n"
-              << "        const float x0 = __shfl_sync(0xffffffffu, z.x, quad | " << j << "u);\n"
-              << "        const float x1 = __shfl_sync(0xffffffffu, z.y, quad | " << j << "u);\n"
-              << "        const float x2 = __shfl_sync(0xffffffffu, z.z, quad | " << j << "u);\n"
-              << "        const float x3 = __shfl_sync(0xffffffffu, z.w, quad | " << j << "u);\n"
-              << "        v" << cone_of_pi[cone_rows[g0 + j]]
-              << " = scale * (q == 0u ? x0 : q == 1u ? x1 : q == 2u ? x2 : x3);\n"
-              << "      }\n";
-        s << "    }\n";
-    }
-    for (size_t g0 = 0; g0 < free_rows.size(); g0 += 4) {
-        s << "    {\n      const unsigned nb = sat::normal4_bits(grp, " << row_select(free_rows, g0)
-          << ", round, key, pos);\n";
-        for (size_t j = 0; j < 4 && g0 + j < free_rows.size(); j++) {
-            const uint32_t r = free_rows[g0 + j];
-            s << "      k" << r / 32 << " |= ((__shfl_sync(0xffffffffu, nb, quad | " << j << "u) >> q) & 1u) << "
-              << r % 32 << ";\n";
-        }
-        s << "    }\n";
-    }
-    s << "  } else {\n";
-    // Initial logits: lane q of each quad draws the Philox block of rows 4t + q for the
-    // quad's four samples (normal4 at group b / 4), and the quad exchanges them so that
-    // every lane holds its own sample's normal of all four rows.
     s << "  // initial logits V = scale * z (the draws of init_normal)\n";
-    for (uint32_t t = 0; 4 * t < npi; t++) {
-        s << "  {\n    const float4 z = sat::normal4(grp, " << 4 * t << "u + q, round, key);\n";
-        for (uint32_t j = 0; j < 4 && 4 * t + j < npi; j++) {
-            const uint32_t r = 4 * t + j;
+    for (size_t g0 = 0; g0 < cone_rows.size(); g0 += 4) {
+        s << "  {\n    const float4 z = sat::normal4(grp, " << row_select(cone_rows, g0) << ", round, key);\n";
+        for (size_t j = 0; j < 4 && g0 + j < cone_rows.size(); j++)
             s << "    {\n"
               << "      const float x0 = __shfl_sync(0xffffffffu, z.x, quad | " << j << "u);\n"
               << "      const float x1 = __shfl_sync(0xffffffffu, z.y, quad | " << j << "u);\n"
               << "      const float x2 = __shfl_sync(0xffffffffu, z.z, quad | " << j << "u);\n"
               << "      const float x3 = __shfl_sync(0xffffffffu, z.w, quad | " << j << "u);\n"
-              << "      const float x = scale * (q == 0u ? x0 : q == 1u ? x1 : q == 2u ? x2 : x3);\n";
-            if (cone_of_pi[r] >= 0) {
-                s << "      v" << cone_of_pi[r] << " = x;\n";
-            } else {  // an input outside every output's cone: its bit is fixed now
-                s << "      k" << r / 32 << " |= (x > 0.0f ? 1u : 0u) << " << r % 32 << ";\n"
-                  << "      if (V != nullptr && in) V[" << r << "LL * ldv + b] = x;\n";
+              << "      v" << cone_of_pi[cone_rows[g0 + j]]
+              << " = scale * (q == 0u ? x0 : q == 1u ? x1 : q == 2u ? x2 : x3);\n"
+              << "    }\n";
+        s << "  }\n";
+    }
+    // their bits come from the signs alone unless the scale is so small that the products
+    // could underflow
+    auto free_bits = [&](const char* draw) {
+        for (size_t g0 = 0; g0 < free_rows.size(); g0 += 4) {
+            s << "    {\n      const unsigned nb = " << draw << "(grp, " << row_select(free_rows, g0)
+              << ", round, key, " << (std::string(draw) == "sat::normal4_bits" ? "scale > 0.0f" : "scale") << ");\n";
+            for (size_t j = 0; j < 4 && g0 + j < free_rows.size(); j++) {
+                const uint32_t r = free_rows[g0 + j];
+                s << "      k" << r / 32 << " |= ((__shfl_sync(0xffffffffu, nb, quad | " << j << "u) >> q) & 1u) << "
+                  << r % 32 << ";\n";
             }
             s << "    }\n";
         }
+    };
+    if (!free_rows.empty()) {
+        s << "  // threshold bits of the inputs outside every output's cone (fixed from here on)\n"
+          << "  if (fabsf(scale) >= sat::BITS_MIN_SCALE) {\n";
+        free_bits("sat::normal4_bits");
+        s << "  } else {\n";
+        free_bits("sat::normal4_bits_formed");
         s << "  }\n";
     }
-    s << "  }\n";
 
     // The steps.
     s << "  #pragma unroll 1\n  for (int step = 0; step < n_steps; step++) {\n";

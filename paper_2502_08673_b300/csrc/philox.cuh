@@ -53,12 +53,13 @@ __device__ __forceinline__ float4 normal4(uint32_t c, uint32_t r, uint32_t round
     return z;
 }
 
-// The threshold bits [scale * z_k > 0] of the same four normals without forming them: the
-// radius is 0 exactly when u1 = 1 (first >> 8 = 2^24 - 1; then z_k = +-0) and positive
-// otherwise, so the sign of scale * z_k is that of scale times the sine or cosine.  Valid for
-// |scale| >= 2^-60, where scale * radius * (sine or cosine) cannot underflow to 0 (radius >=
-// 3.4e-4 and a nonzero sine or cosine of the angle grid >= 3.7e-7).  Bit k of the result is
-// the bit of sample 4c + k.
+// The threshold bits [scale * z_k > 0] of the same four normals (bit k: sample 4c + k),
+// without forming them, for |scale| >= 2^-60 (positive = scale > 0): the radius is 0 exactly
+// when u1 = 1 (first >> 8 = 2^24 - 1; then z = +-0) and positive otherwise, and scale * radius
+// * (sine or cosine) cannot underflow to 0 (radius >= 3.4e-4, a nonzero sine or cosine of the
+// angle grid >= 3.7e-7), so the sign is that of scale times the sine or cosine: no logarithm
+// or square root.
+constexpr float BITS_MIN_SCALE = 8.6736174e-19f;  // 2^-60
 __device__ __forceinline__ uint32_t normal4_bits(uint32_t c, uint32_t r, uint32_t round, uint2 key, bool positive) {
     const uint4 o = philox4x32_10(make_uint4(c, r, round, 0u), key);
     uint32_t bits = 0u;
@@ -79,6 +80,12 @@ __device__ __forceinline__ uint32_t normal4_bits(uint32_t c, uint32_t r, uint32_
         }
     }
     return bits;
+}
+// The same bits for any scale, from the normals themselves.
+__device__ __forceinline__ uint32_t normal4_bits_formed(uint32_t c, uint32_t r, uint32_t round, uint2 key, float scale) {
+    const float4 z = normal4(c, r, round, key);
+    return (scale * z.x > 0.0f ? 1u : 0u) | (scale * z.y > 0.0f ? 2u : 0u) | (scale * z.z > 0.0f ? 4u : 0u) |
+           (scale * z.w > 0.0f ? 8u : 0u);
 }
 
 }  // namespace sat
