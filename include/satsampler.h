@@ -160,6 +160,12 @@ sat_status sat_plan_status(const sat_plan* p, uint32_t* status, int32_t clear, v
  * wait) in a fresh status word, returned in *status.  The kernel then returns
  * normally: the context stays usable.  Synchronises `stream`. */
 sat_status sat_diag_bounded_wait(uint32_t limit_us, uint32_t* status, void* stream);
+/* Diagnostic of the initialisation's sign shortcut (the round kernel's threshold bits of
+ * inputs outside every output's cone): at each of the 2^24 Box-Muller angles 2 pi k / 2^24,
+ * compares the signs (-1, 0, +1) of the sine and cosine that sincospif returns (as the
+ * normal draws compute them) with those read off k; *mismatches = the number of
+ * disagreements (0 expected).  Synchronises `stream`. */
+sat_status sat_diag_angle_signs(uint32_t* mismatches, void* stream);
 /* Elements of one act / adj scratch array for a batch of B samples (enough for
  * either array under every call that takes them without a segment: max(n_cone,
  * adj rows) rows per tile). */

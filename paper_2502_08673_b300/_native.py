@@ -92,6 +92,7 @@ PROTOTYPES = {
     "sat_plan_scratch_elems": (I32, [P, I64, C.POINTER(U64)]),
     "sat_plan_layout_elems": (I32, [P, I32, I64, C.POINTER(U64), C.POINTER(U64)]),
     "sat_diag_bounded_wait": (I32, [U32, C.POINTER(U32), P]),
+    "sat_diag_angle_signs": (I32, [C.POINTER(U32), P]),
     "sat_cached_memory": (I32, [C.POINTER(U64), C.POINTER(U64)]),
     "sat_release_cached_memory": (I32, []),
     "sat_plan_status": (I32, [P, C.POINTER(U32), I32, P]),

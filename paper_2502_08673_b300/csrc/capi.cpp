@@ -252,6 +252,11 @@ bool opt_params_ok(const sat_opt_params* o) { return opt_ok(o); }
 OptParams opt_params_of(const sat_opt_params* o) { return opt_of(o); }
 }  // namespace sat
 
+namespace sat {
+// sample.cu: the angle-grid sign check behind sat_diag_angle_signs
+cudaError_t launch_angle_signs_diag(unsigned* mismatches, cudaStream_t s);
+}  // namespace sat
+
 extern "C" {
 
 const char* sat_version(void) { return "satsampler 0.1 (sm_103a)"; }
@@ -802,6 +807,24 @@ sat_status sat_diag_bounded_wait(uint32_t limit_us, uint32_t* status, void* stre
     cudaFree(d);
     if (e != cudaSuccess) return fail(SAT_ERR_CUDA, std::string("diagnostic kernel: ") + cudaGetErrorString(e));
     *status = h;
+    return SAT_OK;
+}
+
+sat_status sat_diag_angle_signs(uint32_t* mismatches, void* stream) {
+    if (!mismatches) return fail(SAT_ERR_ARG, "NULL argument");
+    unsigned* d = nullptr;
+    if (cudaMalloc(&d, sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SAT_ERR_OOM, "cudaMalloc failed for the counter");
+    }
+    unsigned h = 0;
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(unsigned), S(stream));
+    if (e == cudaSuccess) e = sat::launch_angle_signs_diag(d, S(stream));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(unsigned), cudaMemcpyDeviceToHost, S(stream));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S(stream));
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(SAT_ERR_CUDA, std::string("diagnostic kernel: ") + cudaGetErrorString(e));
+    *mismatches = h;
     return SAT_OK;
 }
 

@@ -53,32 +53,32 @@ __device__ __forceinline__ float4 normal4(uint32_t c, uint32_t r, uint32_t round
     return z;
 }
 
+// Signs (-1, 0, +1) of the cosine and sine of the Box-Muller angle, read off its place on the
+// grid: the angle is pi x with x = k / 2^23, k = second >> 8, and cos(pi x) > 0 on [0, 1/2) and
+// (3/2, 2), = 0 at 1/2 and 3/2, sin(pi x) > 0 on (0, 1), = 0 at 0 and 1.  sincospif's results
+// have these signs at every one of the 2^24 grid points (checked by sat_diag_angle_signs).
+__device__ __forceinline__ void bm_angle_signs(uint32_t second, int* cs, int* sn) {
+    const uint32_t k = second >> 8;
+    *cs = k < 0x400000u ? 1 : k == 0x400000u ? 0 : k < 0xC00000u ? -1 : k == 0xC00000u ? 0 : 1;
+    *sn = k == 0u ? 0 : k < 0x800000u ? 1 : k == 0x800000u ? 0 : -1;
+}
+
 // The threshold bits [scale * z_k > 0] of the same four normals (bit k: sample 4c + k),
 // without forming them, for |scale| >= 2^-60 (positive = scale > 0): the radius is 0 exactly
 // when u1 = 1 (first >> 8 = 2^24 - 1; then z = +-0) and positive otherwise, and scale * radius
 // * (sine or cosine) cannot underflow to 0 (radius >= 3.4e-4, a nonzero sine or cosine of the
-// angle grid >= 3.7e-7), so the sign is that of scale times the sine or cosine: no logarithm
-// or square root.
+// angle grid >= 3.7e-7), so the sign is that of scale times the sine or cosine: no logarithm,
+// square root or sine.
 constexpr float BITS_MIN_SCALE = 8.6736174e-19f;  // 2^-60
 __device__ __forceinline__ uint32_t normal4_bits(uint32_t c, uint32_t r, uint32_t round, uint2 key, bool positive) {
     const uint4 o = philox4x32_10(make_uint4(c, r, round, 0u), key);
+    const int want = positive ? 1 : -1;
     uint32_t bits = 0u;
-    {
-        float sn, cs;
-        bm_angle(o.y, &sn, &cs);
-        if ((o.x >> 8) != 0xFFFFFFu) {
-            bits |= (positive ? cs > 0.0f : cs < 0.0f) ? 1u : 0u;
-            bits |= (positive ? sn > 0.0f : sn < 0.0f) ? 2u : 0u;
-        }
-    }
-    {
-        float sn, cs;
-        bm_angle(o.w, &sn, &cs);
-        if ((o.z >> 8) != 0xFFFFFFu) {
-            bits |= (positive ? cs > 0.0f : cs < 0.0f) ? 4u : 0u;
-            bits |= (positive ? sn > 0.0f : sn < 0.0f) ? 8u : 0u;
-        }
-    }
+    int cs, sn;
+    bm_angle_signs(o.y, &cs, &sn);
+    if ((o.x >> 8) != 0xFFFFFFu) bits |= (cs == want ? 1u : 0u) | (sn == want ? 2u : 0u);
+    bm_angle_signs(o.w, &cs, &sn);
+    if ((o.z >> 8) != 0xFFFFFFu) bits |= (cs == want ? 4u : 0u) | (sn == want ? 8u : 0u);
     return bits;
 }
 // The same bits for any scale, from the normals themselves.

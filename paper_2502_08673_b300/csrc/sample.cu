@@ -283,7 +283,27 @@ __global__ void dedup_commit_kernel(DevDedup d, const uint32_t* keys, int64_t B,
     d.slots[pos] = (d.slots[pos] & 0xffffffff00000000ull) | idx;
 }
 
+// Diagnostic: for every point of the Box-Muller angle grid, the signs of sincospif's sine and
+// cosine (bm_angle, as normal4 computes them) against bm_angle_signs; counts disagreements.
+__global__ void angle_signs_diag_kernel(unsigned* mismatches) {
+    unsigned bad = 0;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < (1u << 24); k += gridDim.x * blockDim.x) {
+        float sn, cs;
+        bm_angle(k << 8, &sn, &cs);
+        int dc, ds;
+        bm_angle_signs(k << 8, &dc, &ds);
+        const int sc = cs > 0.0f ? 1 : cs < 0.0f ? -1 : 0, ss = sn > 0.0f ? 1 : sn < 0.0f ? -1 : 0;
+        bad += (sc != dc) + (ss != ds);
+    }
+    if (bad) atomicAdd(mismatches, bad);
+}
+
 }  // namespace
+
+cudaError_t launch_angle_signs_diag(unsigned* mismatches, cudaStream_t s) {
+    angle_signs_diag_kernel<<<1024, 256, 0, s>>>(mismatches);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_init_normal(const DevPlan& p, uint64_t seed, uint32_t round, float scale, float* V, int64_t ldv,
                                int64_t B, cudaStream_t s) {

@@ -94,6 +94,17 @@ def test_round_equals_separate_kernels(gpu, name):
     assert torch.equal(kc, ks) and torch.equal(vc, vs)
 
 
+def test_angle_signs_match_sincospi(gpu):
+    """The round kernel takes the threshold bits of inputs outside every output's cone from
+    the signs of the Box-Muller angle's sine and cosine read off the angle's grid index; at all
+    2^24 grid points those signs equal the signs of what sincospif returns (zeros included)."""
+    import ctypes as C
+    from paper_2502_08673_b300 import _native as N
+    bad = C.c_uint32(12345)
+    N.check(N.lib().sat_diag_angle_signs(C.byref(bad), None))
+    assert bad.value == 0
+
+
 @pytest.mark.parametrize("name", ["paper_50_50_d5", "planted3sat_20_60", "tseitin_100_200_d8"])
 def test_round_against_oracle(gpu, name):
     """From the oracle's own Philox/Box-Muller logits, five FP64 GD steps (lr 1) land within
